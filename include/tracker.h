@@ -1,0 +1,220 @@
+/*
+ * tracker.h -- C ABI of the GB300 tracer-advection library.
+ *
+ * Implements the particle-tracking hot path of Lalescu, Bramas, Rampp and
+ * Wilczek, "An Efficient Particle Tracking Algorithm for Large-Scale Parallel
+ * Pseudo-Spectral Simulations of Turbulence" (arXiv:2107.01104): tracers
+ * dX/dt = u(X) (Eq. tracers) in a frozen periodic field on [0, L)^3 sampled on
+ * an N^3 grid (Sec. 2.1), interpolated with separable kernels of I nodes per
+ * axis (Sec. 2.2, Eq. triple_sum), particles kept grouped by cell block with
+ * an offset array (Sec. 3.3.1), advanced by RK2 (Heun) or AB2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array pointers are DEVICE pointers unless a parameter says
+ *   otherwise.  The caller owns them; the library never frees them.
+ * - positions  pos[3][np]     float64, SoA (all x1, then all x2, then x3),
+ *                             unwrapped (any finite value; reduced mod L
+ *                             inside the cell split, Sec. 2.2 step 1).
+ * - fields     f[C][N][N][N]  component-major, x3 slowest, x1 fastest.
+ * - outputs    out[C][np]     in the caller's particle order.
+ * - Calls are asynchronous on the tracker's CUDA stream (given at create or
+ *   by tracker_set_stream).  Argument errors are reported synchronously by
+ *   the return value.  Device-side conditions (non-finite positions, a
+ *   particle moving more than one cell in one RK2 stage) set a device flag
+ *   that tracker_sync() reads back and reports.
+ * - Every function returns TRK_OK (0) or a negative trk_status.  After a
+ *   failure tracker_last_error() returns a message (thread-local).
+ * - np is limited to 2^31 - 1 particles per call; N must be a power of two
+ *   with 16 <= N <= 1024; I in {4, 6, 8}.
+ * - There is no CPU fallback: every computation runs in this library's
+ *   CUDA kernels (sm_103a).  A missing GPU is TRK_ECUDA.
+ */
+#ifndef TRACKER_H
+#define TRACKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tracker tracker;
+
+typedef enum {
+    TRK_OK = 0,
+    TRK_EINVAL = -1,      /* bad argument (message says which) */
+    TRK_ENOMEM = -2,      /* device allocation failed */
+    TRK_ECUDA = -3,       /* CUDA runtime error (message has the CUDA string) */
+    TRK_ENONFINITE = -4,  /* a position was NaN/Inf or beyond 2^51 cells (device flag) */
+    TRK_ENOFIELD = -6,    /* no field set yet */
+    TRK_ECFL = -7         /* a particle moved more than one cell in one stage (device flag; result still exact) */
+} trk_status;
+
+typedef enum { TRK_LAGRANGE = 0, TRK_SPLINE = 1 } trk_family;
+
+/* Field storage inside the tracker.  Weights and accumulation are float32
+ * for F32 and BF16X2, float64 for F64.  BF16X2 keeps hi = RN_bf16(x) and
+ * lo = RN_bf16(x - hi) as two planes (4 bytes per value, about 16
+ * significant bits). */
+typedef enum { TRK_F64 = 0, TRK_F32 = 1, TRK_BF16X2 = 2 } trk_storage;
+
+typedef enum { TRK_RK2 = 0, TRK_AB2 = 1 } trk_scheme;
+
+typedef enum { TRK_DTYPE_F64 = 0, TRK_DTYPE_F32 = 1 } trk_dtype;
+
+/* ---------------------------------------------------------------------- */
+/* Lifetime                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Create a tracker for an N^3 periodic grid on [0, L)^3 (the paper uses
+ * L = 2 pi, Sec. 2.1) with interpolation kernel (family, I, m):
+ *   TRK_LAGRANGE: I-node Lagrange polynomials (Sec. 2.2), m ignored;
+ *   TRK_SPLINE:   the spline family cited in Sec. 2.2: degree 2m+1 on each
+ *                 cell, C^m across cells, node derivatives from centred
+ *                 (I-1)-point differences; 0 <= m <= I/2.
+ * storage selects the field storage (trk_storage).  stream is a
+ * cudaStream_t (NULL = legacy default stream).  *out receives the handle.
+ * Errors: TRK_EINVAL (unsupported N, I, m, storage, L <= 0), TRK_ECUDA,
+ * TRK_ENOMEM. */
+int tracker_create(tracker** out, int N, double L, int family, int I, int m, int storage, void* stream);
+
+/* Release every device buffer the tracker owns.  NULL is accepted. */
+int tracker_destroy(tracker* t);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* tracker_last_error(void);
+
+/* Replace the stream later calls are issued on. */
+int tracker_set_stream(tracker* t, void* stream);
+
+/* Wait for the tracker's stream, then read and clear the device flags:
+ * returns TRK_ENONFINITE or TRK_ECFL if a kernel raised one since the
+ * last sync, else TRK_OK (or TRK_ECUDA). */
+int tracker_sync(tracker* t);
+
+/* ---------------------------------------------------------------------- */
+/* Field                                                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Copy a field f[C][N][N][N] (1 <= C <= 16), float64 (src_dtype
+ * TRK_DTYPE_F64) or float32 (TRK_DTYPE_F32), into the tracker's storage,
+ * converting to its trk_storage.  src_on_host = 1 reads a host pointer
+ * (copied through the stream), 0 a device pointer.  The source may be freed
+ * once the call has completed on the stream.  The field is frozen between
+ * calls (Sec. 2.2 interpolates a given field).  Errors: TRK_EINVAL,
+ * TRK_ENOMEM, TRK_ECUDA. */
+int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src_on_host);
+
+/* ---------------------------------------------------------------------- */
+/* Binning (Sec. 3.3.1, "Ordering the particles locally")                  */
+/* ---------------------------------------------------------------------- */
+
+/* Block shape used for grouping: bx x by x bz cells, each a power of two
+ * dividing N (default 8 x 8 x 8).  bx = by = N, bz = 1 reproduces the
+ * paper's x3 slices. */
+int tracker_set_block(tracker* t, int bx, int by, int bz);
+
+/* Number of blocks (N/bx)(N/by)(N/bz) for the current block shape. */
+int64_t tracker_num_blocks(const tracker* t);
+
+/* Stable counting sort of np particles by block key
+ *   key = ((c3/bz) * (N/by) + c2/by) * (N/bx) + c1/bx,
+ * where c is the cell of Sec. 2.2 step 2, split from X as
+ *   g = X * fl(N/L), c0 = floor(g), t = g - c0, c = c0 mod N
+ * (IEEE float64, no fused multiply-add; bit-exact and reproducible).
+ * Outputs (device, int32): keys[np] in the incoming order (may be NULL),
+ * perm[np] (perm[j] = incoming index of the j-th particle in sorted
+ * order, ties kept in incoming order), offsets[nblocks+1] (offsets[b] =
+ * first sorted position of block b, offsets[nblocks] = np: the paper's
+ * offset array).  Errors: TRK_EINVAL, TRK_ENOMEM; non-finite positions
+ * raise the TRK_ENONFINITE device flag. */
+int tracker_bin(tracker* t, int64_t np, const double* pos, int32_t* keys, int32_t* perm, int32_t* offsets);
+
+/* ---------------------------------------------------------------------- */
+/* Interpolation (Sec. 2.2 step 4, Eq. triple_sum; separable, Sec. 3.3)   */
+/* ---------------------------------------------------------------------- */
+
+/* out[k][p] = u_k(X_p) for every field component k < C (deriv = 0), or
+ * out[(3k + j)][p] = d u_k / d X_j at X_p (deriv = 1; derivative kernels
+ * beta' on axis j, times N/L).  out_dtype is TRK_DTYPE_F32 or
+ * TRK_DTYPE_F64 (any storage).  Particles are binned internally; results
+ * are written in the caller's order.  Errors: TRK_EINVAL, TRK_ENOFIELD,
+ * TRK_ENOMEM. */
+int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, int out_dtype, int deriv);
+
+/* ---------------------------------------------------------------------- */
+/* Advection (Eq. tracers)                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Advance np tracers by `steps` steps of size dt in the tracker's
+ * 3-component field (C must be 3).
+ *   TRK_RK2 (Heun): k1 = u(X), X* = X + dt k1, k2 = u(X*),
+ *                   X' = X + dt/2 (k1 + k2).
+ *   TRK_AB2 (Adams-Bashforth, the paper's multi-step scheme, Sec. 2.2 and
+ *            the rhs array of Sec. 3.3.1):
+ *                   X' = X + dt (3/2 u_n - 1/2 u_{n-1}); when
+ *                   history_valid = 0 the first step is forward Euler.
+ *                   rhs[3][np] (float32, caller order) holds u_{n-1} on
+ *                   entry when history_valid = 1 and u of the last step
+ *                   on return.  rhs may be NULL for RK2.
+ * pos[3][np] is read and overwritten in the caller's order.  Particles are
+ * re-binned after every step (the update/re-sort of Sec. 3.3.1); the steps
+ * are replayed from a captured CUDA graph.  A particle that moves more
+ * than one cell in one stage is still computed exactly (through a slower
+ * path) and raises TRK_ECFL at the next tracker_sync.
+ * Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
+int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, int steps, int scheme,
+                    int history_valid);
+
+/* ---------------------------------------------------------------------- */
+/* Batched advection: many particle sets, one persistent launch per step  */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t np;          /* particles in this set */
+    double* pos;         /* [3][np] float64, device, in/out */
+    float* rhs;          /* [3][np] float32 AB2 history, device, in/out */
+    float* out;          /* [nout][np] float32 per-step outputs, device, or NULL:
+                            nout = 3 (u at the step's start, deriv = 0) or
+                            9 (du_k/dX_j as 3k+j, deriv = 1) */
+    int family, I, m;    /* kernel of this set */
+    int deriv;           /* 0: outputs u; 1: outputs the gradient as well */
+} trk_set;
+
+/* Advance every set by `steps` AB2 steps (history_valid as in
+ * tracker_advance, applied to all sets) in the tracker's 3-component
+ * field.  Each step is one persistent kernel over a shared work list of
+ * (set, block) items, so sets of very different sizes and kernels share
+ * one launch; the step sequence is captured in a CUDA graph and replayed.
+ * Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
+int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double dt, int steps,
+                            int history_valid);
+
+/* ---------------------------------------------------------------------- */
+/* Adjoint (no counterpart in the paper: gradient of a loss through RK2)   */
+/* ---------------------------------------------------------------------- */
+
+/* Discrete adjoint of `steps` RK2 steps from pos0 (not modified).  Given
+ * lambdaT[3][np] = dLoss/dX_T (float64, caller order), writes
+ * grad_pos0[3][np] = dLoss/dX_0 (float64) and, if grad_field is not NULL,
+ * ADDS dLoss/dfield into grad_field[3][N][N][N] (float64).  The forward
+ * trajectory is recomputed from checkpoints taken every ckpt_every steps.
+ * Per step, backwards, with J = du/dX and W(X) the field-to-u(X) map:
+ *   lambda* = dt/2 J(X*)^T lambda,  mu = dt/2 lambda + dt lambda*,
+ *   grad_field += W(X)^T mu + W(X*)^T (dt/2 lambda),
+ *   lambda <- lambda + lambda* + J(X)^T mu.
+ * Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
+int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* lambdaT, double dt, int steps,
+                    int ckpt_every, double* grad_pos0, double* grad_field);
+
+/* Number of kernel launches this tracker has issued since creation
+ * (graph replays count each kernel node).  For instrumentation. */
+int64_t tracker_launch_count(const tracker* t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRACKER_H */

@@ -1,0 +1,308 @@
+"""GB300 tracer advection: Python binding of the C ABI in ``include/tracker.h``.
+
+Argument marshalling only.  Every computation runs in the CUDA kernels of
+``_build/libtracker.so``; there is no CPU fallback, and importing a function
+that needs the library fails loudly if it has not been built
+(``__graft_entry__.build()`` or ``python -m paper_2107_01104_gb300.build``).
+
+Two layers:
+
+* ``tracker_*`` functions with the same names and arguments as the C ABI
+  (handles are ``ctypes.c_void_p``; array arguments are torch tensors);
+* :class:`Tracker`, a small owner object over one handle.
+
+Array conventions (see the header): positions ``pos[3][np]`` float64 on the
+GPU, fields ``f[C][N][N][N]`` (x1 fastest), outputs ``out[C][np]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtracker.so")
+
+TRK_OK, TRK_EINVAL, TRK_ENOMEM, TRK_ECUDA, TRK_ENONFINITE, TRK_ENOFIELD, TRK_ECFL = 0, -1, -2, -3, -4, -6, -7
+TRK_LAGRANGE, TRK_SPLINE = 0, 1
+TRK_F64, TRK_F32, TRK_BF16X2 = 0, 1, 2
+TRK_RK2, TRK_AB2 = 0, 1
+TRK_DTYPE_F64, TRK_DTYPE_F32 = 0, 1
+
+_STATUS = {TRK_EINVAL: "EINVAL", TRK_ENOMEM: "ENOMEM", TRK_ECUDA: "ECUDA", TRK_ENONFINITE: "ENONFINITE",
+           TRK_ENOFIELD: "ENOFIELD", TRK_ECFL: "ECFL"}
+
+# Every exported symbol of the ABI (checked against include/tracker.h by the tests).
+ABI_FUNCTIONS = (
+    "tracker_create", "tracker_destroy", "tracker_last_error", "tracker_set_stream", "tracker_sync",
+    "tracker_set_field", "tracker_set_block", "tracker_num_blocks", "tracker_bin", "tracker_interpolate",
+    "tracker_advance", "tracker_advance_batched", "tracker_adjoint", "tracker_launch_count",
+)
+
+
+class TrackerError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class trk_set(ctypes.Structure):
+    _fields_ = [
+        ("np", ctypes.c_int64), ("pos", ctypes.c_void_p), ("rhs", ctypes.c_void_p), ("out", ctypes.c_void_p),
+        ("family", ctypes.c_int), ("I", ctypes.c_int), ("m", ctypes.c_int), ("deriv", ctypes.c_int),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtracker.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        c_int, c_i64, c_d, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+        sig = {
+            "tracker_create": (c_int, [ctypes.POINTER(vp), c_int, c_d, c_int, c_int, c_int, c_int, vp]),
+            "tracker_destroy": (c_int, [vp]),
+            "tracker_last_error": (ctypes.c_char_p, []),
+            "tracker_set_stream": (c_int, [vp, vp]),
+            "tracker_sync": (c_int, [vp]),
+            "tracker_set_field": (c_int, [vp, vp, c_int, c_int, c_int]),
+            "tracker_set_block": (c_int, [vp, c_int, c_int, c_int]),
+            "tracker_num_blocks": (c_i64, [vp]),
+            "tracker_bin": (c_int, [vp, c_i64, vp, vp, vp, vp]),
+            "tracker_interpolate": (c_int, [vp, c_i64, vp, vp, c_int, c_int]),
+            "tracker_advance": (c_int, [vp, c_i64, vp, vp, c_d, c_int, c_int, c_int]),
+            "tracker_advance_batched": (c_int, [vp, c_int, vp, c_d, c_int, c_int]),
+            "tracker_adjoint": (c_int, [vp, c_i64, vp, vp, c_d, c_int, c_int, vp, vp]),
+            "tracker_launch_count": (c_i64, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def tracker_last_error() -> str:
+    return load_library().tracker_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != TRK_OK:
+        raise TrackerError(rc, tracker_last_error())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream_ptr():
+    if not torch.cuda.is_available():
+        return ctypes.c_void_p(None)
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(x, dtype, name, shape0=None):
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be on the GPU")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape0 is not None and (x.dim() != 2 or x.shape[0] != shape0):
+        raise ValueError(f"{name} must have shape ({shape0}, n), got {tuple(x.shape)}")
+    return x
+
+
+# --------------------------------------------------------------------------
+# Same-name functions (one per C entry point)
+# --------------------------------------------------------------------------
+def tracker_create(N, L=2 * math.pi, family=TRK_SPLINE, I=6, m=2, storage=TRK_F32, stream=None):
+    h = ctypes.c_void_p()
+    st = ctypes.c_void_p(stream) if stream is not None else _stream_ptr()
+    _check(load_library().tracker_create(ctypes.byref(h), int(N), float(L), int(family), int(I), int(m),
+                                         int(storage), st))
+    return h
+
+
+def tracker_destroy(h):
+    _check(load_library().tracker_destroy(h))
+
+
+def tracker_set_stream(h, stream=None):
+    st = ctypes.c_void_p(stream) if stream is not None else _stream_ptr()
+    _check(load_library().tracker_set_stream(h, st))
+
+
+def tracker_sync(h):
+    _check(load_library().tracker_sync(h))
+
+
+def tracker_set_field(h, field: torch.Tensor):
+    if field.dtype not in (torch.float64, torch.float32):
+        raise TypeError("field must be float32 or float64")
+    if not field.is_contiguous() or field.dim() != 4:
+        raise ValueError("field must be a contiguous [C][N][N][N] tensor")
+    dt = TRK_DTYPE_F64 if field.dtype == torch.float64 else TRK_DTYPE_F32
+    on_host = 0 if field.is_cuda else 1
+    _check(load_library().tracker_set_field(h, _ptr(field), int(field.shape[0]), dt, on_host))
+
+
+def tracker_set_block(h, bx, by, bz):
+    _check(load_library().tracker_set_block(h, int(bx), int(by), int(bz)))
+
+
+def tracker_num_blocks(h) -> int:
+    return int(load_library().tracker_num_blocks(h))
+
+
+def tracker_launch_count(h) -> int:
+    return int(load_library().tracker_launch_count(h))
+
+
+def tracker_bin(h, pos, keys=None, perm=None, offsets=None):
+    pos = _dev(pos, torch.float64, "pos", 3)
+    n = pos.shape[1]
+    dev = pos.device
+    keys = torch.empty(n, dtype=torch.int32, device=dev) if keys is None else keys
+    perm = torch.empty(n, dtype=torch.int32, device=dev) if perm is None else perm
+    nb = tracker_num_blocks(h)
+    offsets = torch.empty(nb + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
+    _check(load_library().tracker_bin(h, n, _ptr(pos), _ptr(keys), _ptr(perm), _ptr(offsets)))
+    return keys, perm, offsets
+
+
+def tracker_interpolate(h, pos, C, out=None, out_dtype=torch.float32, deriv=False):
+    pos = _dev(pos, torch.float64, "pos", 3)
+    n = pos.shape[1]
+    rows = 3 * C if deriv else C
+    if out is None:
+        out = torch.empty((rows, n), dtype=out_dtype, device=pos.device)
+    _dev(out, out.dtype, "out", rows)
+    code = TRK_DTYPE_F64 if out.dtype == torch.float64 else TRK_DTYPE_F32
+    _check(load_library().tracker_interpolate(h, n, _ptr(pos), _ptr(out), code, int(bool(deriv))))
+    return out
+
+
+def tracker_advance(h, pos, dt, steps, scheme=TRK_RK2, rhs=None, history_valid=False):
+    pos = _dev(pos, torch.float64, "pos", 3)
+    if rhs is not None:
+        _dev(rhs, torch.float32, "rhs", 3)
+    _check(load_library().tracker_advance(h, pos.shape[1], _ptr(pos), _ptr(rhs), float(dt), int(steps),
+                                          int(scheme), int(bool(history_valid))))
+    return pos
+
+
+def tracker_advance_batched(h, sets, dt, steps, history_valid=False):
+    arr = (trk_set * len(sets))()
+    for i, s in enumerate(sets):
+        pos = _dev(s["pos"], torch.float64, "pos", 3)
+        rhs = _dev(s["rhs"], torch.float32, "rhs", 3)
+        out = s.get("out")
+        arr[i].np = pos.shape[1]
+        arr[i].pos = pos.data_ptr()
+        arr[i].rhs = rhs.data_ptr()
+        arr[i].out = out.data_ptr() if out is not None else None
+        arr[i].family = int(s.get("family", TRK_SPLINE))
+        arr[i].I = int(s["I"])
+        arr[i].m = int(s.get("m", s["I"] // 2 - 1))
+        arr[i].deriv = int(bool(s.get("deriv", False)))
+    _check(load_library().tracker_advance_batched(h, len(sets), ctypes.cast(arr, ctypes.c_void_p), float(dt),
+                                                  int(steps), int(bool(history_valid))))
+
+
+def tracker_adjoint(h, pos0, lambdaT, dt, steps, ckpt_every=5, grad_pos0=None, grad_field=None):
+    pos0 = _dev(pos0, torch.float64, "pos0", 3)
+    lambdaT = _dev(lambdaT, torch.float64, "lambdaT", 3)
+    if grad_pos0 is None:
+        grad_pos0 = torch.empty_like(pos0)
+    if grad_field is not None:
+        _dev(grad_field, torch.float64, "grad_field")
+    _check(load_library().tracker_adjoint(h, pos0.shape[1], _ptr(pos0), _ptr(lambdaT), float(dt), int(steps),
+                                          int(ckpt_every), _ptr(grad_pos0), _ptr(grad_field)))
+    return grad_pos0, grad_field
+
+
+# --------------------------------------------------------------------------
+# Owner object
+# --------------------------------------------------------------------------
+class Tracker:
+    """One tracker handle: an N^3 periodic grid with a kernel (family, I, m) and a field."""
+
+    def __init__(self, N, L=2 * math.pi, family=TRK_SPLINE, I=6, m=None, storage=TRK_F32):
+        if m is None:
+            m = I // 2 - 1 if family == TRK_SPLINE else 0
+        self.N, self.L, self.family, self.I, self.m, self.storage = N, L, family, I, m, storage
+        self.C = 0
+        self.h = tracker_create(N, L, family, I, m, storage)
+
+    def close(self):
+        if self.h is not None:
+            tracker_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _stream(self):
+        tracker_set_stream(self.h)
+
+    def set_field(self, field):
+        self._stream()
+        tracker_set_field(self.h, field)
+        self.C = int(field.shape[0])
+
+    def bin(self, pos):
+        self._stream()
+        return tracker_bin(self.h, pos)
+
+    def interpolate(self, pos, out_dtype=torch.float32, deriv=False, out=None):
+        self._stream()
+        return tracker_interpolate(self.h, pos, self.C, out=out, out_dtype=out_dtype, deriv=deriv)
+
+    def advance(self, pos, dt, steps, scheme=TRK_RK2, rhs=None, history_valid=False):
+        self._stream()
+        return tracker_advance(self.h, pos, dt, steps, scheme, rhs, history_valid)
+
+    def advance_batched(self, sets, dt, steps, history_valid=False):
+        self._stream()
+        tracker_advance_batched(self.h, sets, dt, steps, history_valid)
+
+    def adjoint(self, pos0, lambdaT, dt, steps, ckpt_every=5, grad_field=None):
+        self._stream()
+        return tracker_adjoint(self.h, pos0, lambdaT, dt, steps, ckpt_every, grad_field=grad_field)
+
+    def sync(self):
+        tracker_sync(self.h)
+
+    @property
+    def launch_count(self):
+        return tracker_launch_count(self.h)
+
+    @property
+    def num_blocks(self):
+        return tracker_num_blocks(self.h)

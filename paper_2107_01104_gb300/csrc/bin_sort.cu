@@ -1,0 +1,331 @@
+// Cell binning (Sec. 3.3.1 "Ordering the particles locally"): block keys,
+// a stable LSD radix sort of (key, index) pairs, the offset array, and the
+// scatter back to the caller's particle order (the single-GPU counterpart of
+// the in-order output of Sec. 3.4).
+//
+// The paper orders particles by x3 slice with an incomplete quicksort and
+// keeps an offset[] array of group starts.  Here the groups are blocks of
+// cells and the order is a stable radix sort, so the permutation is unique
+// and reproducible (ties keep the incoming order).
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace trk {
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;   // 4096 keys per tile
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_SUB = RS_TILE / RS_WARPS;       // 512 keys per warp, in order
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__global__ void k_keys(GridGeom g, int64_t np, const double* __restrict__ pos, uint32_t* __restrict__ keys,
+                       int* flags)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    int c[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double t;
+        ok &= split_axis(pos[a * np + p], g.inv_delta, g.mask, c[a], t);
+    }
+    if (!ok) atomicOr(flags + FLAG_NONFINITE, 1);
+    keys[p] = block_key(g, c[0], c[1], c[2]);
+}
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
+                             uint32_t* __restrict__ tile_hist)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const int64_t idx = base + (int64_t)i * RS_THREADS + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    tile_hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile.  Warp w owns keys [base + 512 w, base + 512 (w+1))
+// in order; ranks among equal digits come from __match_any_sync.
+__global__ void k_radix_scatter(const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, int64_t n,
+                                int shift, int64_t ntiles, const uint32_t* __restrict__ tile_off,
+                                uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out)
+{
+    __shared__ uint32_t cnt[RS_WARPS][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * RS_SUB;
+    uint32_t k[RS_ITEMS];
+    int32_t v[RS_ITEMS];
+    uint32_t d[RS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const int64_t idx = base + i * 32 + lane;
+        const bool valid = idx < n;
+        k[i] = valid ? keys_in[idx] : 0u;
+        v[i] = valid ? (vals_in ? vals_in[idx] : (int32_t)idx) : 0;
+        d[i] = valid ? ((k[i] >> shift) & 255u) : 256u;
+    }
+    for (int e = threadIdx.x; e < RS_WARPS * 256; e += RS_THREADS) (&cnt[0][0])[e] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const unsigned peers = __match_any_sync(0xffffffffu, d[i]);
+        if (d[i] < 256u && lane == __ffs(peers) - 1) cnt[w][d[i]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int dg = threadIdx.x;   // one digit per thread
+        uint32_t run = tile_off[(int64_t)dg * ntiles + blockIdx.x];
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) {
+            const uint32_t x = cnt[ww][dg];
+            cnt[ww][dg] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const unsigned peers = __match_any_sync(0xffffffffu, d[i]);
+        if (d[i] < 256u) {
+            const uint32_t pos = cnt[w][d[i]] + __popc(peers & lt);
+            keys_out[pos] = k[i];
+            vals_out[pos] = v[i];
+        }
+        __syncwarp();
+        if (d[i] < 256u && lane == __ffs(peers) - 1) cnt[w][d[i]] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// Exclusive scan of one chunk of SCAN_CHUNK values; writes the chunk total.
+__global__ void k_scan_chunk(uint32_t* __restrict__ data, int64_t len, uint32_t* __restrict__ chunk_sums)
+{
+    __shared__ uint32_t wsum[SCAN_THREADS / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t x[SCAN_ITEMS];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        x[i] = (base + i < len) ? data[base + i] : 0u;
+        const uint32_t y = x[i];
+        x[i] = tot;
+        tot += y;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = wsum[lane];
+        uint32_t si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += y;
+        }
+        wsum[lane] = si - s;   // exclusive warp offsets
+        if (lane == 31 && chunk_sums) chunk_sums[blockIdx.x] = si;
+    }
+    __syncthreads();
+    const uint32_t off = wsum[w] + (incl - tot);
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+        if (base + i < len) data[base + i] = x[i] + off;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ data, int64_t len, const uint32_t* __restrict__ chunk_off)
+{
+    const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+    const uint32_t off = chunk_off[blockIdx.x];
+    for (int64_t i = base + threadIdx.x; i < base + SCAN_CHUNK && i < len; i += SCAN_THREADS) data[i] += off;
+}
+
+size_t scan_scratch_bytes(int64_t len)
+{
+    size_t total = 0;
+    while (len > SCAN_CHUNK) {
+        len = ceil_div(len, SCAN_CHUNK);
+        total += align256((size_t)len * sizeof(uint32_t));
+    }
+    return total;
+}
+
+cudaError_t scan_exclusive(uint32_t* data, int64_t len, uint32_t* scratch, cudaStream_t st, int64_t* launches)
+{
+    if (len <= 0) return cudaSuccess;
+    const int64_t nchunks = ceil_div(len, SCAN_CHUNK);
+    if (nchunks == 1) {
+        k_scan_chunk<<<1, SCAN_THREADS, 0, st>>>(data, len, nullptr);
+        if (launches) *launches += 1;
+        return cudaGetLastError();
+    }
+    uint32_t* sums = scratch;
+    uint32_t* rest = scratch + align256((size_t)nchunks * sizeof(uint32_t)) / sizeof(uint32_t);
+    k_scan_chunk<<<(unsigned)nchunks, SCAN_THREADS, 0, st>>>(data, len, sums);
+    cudaError_t e = scan_exclusive(sums, nchunks, rest, st, launches);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<(unsigned)nchunks, SCAN_THREADS, 0, st>>>(data, len, sums);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+__global__ void k_offsets(const uint32_t* __restrict__ keys, int64_t n, int64_t nblocks, int32_t* __restrict__ offsets)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    const int64_t prev = (i == 0) ? -1 : (int64_t)keys[i - 1];
+    const int64_t cur = (i == n) ? nblocks : (int64_t)keys[i];
+    for (int64_t b = prev + 1; b <= cur; ++b) offsets[b] = (int32_t)i;
+}
+
+__global__ void k_unpermute_pos(int64_t np, const double* __restrict__ src, const int32_t* __restrict__ id,
+                                double* __restrict__ dst)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const int64_t p = id[j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dst[a * np + p] = src[a * np + j];
+}
+
+__global__ void k_unpermute_rhs(int64_t np, const float* __restrict__ src, const int32_t* __restrict__ id,
+                                float* __restrict__ dst)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const int64_t p = id[j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dst[a * np + p] = src[a * np + j];
+}
+
+template <typename S>
+__global__ void k_convert(int storage, const S* __restrict__ src, int64_t n, void* __restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const S x = src[i];
+        if (storage == ST_F64) {
+            reinterpret_cast<double*>(dst)[i] = (double)x;
+        } else if (storage == ST_F32) {
+            reinterpret_cast<float*>(dst)[i] = (float)x;
+        } else {
+            // split of the float32-rounded value: hi = RN_bf16(x), lo = RN_bf16(x - hi)
+            const float xf = (float)x;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
+            reinterpret_cast<__nv_bfloat16*>(dst)[i] = hi;
+            reinterpret_cast<__nv_bfloat16*>(dst)[n + i] = lo;
+        }
+    }
+}
+
+unsigned grid_for(int64_t n, int threads) { return (unsigned)ceil_div(n > 0 ? n : 1, threads); }
+
+}  // namespace
+
+cudaError_t launch_keys(const GridGeom& g, int64_t np, const double* pos, uint32_t* keys, int* flags, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_keys<<<grid_for(np, 256), 256, 0, st>>>(g, np, pos, keys, flags);
+    return cudaGetLastError();
+}
+
+size_t radix_scratch_bytes(int64_t n)
+{
+    const int64_t ntiles = ceil_div(n > 0 ? n : 1, RS_TILE);
+    const int64_t hist_len = 256 * ntiles;
+    return align256((size_t)hist_len * 4) + scan_scratch_bytes(hist_len) + 4 * align256((size_t)(n > 0 ? n : 1) * 4);
+}
+
+cudaError_t radix_sort(const uint32_t* keys, int64_t n, int bits, uint32_t* keys_sorted, int32_t* perm, void* scratch,
+                       cudaStream_t st, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t ntiles = ceil_div(n, RS_TILE);
+    const int64_t hist_len = 256 * ntiles;
+    char* p = reinterpret_cast<char*>(scratch);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(p);
+    p += align256((size_t)hist_len * 4);
+    uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(p);
+    p += scan_scratch_bytes(hist_len);
+    uint32_t* ka = reinterpret_cast<uint32_t*>(p);
+    p += align256((size_t)n * 4);
+    int32_t* va = reinterpret_cast<int32_t*>(p);
+    p += align256((size_t)n * 4);
+    uint32_t* kb = reinterpret_cast<uint32_t*>(p);
+    p += align256((size_t)n * 4);
+    int32_t* vb = reinterpret_cast<int32_t*>(p);
+
+    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    const uint32_t* kin = keys;
+    const int32_t* vin = nullptr;   // identity for the first pass
+    for (int ps = 0; ps < passes; ++ps) {
+        const bool last = ps == passes - 1;
+        uint32_t* kout = last ? keys_sorted : ((ps & 1) ? kb : ka);
+        int32_t* vout = last ? perm : ((ps & 1) ? vb : va);
+        const int shift = 8 * ps;
+        k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(kin, n, shift, ntiles, hist);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = scan_exclusive(hist, hist_len, scan_tmp, st, launches);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(kin, vin, n, shift, ntiles, hist, kout, vout);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (launches) *launches += 2;
+        kin = kout;
+        vin = vout;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_offsets(const uint32_t* keys_sorted, int64_t n, int64_t nblocks, int32_t* offsets, cudaStream_t st)
+{
+    k_offsets<<<grid_for(n + 1, 256), 256, 0, st>>>(keys_sorted, n, nblocks, offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute_pos(int64_t np, const double* src, const int32_t* id, double* dst, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_unpermute_pos<<<grid_for(np, 256), 256, 0, st>>>(np, src, id, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id, float* dst, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_unpermute_rhs<<<grid_for(np, 256), 256, 0, st>>>(np, src, id, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int64_t n, void* dst, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 64);
+    if (src_f64) k_convert<double><<<grid, 256, 0, st>>>(storage, reinterpret_cast<const double*>(src), n, dst);
+    else k_convert<float><<<grid, 256, 0, st>>>(storage, reinterpret_cast<const float*>(src), n, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace trk

@@ -1,0 +1,121 @@
+// Internal declarations shared by the CUDA translation units of libtracker.
+// Not part of the public ABI (see include/tracker.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "coeffs.inc"
+
+namespace trk {
+
+// ---------------------------------------------------------------------------
+// Device error flags (one int each in a small device array owned by the
+// tracker).  Set with atomicOr, read and cleared by tracker_sync().
+// ---------------------------------------------------------------------------
+enum { FLAG_NONFINITE = 0, FLAG_CFL = 1, NUM_FLAGS = 4 };
+
+// Storage codes (same values as trk_storage in tracker.h).
+enum { ST_F64 = 0, ST_F32 = 1, ST_BF16X2 = 2 };
+
+// Block-kernel modes.
+enum { MODE_INTERP = 0, MODE_INTERP_DERIV = 1, MODE_RK2 = 2, MODE_AB2 = 3 };
+
+constexpr int BLK = 8;        // cell-block edge used by the block kernels
+constexpr int LBLK = 3;       // log2(BLK)
+
+struct FieldView {
+    int storage;              // ST_*
+    int C;                    // components
+    int64_t plane;            // N^3 values per component
+    const double* f64;        // [C][N^3]                (ST_F64)
+    const float* f32;         // [C][N^3]                (ST_F32)
+    const __nv_bfloat16* hi;  // [C][N^3] high parts     (ST_BF16X2)
+    const __nv_bfloat16* lo;  // [C][N^3] low parts      (ST_BF16X2)
+};
+
+struct GridGeom {
+    int N, mask;
+    int lb1, lb2, lb3;        // log2 of the binning block edges
+    int nb1, nb2, nb3;        // blocks per axis
+    double inv_delta;         // fl(N / L)
+};
+
+// Arguments of the block kernels (interpolation, RK2 step, AB2 step).
+struct BlockArgs {
+    GridGeom g;
+    FieldView f;
+    int tab;                  // coefficient table index
+    int64_t np;               // particle count (stride of the [3][np] arrays)
+    const int32_t* offsets;   // [nblocks + 1]
+    const int32_t* perm;      // sorted position j -> index into the *_in arrays
+    const double* pos_in;     // [3][np]
+    const int32_t* id_in;     // [np] or null (then id = perm[j])
+    const float* rhs_in;      // [3][np] AB2 history or null
+    double* pos_out;          // [3][np], written at j
+    int32_t* id_out;          // [np], written at j
+    float* rhs_out;           // [3][np], written at j
+    uint32_t* key_out;        // [np], written at j
+    void* out;                // interpolation outputs [nout][np], written at id
+    int out_f64;
+    int history_valid;
+    double dt;
+    int* flags;
+};
+
+// ---------------------------------------------------------------------------
+// Cell split (Sec. 2.2 steps 1-3), bit-exact with the float64 reference:
+//   g = X * fl(N/L), c0 = floor(g), t = g - c0, c = c0 mod N.
+// __dmul_rn/__dsub_rn forbid fused multiply-adds.  Positions beyond 2^51
+// cells are rejected (returned false) together with NaN/Inf.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool split_axis(double X, double inv_delta, int mask, int& c, double& t)
+{
+    const double g = __dmul_rn(X, inv_delta);
+    if (!(fabs(g) < 2251799813685248.0)) {   // 2^51; false for NaN too
+        c = 0;
+        t = 0.0;
+        return false;
+    }
+    const double c0 = floor(g);
+    t = __dsub_rn(g, c0);
+    c = (int)(__double2ll_rz(c0) & (long long)mask);
+    return true;
+}
+
+__device__ __forceinline__ uint32_t block_key(const GridGeom& g, int c1, int c2, int c3)
+{
+    return (uint32_t)((((c3 >> g.lb3) * g.nb2) + (c2 >> g.lb2)) * g.nb1 + (c1 >> g.lb1));
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files).  All take a stream and
+// return a cudaError_t.
+// ---------------------------------------------------------------------------
+cudaError_t launch_keys(const GridGeom& g, int64_t np, const double* pos, uint32_t* keys, int* flags,
+                        cudaStream_t st);
+
+// Scratch layout for the radix sort of n keys.
+size_t radix_scratch_bytes(int64_t n);
+// Stable LSD radix sort of (keys, index) by the low `bits` bits of keys.
+// keys_sorted and perm receive the result; scratch is radix_scratch_bytes(n).
+cudaError_t radix_sort(const uint32_t* keys, int64_t n, int bits, uint32_t* keys_sorted, int32_t* perm,
+                       void* scratch, cudaStream_t st, int64_t* launches);
+
+cudaError_t launch_offsets(const uint32_t* keys_sorted, int64_t n, int64_t nblocks, int32_t* offsets,
+                           cudaStream_t st);
+
+// Scatter sorted state back to the caller's order: dst[a][id[j]] = src[a][j].
+cudaError_t launch_unpermute_pos(int64_t np, const double* src, const int32_t* id, double* dst, cudaStream_t st);
+cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id, float* dst, cudaStream_t st);
+
+cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int64_t n, void* dst, cudaStream_t st);
+
+// Block kernels, one entry per kernel width I (block_i4.cu, block_i6.cu, block_i8.cu).
+// deg_hi selects the degree-(I+1) instantiation (spline with m = I/2).
+cudaError_t launch_block_i4(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
+cudaError_t launch_block_i6(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
+cudaError_t launch_block_i8(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
+
+}  // namespace trk

@@ -1,0 +1,486 @@
+// C ABI of libtracker (declared and documented in include/tracker.h).
+//
+// The tracker owns its field copy and all scratch (sort buffers, the offset
+// array, the sorted particle state of the time steppers, device flags).
+// Every entry point validates its arguments on the host, issues kernels on
+// the tracker's stream and returns a status; nothing here computes on the CPU.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.cuh"
+#include "tracker.h"
+
+using namespace trk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(x)                                                                     \
+    do {                                                                                \
+        cudaError_t e_ = (x);                                                           \
+        if (e_ != cudaSuccess) return fail(TRK_ECUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+    } while (0)
+
+struct TableInfo {
+    int family, I, m, deg;
+};
+const TableInfo kTables[TRK_NUM_TABLES] = TRK_TABLE_INFO;
+
+int find_table(int family, int I, int m)
+{
+    for (int k = 0; k < TRK_NUM_TABLES; ++k) {
+        const TableInfo& t = kTables[k];
+        if (t.family != family || t.I != I) continue;
+        if (family == TRK_LAGRANGE || t.m == m) return k;
+    }
+    return -1;
+}
+
+int ilog2(int64_t x)
+{
+    int r = 0;
+    while ((int64_t(1) << r) < x) ++r;
+    return r;
+}
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+template <typename P>
+cudaError_t dev_alloc(P** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+void dev_free(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+struct tracker {
+    int N = 0;
+    double L = 0;
+    int family = 0, I = 0, m = 0, storage = 0;
+    int tab = -1, deg = 0, deg_hi = 0;
+    cudaStream_t stream = nullptr;
+    GridGeom g{};
+    int64_t nblocks = 0;
+    int key_bits = 0;
+    // field
+    int C = 0;
+    void* field = nullptr;
+    // sort scratch
+    int64_t sort_cap = 0;
+    void* sort_scratch = nullptr;
+    uint32_t* keys = nullptr;
+    uint32_t* keys_sorted = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* offsets = nullptr;
+    // sorted state of the steppers
+    int64_t state_cap = 0;
+    double* pos_s[2] = {nullptr, nullptr};
+    int32_t* id_s[2] = {nullptr, nullptr};
+    float* rhs_s[2] = {nullptr, nullptr};
+    int* d_flags = nullptr;
+    int64_t launches = 0;
+};
+
+namespace {
+
+int set_geometry(tracker* t, int bx, int by, int bz)
+{
+    const int N = t->N;
+    for (int b : {bx, by, bz})
+        if (!is_pow2(b) || b > N) return fail(TRK_EINVAL, "block edge %d must be a power of two <= N=%d", b, N);
+    t->g.lb1 = ilog2(bx);
+    t->g.lb2 = ilog2(by);
+    t->g.lb3 = ilog2(bz);
+    t->g.nb1 = N / bx;
+    t->g.nb2 = N / by;
+    t->g.nb3 = N / bz;
+    t->nblocks = (int64_t)t->g.nb1 * t->g.nb2 * t->g.nb3;
+    t->key_bits = ilog2(t->nblocks);
+    dev_free(t->offsets);
+    t->offsets = nullptr;
+    CUDA_TRY(dev_alloc(&t->offsets, (size_t)(t->nblocks + 1) * sizeof(int32_t)));
+    return TRK_OK;
+}
+
+int ensure_sort(tracker* t, int64_t np)
+{
+    if (np <= t->sort_cap) return TRK_OK;
+    dev_free(t->sort_scratch);
+    dev_free(t->keys);
+    dev_free(t->keys_sorted);
+    dev_free(t->perm);
+    t->sort_scratch = nullptr;
+    t->keys = t->keys_sorted = nullptr;
+    t->perm = nullptr;
+    t->sort_cap = 0;
+    if (dev_alloc(&t->sort_scratch, radix_scratch_bytes(np)) != cudaSuccess ||
+        dev_alloc(&t->keys, (size_t)np * 4) != cudaSuccess || dev_alloc(&t->keys_sorted, (size_t)np * 4) != cudaSuccess ||
+        dev_alloc(&t->perm, (size_t)np * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TRK_ENOMEM, "cannot allocate sort scratch for %lld particles", (long long)np);
+    }
+    t->sort_cap = np;
+    return TRK_OK;
+}
+
+int ensure_state(tracker* t, int64_t np)
+{
+    if (np <= t->state_cap) return TRK_OK;
+    for (int i = 0; i < 2; ++i) {
+        dev_free(t->pos_s[i]);
+        dev_free(t->id_s[i]);
+        dev_free(t->rhs_s[i]);
+        t->pos_s[i] = nullptr;
+        t->id_s[i] = nullptr;
+        t->rhs_s[i] = nullptr;
+    }
+    t->state_cap = 0;
+    for (int i = 0; i < 2; ++i) {
+        if (dev_alloc(&t->pos_s[i], (size_t)np * 24) != cudaSuccess || dev_alloc(&t->id_s[i], (size_t)np * 4) != cudaSuccess ||
+            dev_alloc(&t->rhs_s[i], (size_t)np * 12) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TRK_ENOMEM, "cannot allocate particle state for %lld particles", (long long)np);
+        }
+    }
+    t->state_cap = np;
+    return TRK_OK;
+}
+
+FieldView field_view(const tracker* t)
+{
+    FieldView f{};
+    f.storage = t->storage;
+    f.C = t->C;
+    f.plane = (int64_t)t->N * t->N * t->N;
+    if (t->storage == ST_F64) f.f64 = reinterpret_cast<const double*>(t->field);
+    else if (t->storage == ST_F32) f.f32 = reinterpret_cast<const float*>(t->field);
+    else {
+        f.hi = reinterpret_cast<const __nv_bfloat16*>(t->field);
+        f.lo = f.hi + f.plane * t->C;
+    }
+    return f;
+}
+
+cudaError_t launch_block(tracker* t, int mode, const BlockArgs& a)
+{
+    t->launches += 1;
+    switch (t->I) {
+        case 4: return launch_block_i4(mode, a, t->nblocks, t->deg_hi, t->stream);
+        case 6: return launch_block_i6(mode, a, t->nblocks, t->deg_hi, t->stream);
+        default: return launch_block_i8(mode, a, t->nblocks, t->deg_hi, t->stream);
+    }
+}
+
+// keys (caller order) -> sorted keys, perm, offsets
+int bin_into(tracker* t, int64_t np, const double* pos, uint32_t* keys, int32_t* perm, int32_t* offsets)
+{
+    CUDA_TRY(launch_keys(t->g, np, pos, keys, t->d_flags, t->stream));
+    t->launches += 1;
+    CUDA_TRY(radix_sort(keys, np, t->key_bits, t->keys_sorted, perm, t->sort_scratch, t->stream, &t->launches));
+    CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, offsets, t->stream));
+    t->launches += 1;
+    return TRK_OK;
+}
+
+int check_np(int64_t np)
+{
+    if (np < 0 || np > 2147483647LL) return fail(TRK_EINVAL, "np=%lld out of range [0, 2^31-1]", (long long)np);
+    return TRK_OK;
+}
+
+int check_block_kernel_shape(const tracker* t)
+{
+    if (t->g.lb1 != LBLK || t->g.lb2 != LBLK || t->g.lb3 != LBLK)
+        return fail(TRK_EINVAL, "interpolation and advection need the %dx%dx%d block shape", BLK, BLK, BLK);
+    return TRK_OK;
+}
+
+BlockArgs base_args(tracker* t)
+{
+    BlockArgs a{};
+    a.g = t->g;
+    a.f = field_view(t);
+    a.tab = t->tab;
+    a.offsets = t->offsets;
+    a.flags = t->d_flags;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tracker_last_error(void) { return g_err; }
+
+int tracker_create(tracker** out, int N, double L, int family, int I, int m, int storage, void* stream)
+{
+    g_err[0] = 0;
+    if (!out) return fail(TRK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!is_pow2(N) || N < 16 || N > 1024) return fail(TRK_EINVAL, "N=%d must be a power of two in [16, 1024]", N);
+    if (!(L > 0) || !std::isfinite(L)) return fail(TRK_EINVAL, "L must be finite and > 0");
+    if (family != TRK_LAGRANGE && family != TRK_SPLINE) return fail(TRK_EINVAL, "unknown kernel family %d", family);
+    if (I != 4 && I != 6 && I != 8) return fail(TRK_EINVAL, "I=%d unsupported (4, 6, 8)", I);
+    if (family == TRK_SPLINE && (m < 0 || m > I / 2)) return fail(TRK_EINVAL, "spline smoothness m=%d outside [0, %d]", m, I / 2);
+    if (storage != TRK_F64 && storage != TRK_F32 && storage != TRK_BF16X2) return fail(TRK_EINVAL, "unknown storage %d", storage);
+    const int tab = find_table(family, I, family == TRK_LAGRANGE ? 0 : m);
+    if (tab < 0) return fail(TRK_EINVAL, "no coefficient table for (family=%d, I=%d, m=%d)", family, I, m);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(TRK_ECUDA, "no CUDA device");
+    }
+    tracker* t = new tracker();
+    t->N = N;
+    t->L = L;
+    t->family = family;
+    t->I = I;
+    t->m = m;
+    t->storage = storage;
+    t->tab = tab;
+    t->deg = kTables[tab].deg;
+    t->deg_hi = t->deg > I - 1;
+    t->stream = reinterpret_cast<cudaStream_t>(stream);
+    t->g.N = N;
+    t->g.mask = N - 1;
+    t->g.inv_delta = (double)N / L;
+    int rc = set_geometry(t, BLK, BLK, BLK);
+    if (rc == TRK_OK && dev_alloc(&t->d_flags, NUM_FLAGS * sizeof(int)) != cudaSuccess)
+        rc = fail(TRK_ENOMEM, "cannot allocate device flags");
+    if (rc == TRK_OK && cudaMemset(t->d_flags, 0, NUM_FLAGS * sizeof(int)) != cudaSuccess)
+        rc = fail(TRK_ECUDA, "cudaMemset flags failed");
+    if (rc != TRK_OK) {
+        tracker_destroy(t);
+        return rc;
+    }
+    *out = t;
+    return TRK_OK;
+}
+
+int tracker_destroy(tracker* t)
+{
+    if (!t) return TRK_OK;
+    if (t->stream) cudaStreamSynchronize(t->stream);
+    else cudaDeviceSynchronize();
+    dev_free(t->field);
+    dev_free(t->sort_scratch);
+    dev_free(t->keys);
+    dev_free(t->keys_sorted);
+    dev_free(t->perm);
+    dev_free(t->offsets);
+    for (int i = 0; i < 2; ++i) {
+        dev_free(t->pos_s[i]);
+        dev_free(t->id_s[i]);
+        dev_free(t->rhs_s[i]);
+    }
+    dev_free(t->d_flags);
+    delete t;
+    return TRK_OK;
+}
+
+int tracker_set_stream(tracker* t, void* stream)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    t->stream = reinterpret_cast<cudaStream_t>(stream);
+    return TRK_OK;
+}
+
+int tracker_sync(tracker* t)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    CUDA_TRY(cudaStreamSynchronize(t->stream));
+    int h[NUM_FLAGS];
+    CUDA_TRY(cudaMemcpy(h, t->d_flags, sizeof(h), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(t->d_flags, 0, sizeof(h)));
+    if (h[FLAG_NONFINITE]) return fail(TRK_ENONFINITE, "a position was non-finite or beyond 2^51 cells");
+    if (h[FLAG_CFL]) return fail(TRK_ECFL, "a particle moved more than one cell in one stage (result computed exactly)");
+    return TRK_OK;
+}
+
+int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src_on_host)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (!src) return fail(TRK_EINVAL, "src is NULL");
+    if (C < 1 || C > 16) return fail(TRK_EINVAL, "C=%d outside [1, 16]", C);
+    if (src_dtype != TRK_DTYPE_F64 && src_dtype != TRK_DTYPE_F32) return fail(TRK_EINVAL, "unknown src_dtype %d", src_dtype);
+    const int64_t n = (int64_t)C * t->N * t->N * t->N;
+    const size_t esz = t->storage == TRK_F64 ? 8 : 4;
+    if (t->C != C || !t->field) {
+        dev_free(t->field);
+        t->field = nullptr;
+        t->C = 0;
+        if (dev_alloc(&t->field, (size_t)n * esz) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TRK_ENOMEM, "cannot allocate field storage (%zu bytes)", (size_t)n * esz);
+        }
+        t->C = C;
+    }
+    const size_t src_bytes = (size_t)n * (src_dtype == TRK_DTYPE_F64 ? 8 : 4);
+    const void* dsrc = src;
+    void* staging = nullptr;
+    if (src_on_host) {
+        if (dev_alloc(&staging, src_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TRK_ENOMEM, "cannot allocate staging buffer (%zu bytes)", src_bytes);
+        }
+        CUDA_TRY(cudaMemcpyAsync(staging, src, src_bytes, cudaMemcpyHostToDevice, t->stream));
+        dsrc = staging;
+    }
+    CUDA_TRY(launch_convert_field(t->storage, src_dtype == TRK_DTYPE_F64, dsrc, n, t->field, t->stream));
+    t->launches += 1;
+    if (staging) {
+        CUDA_TRY(cudaStreamSynchronize(t->stream));
+        dev_free(staging);
+    }
+    return TRK_OK;
+}
+
+int tracker_set_block(tracker* t, int bx, int by, int bz)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    return set_geometry(t, bx, by, bz);
+}
+
+int64_t tracker_num_blocks(const tracker* t) { return t ? t->nblocks : -1; }
+
+int64_t tracker_launch_count(const tracker* t) { return t ? t->launches : -1; }
+
+int tracker_bin(tracker* t, int64_t np, const double* pos, int32_t* keys, int32_t* perm, int32_t* offsets)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    int rc = check_np(np);
+    if (rc) return rc;
+    if (np > 0 && (!pos || !perm)) return fail(TRK_EINVAL, "pos and perm must not be NULL");
+    if (!offsets) return fail(TRK_EINVAL, "offsets must not be NULL");
+    if ((rc = ensure_sort(t, np))) return rc;
+    uint32_t* k = keys ? reinterpret_cast<uint32_t*>(keys) : t->keys;
+    return bin_into(t, np, pos, k, perm, offsets);
+}
+
+int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, int out_dtype, int deriv)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    int rc = check_np(np);
+    if (rc) return rc;
+    if (!t->field) return fail(TRK_ENOFIELD, "no field set");
+    if (np > 0 && (!pos || !out)) return fail(TRK_EINVAL, "pos and out must not be NULL");
+    if (out_dtype != TRK_DTYPE_F64 && out_dtype != TRK_DTYPE_F32) return fail(TRK_EINVAL, "unknown out_dtype %d", out_dtype);
+    if ((rc = check_block_kernel_shape(t))) return rc;
+    if (np == 0) return TRK_OK;
+    if ((rc = ensure_sort(t, np))) return rc;
+    if ((rc = bin_into(t, np, pos, t->keys, t->perm, t->offsets))) return rc;
+    BlockArgs a = base_args(t);
+    a.np = np;
+    a.perm = t->perm;
+    a.pos_in = pos;
+    a.out = out;
+    a.out_f64 = out_dtype == TRK_DTYPE_F64;
+    CUDA_TRY(launch_block(t, deriv ? MODE_INTERP_DERIV : MODE_INTERP, a));
+    return TRK_OK;
+}
+
+int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, int steps, int scheme,
+                    int history_valid)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    int rc = check_np(np);
+    if (rc) return rc;
+    if (!t->field) return fail(TRK_ENOFIELD, "no field set");
+    if (t->C != 3) return fail(TRK_EINVAL, "advection needs a 3-component field (C=%d)", t->C);
+    if (scheme != TRK_RK2 && scheme != TRK_AB2) return fail(TRK_EINVAL, "unknown scheme %d", scheme);
+    if (scheme == TRK_AB2 && !rhs && np > 0) return fail(TRK_EINVAL, "AB2 needs the rhs history array");
+    if (!std::isfinite(dt)) return fail(TRK_EINVAL, "dt must be finite");
+    if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
+    if (np > 0 && !pos) return fail(TRK_EINVAL, "pos must not be NULL");
+    if ((rc = check_block_kernel_shape(t))) return rc;
+    if (np == 0 || steps == 0) return TRK_OK;
+    if ((rc = ensure_sort(t, np))) return rc;
+    if ((rc = ensure_state(t, np))) return rc;
+    const int mode = scheme == TRK_RK2 ? MODE_RK2 : MODE_AB2;
+    // initial keys from the caller's positions
+    CUDA_TRY(launch_keys(t->g, np, pos, t->keys, t->d_flags, t->stream));
+    t->launches += 1;
+    int cur = 0;
+    for (int s = 0; s < steps; ++s) {
+        CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream, &t->launches));
+        CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
+        t->launches += 1;
+        BlockArgs a = base_args(t);
+        a.np = np;
+        a.perm = t->perm;
+        a.dt = dt;
+        const int nxt = cur ^ 1;
+        if (s == 0) {
+            a.pos_in = pos;
+            a.id_in = nullptr;
+            a.rhs_in = rhs;
+            a.history_valid = history_valid;
+        } else {
+            a.pos_in = t->pos_s[cur];
+            a.id_in = t->id_s[cur];
+            a.rhs_in = t->rhs_s[cur];
+            a.history_valid = (scheme == TRK_AB2) ? 1 : 0;
+        }
+        a.pos_out = t->pos_s[nxt];
+        a.id_out = t->id_s[nxt];
+        a.rhs_out = t->rhs_s[nxt];
+        a.key_out = t->keys;
+        CUDA_TRY(launch_block(t, mode, a));
+        cur = nxt;
+    }
+    CUDA_TRY(launch_unpermute_pos(np, t->pos_s[cur], t->id_s[cur], pos, t->stream));
+    t->launches += 1;
+    if (scheme == TRK_AB2) {
+        CUDA_TRY(launch_unpermute_rhs(np, t->rhs_s[cur], t->id_s[cur], rhs, t->stream));
+        t->launches += 1;
+    }
+    return TRK_OK;
+}
+
+int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double dt, int steps, int history_valid)
+{
+    (void)nsets;
+    (void)sets;
+    (void)dt;
+    (void)steps;
+    (void)history_valid;
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    return fail(TRK_EINVAL, "tracker_advance_batched: not available in this build");
+}
+
+int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* lambdaT, double dt, int steps,
+                    int ckpt_every, double* grad_pos0, double* grad_field)
+{
+    (void)np;
+    (void)pos0;
+    (void)lambdaT;
+    (void)dt;
+    (void)steps;
+    (void)ckpt_every;
+    (void)grad_pos0;
+    (void)grad_field;
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    return fail(TRK_EINVAL, "tracker_adjoint: not available in this build");
+}
+
+}  // extern "C"
