@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the tracer-advection hot path on GB300.
+
+Workload (one bench "step" = one tracker_advance call = the whole hot path:
+cell split, block keys, stable radix re-binning, stencil gather + separable
+contraction, fused RK2 update, re-binned after every RK2 step):
+
+    256^3 float32 velocity field (divergence-free random Fourier modes,
+    |k| <= 85, E(k) ~ k^-5/3), 2^20 uniform tracers with float64 positions,
+    spline kernel I = 6 (m = 2), 100 RK2 steps of dt = 5e-3.
+
+Metric: particle-steps/s (particles x RK2 steps per second), whole job.
+Multi-GPU: replicas (each rank advances its own tracer set in its own copy of
+the field; no data-path collective), weak scaling.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on the same
+workload (bounded particle sample per step); it is the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, KMAX, NP, I, M, DT, INNER = 256, 85, 1 << 20, 6, 2, 5e-3, 100
+SEED_FIELD, SEED_POS = 1001, 2
+WORKLOAD = (f"{N}^3 fp32 velocity |k|<={KMAX}, 2^20 uniform tracers (fp64 positions), spline I={I} m={M}, "
+            f"{INNER} RK2 steps dt={DT}, re-binned every step")
+METRIC, UNIT = "particle-steps/s", "particle-steps/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--inner", type=int, default=INNER, help="RK2 steps per bench step (workload: 100)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the float64 and split-bf16 forms")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+def field_and_particles():
+    import numpy as np
+
+    import synth
+
+    field = synth.velocity_field_np(N, KMAX, SEED_FIELD).astype(np.float32)
+    pos = synth.uniform_particles_np(NP, SEED_POS)
+    return field, pos
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("block_kernel.cuh", "block_i6.cu", "internal.cuh", "coeffs.inc"):
+        with open(os.path.join(ROOT, "paper_2107_01104_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(sha):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it matches the source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get("k_block_rk2_f32_i6")
+    if not e or e.get("source_sha") != sha:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def sync_flags(tr, trk, notes):
+    """Wait for the tracker; a CFL flag (a particle moved more than one cell in
+    one stage, computed exactly through the slow path) is recorded, not fatal."""
+    try:
+        tr.sync()
+    except trk.TrackerError as e:
+        if e.status != trk.TRK_ECFL:
+            raise
+        notes["cfl_slow_path_used"] = True
+
+
+def cpu_baseline(field, pos, seconds):
+    """The oracle as it stands, on this host's cores, on a bounded particle sample."""
+    import numpy as np
+
+    import oracle
+
+    f64 = field.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.advance(f64, pos[:, :256], DT, 2, oracle.SPLINE, I, M)
+    cal = (time.perf_counter() - t0) / (256 * 2)
+    n = int(max(512, min(NP, seconds / max(cal, 1e-9) / INNER)))
+    t0 = time.perf_counter()
+    oracle.advance(f64, pos[:, :n], DT, INNER, oracle.SPLINE, I, M)
+    el = time.perf_counter() - t0
+    return {"value": n * INNER / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} of the {NP} tracers x {INNER} RK2 steps ({el:.1f} s)"}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    field, pos = field_and_particles()
+    f64 = field.astype(np.float64)
+    # bounded sample per step, sized so the whole run stays within a few minutes
+    t0 = time.perf_counter()
+    oracle.advance(f64, pos[:, :256], DT, 2, oracle.SPLINE, I, M)
+    cal = (time.perf_counter() - t0) / (256 * 2)
+    per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
+    n = int(max(256, min(NP, per_step_s / max(cal, 1e-9) / args.inner)))
+    p = pos[:, :n].copy()
+    for _ in range(args.warmup):
+        p = oracle.advance(f64, p, DT, args.inner, oracle.SPLINE, I, M)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p = oracle.advance(f64, p, DT, args.inner, oracle.SPLINE, I, M)
+    el = time.perf_counter() - t0
+    value = n * args.inner * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_particles": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{n} tracers x {args.inner} RK2 steps per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GB300 arm
+# --------------------------------------------------------------------------
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import paper_2107_01104_gb300 as trk
+    from paper_2107_01104_gb300 import build as lib_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        lib_build.build()
+    if ws > 1:
+        dist.barrier()
+    trk.load_library()
+
+    field, pos = field_and_particles()
+    tr = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
+    tr.set_field(torch.from_numpy(field).to(dev))
+    p = torch.from_numpy(pos).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    notes = {"cfl_slow_path_used": False}
+    for _ in range(args.warmup):
+        tr.advance(p, DT, args.inner, trk.TRK_RK2)
+    sync_flags(tr, trk, notes)
+
+    # ---------------- device-timed region ----------------
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier_sync()
+    clocks.start()
+    time.sleep(0.2)
+    launches0 = tr.launch_count
+    trk.tracker_profile(tr.h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tr.advance(p, DT, args.inner, trk.TRK_RK2)
+    e1.record(stream)
+    barrier_sync()
+    clk = clocks.stop()
+    prof = trk.tracker_profile_read(tr.h)
+    trk.tracker_profile(tr.h, False)
+    launches = tr.launch_count - launches0
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sync_flags(tr, trk, notes)
+    total_ps = NP * args.inner * args.steps * ws
+    value = total_ps / (ms * 1e-3)
+
+    # ---------------- roofline of the step kernel ----------------
+    step_ms, step_n = prof["step"]
+    avg_launch_s = step_ms * 1e-3 / max(step_n, 1)
+    field_bytes = 3 * N ** 3 * 4
+    alg_bytes = field_bytes + 48 * NP                 # field once + fp64 positions read and written
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    sha = kernel_source_sha()
+    gather_bytes = NP * 2 * I ** 3 * 3 * 4            # two stencil gathers per RK2 step, float32
+    sm_mhz = clk.get("sm_mhz") or 1900.0
+    smem_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * sm_mhz * 1e6 / 1e9
+
+    # ---------------- end-to-end through the public API ----------------
+    host = torch.from_numpy(pos).pin_memory()
+    back = torch.empty_like(host).pin_memory()
+    barrier_sync()
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    for _ in range(args.steps):
+        p.copy_(host, non_blocking=True)
+        tr.advance(p, DT, args.inner, trk.TRK_RK2)
+        back.copy_(p, non_blocking=True)
+    w1.record(stream)
+    barrier_sync()
+    e2e_ms = w0.elapsed_time(w1)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": total_ps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": host.numel() * 8,
+           "d2h_bytes_per_step": back.numel() * 8}
+
+    # ---------------- other precision forms of the same workload ----------------
+    variants = {}
+    if not args.no_variants:
+        for name, storage, inner in (("f64", trk.TRK_F64, 5), ("bf16x2", trk.TRK_BF16X2, args.inner)):
+            tv = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=M, storage=storage)
+            tv.set_field(torch.from_numpy(field).to(dev))
+            pv = torch.from_numpy(pos).to(dev)
+            tv.advance(pv, DT, 1, trk.TRK_RK2)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            reps = 2
+            for _ in range(reps):
+                tv.advance(pv, DT, inner, trk.TRK_RK2)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vms = v0.elapsed_time(v1)
+            variants[name] = {"value": NP * inner * reps / (vms * 1e-3), "unit": UNIT, "rk2_steps": inner * reps}
+            tv.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(field, pos, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "np": NP, "kernel": f"spline I={I} m={M}", "scheme": "RK2",
+                       "dt": DT, "rk2_steps_per_bench_step": args.inner, "field_storage": "f32",
+                       "positions": "f64", "l2": "inputs larger than L2 (201 MB field vs 129 MB L2)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": ncu_traffic(sha), "kernel": "k_block<float,6,5,RK2,F32>",
+                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                         "launches_timed": step_n, "peak_kind": peak_kind, "source_sha": sha},
+            "smem_roofline": {"achieved": gather_bytes / avg_launch_s / 1e9, "peak": smem_peak, "unit": "GB/s",
+                              "frac": gather_bytes / avg_launch_s / 1e9 / smem_peak,
+                              "gather_bytes_per_launch": gather_bytes,
+                              "peak_def": "SMs x 128 B/clk x median SM clock under load"},
+            "phase_ms_per_step": {"step_kernel": step_ms / args.steps, "binning": prof["bin"][0] / args.steps,
+                                  "other": prof["other"][0] / args.steps},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "variants": variants, "notes": notes,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    tr.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

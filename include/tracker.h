@@ -213,6 +213,19 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
  * (graph replays count each kernel node).  For instrumentation. */
 int64_t tracker_launch_count(const tracker* t);
 
+/* Instrumentation.  tracker_profile(t, 1) clears and starts recording CUDA
+ * events on the tracker's stream around each kernel class; 0 stops.  While
+ * recording, tracker_advance launches its kernels directly instead of
+ * replaying a CUDA graph.  tracker_profile_read waits for the stream and
+ * returns the accumulated device time in milliseconds and the number of
+ * timed launches per class:
+ *   [0] interpolation / step kernels (the per-block gather-contract-update),
+ *   [1] binning (block keys, radix-sort passes, offsets),
+ *   [2] everything else (field conversion, scatter back to caller order).
+ * ms and launches each point to 3 host values. */
+int tracker_profile(tracker* t, int enable);
+int tracker_profile_read(tracker* t, double* ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,7 @@ ABI_FUNCTIONS = (
     "tracker_create", "tracker_destroy", "tracker_last_error", "tracker_set_stream", "tracker_sync",
     "tracker_set_field", "tracker_set_block", "tracker_num_blocks", "tracker_bin", "tracker_interpolate",
     "tracker_advance", "tracker_advance_batched", "tracker_adjoint", "tracker_launch_count",
+    "tracker_profile", "tracker_profile_read",
 )
 
 
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH):
             "tracker_advance_batched": (c_int, [vp, c_int, vp, c_d, c_int, c_int]),
             "tracker_adjoint": (c_int, [vp, c_i64, vp, vp, c_d, c_int, c_int, vp, vp]),
             "tracker_launch_count": (c_i64, [vp]),
+            "tracker_profile": (c_int, [vp, c_int]),
+            "tracker_profile_read": (c_int, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -173,6 +176,18 @@ def tracker_num_blocks(h) -> int:
 
 def tracker_launch_count(h) -> int:
     return int(load_library().tracker_launch_count(h))
+
+
+def tracker_profile(h, enable: bool):
+    _check(load_library().tracker_profile(h, int(bool(enable))))
+
+
+def tracker_profile_read(h):
+    """{'step': (ms, launches), 'bin': (...), 'other': (...)} of device time since tracker_profile(h, True)."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 3)()
+    _check(load_library().tracker_profile_read(h, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p)))
+    return {"step": (ms[0], n[0]), "bin": (ms[1], n[1]), "other": (ms[2], n[2])}
 
 
 def tracker_bin(h, pos, keys=None, perm=None, offsets=None):

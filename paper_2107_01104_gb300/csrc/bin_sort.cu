@@ -220,11 +220,21 @@ __global__ void k_unpermute_rhs(int64_t np, const float* __restrict__ src, const
     for (int a = 0; a < 3; ++a) dst[a * np + p] = src[a * np + j];
 }
 
+// Fills the ghost-padded storage: padded node (x1, x2, x3) in [-PAD, N+PAD)^3
+// takes the value of node (x mod N) of the dense source (periodic ghosts).
 template <typename S>
-__global__ void k_convert(int storage, const S* __restrict__ src, int64_t n, void* __restrict__ dst)
+__global__ void k_convert_padded(int storage, const S* __restrict__ src, int C, int N, void* __restrict__ dst)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const S x = src[i];
+    const int NP = N + 2 * PAD;
+    const int64_t plane = (int64_t)NP * NP * NP;
+    const int64_t total = plane * C;
+    const int mask = N - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / plane, r = i - k * plane;
+        const int x3 = (int)(r / ((int64_t)NP * NP)), r2 = (int)(r - (int64_t)x3 * NP * NP);
+        const int x2 = r2 / NP, x1 = r2 - x2 * NP;
+        const int64_t si = (((int64_t)k * N + ((x3 - PAD) & mask)) * N + ((x2 - PAD) & mask)) * N + ((x1 - PAD) & mask);
+        const S x = src[si];
         if (storage == ST_F64) {
             reinterpret_cast<double*>(dst)[i] = (double)x;
         } else if (storage == ST_F32) {
@@ -235,7 +245,7 @@ __global__ void k_convert(int storage, const S* __restrict__ src, int64_t n, voi
             const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
             const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
             reinterpret_cast<__nv_bfloat16*>(dst)[i] = hi;
-            reinterpret_cast<__nv_bfloat16*>(dst)[n + i] = lo;
+            reinterpret_cast<__nv_bfloat16*>(dst)[total + i] = lo;
         }
     }
 }
@@ -320,11 +330,13 @@ cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int64_t n, void* dst, cudaStream_t st)
+cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int C, int N, void* dst, cudaStream_t st)
 {
+    const int64_t NP = N + 2 * PAD;
+    const int64_t n = NP * NP * NP * C;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 64);
-    if (src_f64) k_convert<double><<<grid, 256, 0, st>>>(storage, reinterpret_cast<const double*>(src), n, dst);
-    else k_convert<float><<<grid, 256, 0, st>>>(storage, reinterpret_cast<const float*>(src), n, dst);
+    if (src_f64) k_convert_padded<double><<<grid, 256, 0, st>>>(storage, reinterpret_cast<const double*>(src), C, N, dst);
+    else k_convert_padded<float><<<grid, 256, 0, st>>>(storage, reinterpret_cast<const float*>(src), C, N, dst);
     return cudaGetLastError();
 }
 

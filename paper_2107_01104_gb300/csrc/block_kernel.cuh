@@ -1,22 +1,24 @@
 // Block kernels: one CTA per cell block of BLK^3 cells (the block grouping of
 // Sec. 3.3.1, with the paper's x3 slices generalised to cubes).
 //
-// A CTA stages the block's field halo in shared memory once and then runs
-// the per-particle work in phases separated by __syncthreads():
+// A CTA stages the block's field halo in shared memory once (16-byte vector
+// loads from the ghost-padded field) and then runs the per-particle work in
+// phases separated by __syncthreads():
 //
 //   P1  one thread per particle: read X through the sort permutation, split it
 //       into cell c and offset t (float64, Sec. 2.2 steps 1-3);
-//   Q1  one warp per particle: evaluate the 1-D weights beta_i once per axis,
-//       gather the I x I x I stencil from shared memory and contract it
-//       (Eq. triple_sum, separably as in Sec. 3.3), reduce across the warp;
-//   P2  (RK2) one thread per particle: stage-2 point X* = X + dt k1;
-//   Q2  (RK2) warp per particle at X*;
-//   P3  one thread per particle: float64 update of X (RK2 or AB2), new cell
+//   Q   one warp per particle: evaluate the 1-D weights beta_i per axis, gather
+//       the I x I x I stencil from shared memory into registers and contract it
+//       (Eq. triple_sum, separably as in Sec. 3.3), reduce across the warp.
+//       For RK2 the warp then forms the stage-2 point in cell-relative
+//       coordinates, t* = t + dt u(X) / delta, and contracts again, re-using
+//       the stencil registers when X* lies in the same cell;
+//   P3  one thread per particle: float64 position update (RK2 or AB2), new cell
 //       split and block key for the next re-binning, coalesced write-out.
 //
-// Warp-per-particle lane maps (chosen so that every warp-wide shared load
-// hits 32 distinct banks, see Layout):
-//   I = 8: lane = (i1 in 0..7, j in 0..3); i2 = j and j+4; loop i3 in 0..7
+// Warp-per-particle lane maps (every warp-wide shared load hits 32 distinct
+// banks, see Layout):
+//   I = 8: lane = (i1 in 0..7, j in 0..3); i2 = j and j+4; i3 = 0..7
 //   I = 6: lane = (i1 in 0..5, j in 0..4); pass A i2 = j, i3 = 0..5;
 //          pass B i2 = 5, i3 = j; pass C (lanes 0..5) i2 = i3 = 5
 //   I = 4: lane = (i1, i2 in 0..3, p in 0..1); i3 = p and p+2
@@ -30,22 +32,10 @@ constexpr int NT = 256;           // threads per CTA
 constexpr int NW = NT / 32;       // warps per CTA
 constexpr int PB = NT;            // particles per batch (one per thread in the P phases)
 
-static __constant__ double c_coef_d[TRK_NUM_TABLES][TRK_TAB_MAX_I][TRK_TAB_MAX_DEG] = TRK_COEF_INIT;
-static __constant__ float c_coef_f[TRK_NUM_TABLES][TRK_TAB_MAX_I][TRK_TAB_MAX_DEG] = TRK_COEF_INIT;
-static __constant__ double c_dcoef_d[TRK_NUM_TABLES][TRK_TAB_MAX_I][TRK_TAB_MAX_DEG] = TRK_DCOEF_INIT;
-static __constant__ float c_dcoef_f[TRK_NUM_TABLES][TRK_TAB_MAX_I][TRK_TAB_MAX_DEG] = TRK_DCOEF_INIT;
-
-template <typename T> __device__ __forceinline__ T coef(int tab, int i, int d);
-template <> __device__ __forceinline__ float coef<float>(int tab, int i, int d) { return c_coef_f[tab][i][d]; }
-template <> __device__ __forceinline__ double coef<double>(int tab, int i, int d) { return c_coef_d[tab][i][d]; }
-template <typename T> __device__ __forceinline__ T dcoef(int tab, int i, int d);
-template <> __device__ __forceinline__ float dcoef<float>(int tab, int i, int d) { return c_dcoef_f[tab][i][d]; }
-template <> __device__ __forceinline__ double dcoef<double>(int tab, int i, int d) { return c_dcoef_d[tab][i][d]; }
-
 // ---------------------------------------------------------------------------
 // Shared-memory layout of the halo: [3 components][H][H][S2], row stride S2,
-// plane stride S3, component stride SC.  S2 and S3 are the smallest strides
-// for which the lane map of kernel width I reads 32 distinct banks.
+// plane stride S3, component stride SC.  S2, S3: the smallest strides for
+// which the lane map of kernel width I reads 32 distinct banks.
 // ---------------------------------------------------------------------------
 constexpr bool distinct_banks(const int* offs, int n)
 {
@@ -89,7 +79,6 @@ constexpr bool plane_ok(int S2, int S3)
     }
 }
 
-// Joint search: smallest row stride S2 >= H that admits a plane stride S3.
 template <int I>
 constexpr int find_s3(int H, int S2)
 {
@@ -115,20 +104,23 @@ struct Layout {
 };
 
 // ---------------------------------------------------------------------------
-// Horner evaluation of beta_i(s) (s = t - 1/2) from a register row or from
-// the constant table.
+// Weight polynomials
 // ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ const CoefTable<T>& table(const BlockArgs& a);
+template <> __device__ __forceinline__ const CoefTable<float>& table<float>(const BlockArgs& a) { return a.cf; }
+template <> __device__ __forceinline__ const CoefTable<double>& table<double>(const BlockArgs& a) { return a.cd; }
+
 template <typename T, int DEG>
 struct Row {
     T c[DEG + 1];
 };
 
 template <typename T, int DEG>
-__device__ __forceinline__ Row<T, DEG> load_row(int tab, int i, bool deriv)
+__device__ __forceinline__ Row<T, DEG> load_row(const T (&tab)[TRK_TAB_MAX_I][TRK_TAB_MAX_DEG], int i)
 {
     Row<T, DEG> r;
 #pragma unroll
-    for (int d = 0; d <= DEG; ++d) r.c[d] = deriv ? dcoef<T>(tab, i, d) : coef<T>(tab, i, d);
+    for (int d = 0; d <= DEG; ++d) r.c[d] = tab[i][d];
     return r;
 }
 
@@ -141,257 +133,22 @@ __device__ __forceinline__ T horner(const Row<T, DEG>& r, T s)
     return acc;
 }
 
+// compile-time row of a table held in the (grid-constant) kernel parameters
 template <typename T, int DEG>
-__device__ __forceinline__ T horner_tab(int tab, int i, T s)
+__device__ __forceinline__ T horner_c(const T (&row)[TRK_TAB_MAX_DEG], T s)
 {
-    T acc = coef<T>(tab, i, DEG);
+    T acc = row[DEG];
 #pragma unroll
-    for (int d = DEG - 1; d >= 0; --d) acc = fma(acc, s, coef<T>(tab, i, d));
+    for (int d = DEG - 1; d >= 0; --d) acc = fma(acc, s, row[d]);
     return acc;
 }
 
-template <typename T, int DEG>
-__device__ __forceinline__ T dhorner_tab(int tab, int i, T s)
-{
-    // derivative polynomial has degree DEG - 1
-    T acc = dcoef<T>(tab, i, DEG - 1);
-#pragma unroll
-    for (int d = DEG - 2; d >= 0; --d) acc = fma(acc, s, dcoef<T>(tab, i, d));
-    return acc;
-}
-
-// Per-lane coefficient rows (lane-dependent node indices), loaded once per CTA.
-template <typename T, int I, int DEG, bool D>
-struct LaneRows;
-
-template <typename T, int DEG, bool D>
-struct LaneRows<T, 8, DEG, D> {
-    Row<T, DEG> a, b, c;        // rows i1, j, j+4
-    Row<T, DEG> da, db, dc;     // derivative rows (used when D)
-    __device__ void load(int tab, int lane)
-    {
-        const int i1 = lane & 7, j = lane >> 3;
-        a = load_row<T, DEG>(tab, i1, false);
-        b = load_row<T, DEG>(tab, j, false);
-        c = load_row<T, DEG>(tab, j + 4, false);
-        if (D) {
-            da = load_row<T, DEG>(tab, i1, true);
-            db = load_row<T, DEG>(tab, j, true);
-            dc = load_row<T, DEG>(tab, j + 4, true);
-        }
-    }
-};
-
-template <typename T, int DEG, bool D>
-struct LaneRows<T, 6, DEG, D> {
-    Row<T, DEG> a, b;           // rows i1, j
-    Row<T, DEG> da, db;
-    __device__ void load(int tab, int lane)
-    {
-        const int i1 = lane % 6, j = min(lane / 6, 5);
-        a = load_row<T, DEG>(tab, i1, false);
-        b = load_row<T, DEG>(tab, j, false);
-        if (D) {
-            da = load_row<T, DEG>(tab, i1, true);
-            db = load_row<T, DEG>(tab, j, true);
-        }
-    }
-};
-
-template <typename T, int DEG, bool D>
-struct LaneRows<T, 4, DEG, D> {
-    Row<T, DEG> a, b, c, e;     // rows i1, i2, p, p+2
-    Row<T, DEG> da, db, dc, de;
-    __device__ void load(int tab, int lane)
-    {
-        const int i1 = lane & 3, i2 = (lane >> 2) & 3, p = lane >> 4;
-        a = load_row<T, DEG>(tab, i1, false);
-        b = load_row<T, DEG>(tab, i2, false);
-        c = load_row<T, DEG>(tab, p, false);
-        e = load_row<T, DEG>(tab, p + 2, false);
-        if (D) {
-            da = load_row<T, DEG>(tab, i1, true);
-            db = load_row<T, DEG>(tab, i2, true);
-            dc = load_row<T, DEG>(tab, p, true);
-            de = load_row<T, DEG>(tab, p + 2, true);
-        }
-    }
-};
-
 // ---------------------------------------------------------------------------
-// Warp-level stencil gather + contraction for one particle.
-// ld(k, a1, a2, a3) returns component k of node (c + a - (I/2 - 1)).
-// On return (before the warp reduction) every lane holds a partial sum:
-//   acc[k]            value      u_k
-//   acc[3 + 3k + j]   derivative d u_k / d t_j  (when D)
-// ---------------------------------------------------------------------------
-template <typename T, int DEG, bool D, class LD>
-__device__ __forceinline__ void gather_i8(const LD& ld, int lane, int tab, const LaneRows<T, 8, DEG, D>& R,
-                                          T s1, T s2, T s3, T (&acc)[12])
-{
-    const int i1 = lane & 7, j = lane >> 3;
-    const T w1 = horner(R.a, s1);
-    const T w2[2] = {horner(R.b, s2), horner(R.c, s2)};
-    T w3[8], dw3[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        w3[i] = horner_tab<T, DEG>(tab, i, s3);
-        if (D) dw3[i] = dhorner_tab<T, DEG>(tab, i, s3);
-    }
-    T dw1 = 0, dw2[2] = {0, 0};
-    if (D) {
-        dw1 = horner(R.da, s1);
-        dw2[0] = horner(R.db, s2);
-        dw2[1] = horner(R.dc, s2);
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        T pv[3] = {0, 0, 0}, pd[3] = {0, 0, 0};
-#pragma unroll
-        for (int i3 = 0; i3 < 8; ++i3) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const T f = ld(k, i1, j + 4 * h, i3);
-                pv[k] = fma(w3[i3], f, pv[k]);
-                if (D) pd[k] = fma(dw3[i3], f, pd[k]);
-            }
-        }
-        const T a12 = w1 * w2[h];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            acc[k] = fma(a12, pv[k], acc[k]);
-            if (D) {
-                acc[3 + 3 * k + 0] = fma(dw1 * w2[h], pv[k], acc[3 + 3 * k + 0]);
-                acc[3 + 3 * k + 1] = fma(w1 * dw2[h], pv[k], acc[3 + 3 * k + 1]);
-                acc[3 + 3 * k + 2] = fma(a12, pd[k], acc[3 + 3 * k + 2]);
-            }
-        }
-    }
-}
-
-template <typename T, int DEG, bool D, class LD>
-__device__ __forceinline__ void gather_i6(const LD& ld, int lane, int tab, const LaneRows<T, 6, DEG, D>& R,
-                                          T s1, T s2, T s3, T (&acc)[12])
-{
-    const int i1 = lane % 6, j = min(lane / 6, 5);
-    const bool act = lane < 30;
-    const T w1 = horner(R.a, s1), w2j = horner(R.b, s2), w3j = horner(R.b, s3);
-    const T w25 = horner_tab<T, DEG>(tab, 5, s2);
-    T w3[6], dw3[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        w3[i] = horner_tab<T, DEG>(tab, i, s3);
-        if (D) dw3[i] = dhorner_tab<T, DEG>(tab, i, s3);
-    }
-    T dw1 = 0, dw2j = 0, dw3j = 0, dw25 = 0;
-    if (D) {
-        dw1 = horner(R.da, s1);
-        dw2j = horner(R.db, s2);
-        dw3j = horner(R.db, s3);
-        dw25 = dhorner_tab<T, DEG>(tab, 5, s2);
-    }
-    if (act) {
-        // pass A: i2 = j, i3 = 0..5
-        T pv[3] = {0, 0, 0}, pd[3] = {0, 0, 0};
-#pragma unroll
-        for (int i3 = 0; i3 < 6; ++i3) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const T f = ld(k, i1, j, i3);
-                pv[k] = fma(w3[i3], f, pv[k]);
-                if (D) pd[k] = fma(dw3[i3], f, pd[k]);
-            }
-        }
-        const T a12 = w1 * w2j;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            acc[k] = fma(a12, pv[k], acc[k]);
-            if (D) {
-                acc[3 + 3 * k + 0] = fma(dw1 * w2j, pv[k], acc[3 + 3 * k + 0]);
-                acc[3 + 3 * k + 1] = fma(w1 * dw2j, pv[k], acc[3 + 3 * k + 1]);
-                acc[3 + 3 * k + 2] = fma(a12, pd[k], acc[3 + 3 * k + 2]);
-            }
-        }
-        // pass B: i2 = 5, i3 = j
-        const T wb = w1 * w25 * w3j;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const T f = ld(k, i1, 5, j);
-            acc[k] = fma(wb, f, acc[k]);
-            if (D) {
-                acc[3 + 3 * k + 0] = fma(dw1 * w25 * w3j, f, acc[3 + 3 * k + 0]);
-                acc[3 + 3 * k + 1] = fma(w1 * dw25 * w3j, f, acc[3 + 3 * k + 1]);
-                acc[3 + 3 * k + 2] = fma(w1 * w25 * dw3j, f, acc[3 + 3 * k + 2]);
-            }
-        }
-    }
-    if (lane < 6) {
-        // pass C: i2 = i3 = 5
-        const T wc = w1 * w25 * w3[5];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const T f = ld(k, i1, 5, 5);
-            acc[k] = fma(wc, f, acc[k]);
-            if (D) {
-                acc[3 + 3 * k + 0] = fma(dw1 * w25 * w3[5], f, acc[3 + 3 * k + 0]);
-                acc[3 + 3 * k + 1] = fma(w1 * dw25 * w3[5], f, acc[3 + 3 * k + 1]);
-                acc[3 + 3 * k + 2] = fma(w1 * w25 * dw3[5], f, acc[3 + 3 * k + 2]);
-            }
-        }
-    }
-}
-
-template <typename T, int DEG, bool D, class LD>
-__device__ __forceinline__ void gather_i4(const LD& ld, int lane, int tab, const LaneRows<T, 4, DEG, D>& R,
-                                          T s1, T s2, T s3, T (&acc)[12])
-{
-    const int i1 = lane & 3, i2 = (lane >> 2) & 3, p = lane >> 4;
-    const T w1 = horner(R.a, s1), w2 = horner(R.b, s2);
-    const T w3a = horner(R.c, s3), w3b = horner(R.e, s3);
-    T dw1 = 0, dw2 = 0, dw3a = 0, dw3b = 0;
-    if (D) {
-        dw1 = horner(R.da, s1);
-        dw2 = horner(R.db, s2);
-        dw3a = horner(R.dc, s3);
-        dw3b = horner(R.de, s3);
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const T f0 = ld(k, i1, i2, p), f1 = ld(k, i1, i2, p + 2);
-        const T pv = fma(w3a, f0, w3b * f1);
-        acc[k] = fma(w1 * w2, pv, acc[k]);
-        if (D) {
-            const T pd = fma(dw3a, f0, dw3b * f1);
-            acc[3 + 3 * k + 0] = fma(dw1 * w2, pv, acc[3 + 3 * k + 0]);
-            acc[3 + 3 * k + 1] = fma(w1 * dw2, pv, acc[3 + 3 * k + 1]);
-            acc[3 + 3 * k + 2] = fma(w1 * w2, pd, acc[3 + 3 * k + 2]);
-        }
-    }
-}
-
-template <typename T, int I, int DEG, bool D, class LD>
-__device__ __forceinline__ void gather(const LD& ld, int lane, int tab, const LaneRows<T, I, DEG, D>& R, T s1, T s2,
-                                       T s3, T (&acc)[12])
-{
-#pragma unroll
-    for (int r = 0; r < 12; ++r) acc[r] = 0;
-    if constexpr (I == 8) gather_i8<T, DEG, D>(ld, lane, tab, R, s1, s2, s3, acc);
-    else if constexpr (I == 6) gather_i6<T, DEG, D>(ld, lane, tab, R, s1, s2, s3, acc);
-    else gather_i4<T, DEG, D>(ld, lane, tab, R, s1, s2, s3, acc);
-    constexpr int NV = D ? 12 : 3;
-#pragma unroll
-    for (int r = 0; r < NV; ++r) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Loaders
+// Loaders: ld(k, a1, a2, a3) = component k of node c + a - (I/2 - 1)
 // ---------------------------------------------------------------------------
 template <typename T, int S2, int S3, int SC>
 struct SmemLd {
-    const T* base;   // node (c - (I/2 - 1)) of component 0
+    const T* base;
     __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
     {
         return base[k * SC + a3 * S3 + a2 * S2 + a1];
@@ -407,33 +164,352 @@ __device__ __forceinline__ T fetch(const FieldView& f, int k, int64_t idx)
     else return (T)(__bfloat162float(f.hi[o]) + __bfloat162float(f.lo[o]));
 }
 
-// Global-memory loader with periodic wrap (for stencils outside the staged halo).
+// Global-memory loader with periodic wrap (stencils outside the staged halo).
 template <typename T, int STORE, int I>
 struct GlobalLd {
     FieldView f;
-    int c1, c2, c3, k0, kmax, N, mask;
+    int c1, c2, c3, k0, kmax, mask;
     __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
     {
         const int x1 = (c1 + a1 - (I / 2 - 1)) & mask;
         const int x2 = (c2 + a2 - (I / 2 - 1)) & mask;
         const int x3 = (c3 + a3 - (I / 2 - 1)) & mask;
-        const int kk = min(k0 + k, kmax);
-        return fetch<T, STORE>(f, kk, ((int64_t)x3 * N + x2) * N + x1);
+        return fetch<T, STORE>(f, min(k0 + k, kmax), padded_index(f.NP, x1, x2, x3));
     }
 };
 
-template <typename T, int STORE, int H, int S2, int S3, int SC>
-__device__ __forceinline__ void load_halo(T* halo, const FieldView& f, int k0, int ox, int oy, int oz, int N,
-                                          int mask)
+// ---------------------------------------------------------------------------
+// 1-D weights, once per particle and axis: lane l < 3I evaluates
+// beta_i(s_a) (a = l / I, i = l % I) by Horner's rule and stores it in the
+// warp's weight buffer wv[3][8] (and beta' in wd[3][8] when D); the lanes then
+// read the weights they need.
+// ---------------------------------------------------------------------------
+template <typename T, int I, int DEG, bool D>
+struct WeightEval {
+    Row<T, DEG> r, dr;
+    int ax, i;
+    bool act;
+    __device__ void init(const CoefTable<T>& tb, int lane)
+    {
+        act = lane < 3 * I;
+        ax = act ? lane / I : 0;
+        i = act ? lane % I : 0;
+        r = load_row<T, DEG>(tb.c, i);
+        if (D) dr = load_row<T, DEG>(tb.d, i);
+    }
+    __device__ __forceinline__ void eval(T s1, T s2, T s3, T* wv, T* wd) const
+    {
+        __syncwarp();                        // previous readers of the buffer are done
+        if (act) {
+            const T s = ax == 0 ? s1 : (ax == 1 ? s2 : s3);
+            wv[ax * 8 + i] = horner(r, s);
+            if (D) wd[ax * 8 + i] = horner(dr, s);
+        }
+        __syncwarp();
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Per-lane stencil registers and contraction, one specialisation per I.
+//   acc[k] = u_k partial; with D also acc[3 + 3k + j] = d u_k / d t_j partial.
+// Idle lanes read a duplicate of an active lane's address (a broadcast, not a
+// bank conflict) and carry zero weights.
+// ---------------------------------------------------------------------------
+template <typename T, int I, bool D>
+struct Lane;
+
+template <typename T, bool D>
+struct Lane<T, 8, D> {
+    int i1, j;
+    T f[3][2][8];
+    __device__ void init(int lane)
+    {
+        i1 = lane & 7;
+        j = lane >> 3;
+    }
+    template <class LD>
+    __device__ __forceinline__ void load(const LD& ld)
+    {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i3 = 0; i3 < 8; ++i3) f[k][h][i3] = ld(k, i1, j + 4 * h, i3);
+    }
+    __device__ __forceinline__ void contract(const T* wv, const T* wd, T (&acc)[12]) const
+    {
+        T w3[8], dw3[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            w3[i] = wv[16 + i];
+            if (D) dw3[i] = wd[16 + i];
+        }
+        const T w1 = wv[i1];
+        const T w2[2] = {wv[8 + j], wv[12 + j]};
+        T dw1 = 0, dw2[2] = {0, 0};
+        if (D) {
+            dw1 = wd[i1];
+            dw2[0] = wd[8 + j];
+            dw2[1] = wd[12 + j];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T v = 0, d1 = 0, d2 = 0, d3 = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                T pv = 0, pd = 0;
+#pragma unroll
+                for (int i3 = 0; i3 < 8; ++i3) {
+                    pv = fma(w3[i3], f[k][h][i3], pv);
+                    if (D) pd = fma(dw3[i3], f[k][h][i3], pd);
+                }
+                v = fma(w1 * w2[h], pv, v);
+                if (D) {
+                    d1 = fma(dw1 * w2[h], pv, d1);
+                    d2 = fma(w1 * dw2[h], pv, d2);
+                    d3 = fma(w1 * w2[h], pd, d3);
+                }
+            }
+            acc[k] = v;
+            if (D) {
+                acc[3 + 3 * k + 0] = d1;
+                acc[3 + 3 * k + 1] = d2;
+                acc[3 + 3 * k + 2] = d3;
+            }
+        }
+    }
+};
+
+template <typename T, bool D>
+struct Lane<T, 6, D> {
+    int i1, j;
+    bool act, actc;
+    T f[3][8];                               // pass A (6), pass B, pass C
+    __device__ void init(int lane)
+    {
+        act = lane < 30;
+        actc = lane < 6;
+        i1 = lane % 6;                       // lanes 30, 31 duplicate lanes 0, 1
+        j = act ? lane / 6 : 0;
+    }
+    template <class LD>
+    __device__ __forceinline__ void load(const LD& ld)
+    {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int i3 = 0; i3 < 6; ++i3) f[k][i3] = ld(k, i1, j, i3);
+            f[k][6] = ld(k, i1, 5, j);
+            f[k][7] = ld(k, i1, 5, 5);
+        }
+    }
+    __device__ __forceinline__ void contract(const T* wv, const T* wd, T (&acc)[12]) const
+    {
+        T w3[6], dw3[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            w3[i] = wv[16 + i];
+            if (D) dw3[i] = wd[16 + i];
+        }
+        const T w1 = wv[i1], w2j = wv[8 + j], w3j = wv[16 + j], w25 = wv[13];
+        const T z = 0;
+        // coefficients of the three passes (zero on idle lanes)
+        const T aA = act ? w1 * w2j : z;
+        const T aB = act ? w1 * w25 * w3j : z;
+        const T aC = actc ? w1 * w25 * w3[5] : z;
+        T dw1 = 0, dw2j = 0, dw3j = 0, dw25 = 0;
+        if (D) {
+            dw1 = wd[i1];
+            dw2j = wd[8 + j];
+            dw3j = wd[16 + j];
+            dw25 = wd[13];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T pv = 0, pd = 0;
+#pragma unroll
+            for (int i3 = 0; i3 < 6; ++i3) {
+                pv = fma(w3[i3], f[k][i3], pv);
+                if (D) pd = fma(dw3[i3], f[k][i3], pd);
+            }
+            acc[k] = fma(aA, pv, fma(aB, f[k][6], aC * f[k][7]));
+            if (D) {
+                const T b1 = act ? dw1 * w2j : z, b2 = act ? w1 * dw2j : z;
+                const T c1 = act ? dw1 * w25 * w3j : z, c2 = act ? w1 * dw25 * w3j : z, c3 = act ? w1 * w25 * dw3j : z;
+                const T e1 = actc ? dw1 * w25 * w3[5] : z, e2 = actc ? w1 * dw25 * w3[5] : z;
+                const T e3 = actc ? w1 * w25 * dw3[5] : z;
+                acc[3 + 3 * k + 0] = fma(b1, pv, fma(c1, f[k][6], e1 * f[k][7]));
+                acc[3 + 3 * k + 1] = fma(b2, pv, fma(c2, f[k][6], e2 * f[k][7]));
+                acc[3 + 3 * k + 2] = fma(aA, pd, fma(c3, f[k][6], e3 * f[k][7]));
+            }
+        }
+    }
+};
+
+template <typename T, bool D>
+struct Lane<T, 4, D> {
+    int i1, i2, p;
+    T f[3][2];
+    __device__ void init(int lane)
+    {
+        i1 = lane & 3;
+        i2 = (lane >> 2) & 3;
+        p = lane >> 4;
+    }
+    template <class LD>
+    __device__ __forceinline__ void load(const LD& ld)
+    {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            f[k][0] = ld(k, i1, i2, p);
+            f[k][1] = ld(k, i1, i2, p + 2);
+        }
+    }
+    __device__ __forceinline__ void contract(const T* wv, const T* wd, T (&acc)[12]) const
+    {
+        const T w1 = wv[i1], w2 = wv[8 + i2];
+        const T w3a = wv[16 + p], w3b = wv[18 + p];
+        T dw1 = 0, dw2 = 0, dw3a = 0, dw3b = 0;
+        if (D) {
+            dw1 = wd[i1];
+            dw2 = wd[8 + i2];
+            dw3a = wd[16 + p];
+            dw3b = wd[18 + p];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T pv = fma(w3a, f[k][0], w3b * f[k][1]);
+            acc[k] = w1 * w2 * pv;
+            if (D) {
+                const T pd = fma(dw3a, f[k][0], dw3b * f[k][1]);
+                acc[3 + 3 * k + 0] = dw1 * w2 * pv;
+                acc[3 + 3 * k + 1] = w1 * dw2 * pv;
+                acc[3 + 3 * k + 2] = w1 * w2 * pd;
+            }
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Warp reductions.  reduce4: three values (padded to four) summed over the 32
+// lanes in 6 shuffles; lane l ends with value 2*bit4(l) + bit3(l).
+// reduce16: twelve values (padded to 16) in 16 shuffles; lane l ends with
+// value 8*bit4 + 4*bit3 + 2*bit2 + bit1.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T xor_shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+
+template <typename T>
+__device__ __forceinline__ T reduce4(const T (&acc)[12], int lane)
 {
-    constexpr int NPC = H * H * H;
-    for (int k = 0; k < 3; ++k) {
-        const int kk = k0 + k;
-        if (kk >= f.C) break;
-        for (int e = threadIdx.x; e < NPC; e += NT) {
-            const int x = e % H, yz = e / H, y = yz % H, z = yz / H;
-            const int64_t gi = ((int64_t)((oz + z) & mask) * N + ((oy + y) & mask)) * N + ((ox + x) & mask);
-            halo[k * SC + z * S3 + y * S2 + x] = fetch<T, STORE>(f, kk, gi);
+    const bool b4 = lane & 16, b3 = lane & 8;
+    const T z = 0;
+    // level 16: keep values (0,1) or (2,3)
+    T k0 = b4 ? acc[2] : acc[0];
+    T k1 = b4 ? z : acc[1];
+    k0 += xor_shfl(b4 ? acc[0] : acc[2], 16);
+    k1 += xor_shfl(b4 ? acc[1] : z, 16);
+    // level 8: keep one value, then a full reduction of it
+    T m = b3 ? k1 : k0;
+    m += xor_shfl(b3 ? k0 : k1, 8);
+    m += xor_shfl(m, 4);
+    m += xor_shfl(m, 2);
+    m += xor_shfl(m, 1);
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T reduce16(const T (&acc)[12], int lane)
+{
+    T v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = i < 12 ? acc[i] : (T)0;
+#pragma unroll
+    for (int lev = 0; lev < 4; ++lev) {
+        const int off = 16 >> lev;
+        const int half = 8 >> lev;
+        const bool hi = lane & off;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const T send = hi ? v[i] : v[i + half];
+            const T keep = hi ? v[i + half] : v[i];
+            v[i] = keep + xor_shfl(send, off);
+        }
+    }
+    v[0] += xor_shfl(v[0], 1);
+    return v[0];
+}
+
+// ---------------------------------------------------------------------------
+// Halo staging: 16-byte vector loads of the ghost-padded field rows.
+// ---------------------------------------------------------------------------
+template <int STORE>
+struct VecOf {
+    static constexpr int n = STORE == ST_F64 ? 2 : (STORE == ST_F32 ? 4 : 8);
+};
+
+template <typename T, int STORE, int VEC>
+__device__ __forceinline__ void load_vec(const FieldView& f, int64_t g, T (&vals)[VEC])
+{
+    if constexpr (STORE == ST_F32) {
+        const float4 w = __ldg(reinterpret_cast<const float4*>(f.f32 + g));
+        vals[0] = w.x;
+        vals[1] = w.y;
+        vals[2] = w.z;
+        vals[3] = w.w;
+    } else if constexpr (STORE == ST_F64) {
+        const double2 w = __ldg(reinterpret_cast<const double2*>(f.f64 + g));
+        vals[0] = (T)w.x;
+        vals[1] = (T)w.y;
+    } else {
+        const uint4 hv = __ldg(reinterpret_cast<const uint4*>(f.hi + g));
+        const uint4 lv = __ldg(reinterpret_cast<const uint4*>(f.lo + g));
+        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            vals[2 * e] = (T)(__uint_as_float(hw[e] << 16) + __uint_as_float(lw[e] << 16));
+            vals[2 * e + 1] = (T)(__uint_as_float(hw[e] & 0xffff0000u) + __uint_as_float(lw[e] & 0xffff0000u));
+        }
+    }
+}
+
+// KC > 0: compile-time component count (loads batched UNR deep so they are in
+// flight together); KC = 0: runtime count kc.
+template <typename T, int STORE, int H, int G, int S2, int S3, int SC, int KC>
+__device__ __forceinline__ void load_halo(T* halo, const FieldView& f, int k0, int kc, int o1, int o2, int o3)
+{
+    constexpr int VEC = VecOf<STORE>::n;
+    constexpr int OFF = ((PAD - G) % VEC + VEC) % VEC;   // block origins are multiples of 8
+    constexpr int NV = (OFF + H + VEC - 1) / VEC;        // vectors per halo row
+    constexpr int UNR = 4;
+    const int nq = (KC > 0 ? KC : kc) * H * H * NV;
+    const int NP = f.NP;
+    const int xa = o1 + PAD - OFF;                        // aligned padded x of the row start
+    const int64_t gbase = (int64_t)k0 * f.plane + ((int64_t)(o3 + PAD) * NP + (o2 + PAD)) * NP + xa;
+    for (int q0 = threadIdx.x; q0 < nq; q0 += UNR * NT) {
+        T vals[UNR][VEC];
+        int dsto[UNR], vv[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int q = q0 + u * NT;
+            const int row = q / NV, v = q - row * NV;
+            const int y = row % H, zk = row / H;
+            const int z = zk % H, k = zk / H;
+            vv[u] = v;
+            dsto[u] = k * SC + z * S3 + y * S2;
+            if (q < nq) load_vec<T, STORE, VEC>(f, gbase + (int64_t)k * f.plane + ((int64_t)z * NP + y) * NP + v * VEC,
+                                                vals[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (q0 + u * NT < nq) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const int x = vv[u] * VEC + e - OFF;
+                    if (x >= 0 && x < H) halo[dsto[u] + x] = vals[u][e];
+                }
+            }
         }
     }
 }
@@ -441,45 +517,74 @@ __device__ __forceinline__ void load_halo(T* halo, const FieldView& f, int k0, i
 __device__ __forceinline__ int pack_rel(int r1, int r2, int r3) { return r1 | (r2 << 8) | (r3 << 16); }
 __device__ __forceinline__ int pack_cell(int c1, int c2, int c3) { return c1 | (c2 << 10) | (c3 << 20); }
 
+// Per-particle record written in P1 and read (broadcast) by the Q warps.
+template <typename T>
+struct alignas(4 * sizeof(T)) PRec {
+    T t[3];         // offsets in the cell (Sec. 2.2 step 3, normalised by delta)
+    T relf;         // packed relative cell (pack_rel), bit-cast into T's storage
+};
+
+// Byte offsets of the shared-memory regions, each 32-byte aligned (the
+// particle records are read and written as 16- or 32-byte vectors).
+constexpr size_t align32(size_t x) { return (x + 31) & ~size_t(31); }
+
+template <typename T, int SC>
+struct SmemPlan {
+    static constexpr size_t rec = align32((size_t)3 * SC * sizeof(T));
+    static constexpr size_t k = align32(rec + PB * sizeof(PRec<T>));
+    static constexpr size_t w = align32(k + (size_t)6 * PB * sizeof(T));
+    static constexpr size_t cell = align32(w + (size_t)NW * 48 * sizeof(T));
+    static constexpr size_t total = cell + PB * sizeof(int);
+};
+
 // ---------------------------------------------------------------------------
 // The block kernel.
 // ---------------------------------------------------------------------------
 template <typename T, int I, int DEG, int MODE, int STORE>
-__global__ void __launch_bounds__(NT) k_block(const BlockArgs a)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_block(const __grid_constant__ BlockArgs a)
 {
     constexpr bool IS_STEP = (MODE == MODE_RK2 || MODE == MODE_AB2);
     constexpr bool D = (MODE == MODE_INTERP_DERIV);
     constexpr int MARGIN = (MODE == MODE_RK2) ? 1 : 0;     // halo margin for the stage-2 point
     constexpr int H = BLK + I - 1 + 2 * MARGIN;
     constexpr int G = I / 2 - 1 + MARGIN;                   // halo origin = block origin - G
+    constexpr int LO = I / 2 - 1;                           // stencil node offset
+    constexpr int RMAX = H - 1 - I / 2;                     // largest cell whose stencil fits the halo
     using Lay = Layout<I, H>;
     constexpr int S2 = Lay::S2, S3 = Lay::S3, SC = Lay::SC;
-    constexpr int LO = I / 2 - 1;                           // stencil node offset
+    using SL = SmemLd<T, S2, S3, SC>;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* halo = reinterpret_cast<T*>(smem_raw);
-    T* p_t = halo + 3 * SC;                                 // [3][PB]
-    T* p_k1 = p_t + 3 * PB;                                 // [3][PB]
-    T* p_k2 = p_k1 + 3 * PB;                                // [3][PB]
-    int* p_rel = reinterpret_cast<int*>(p_k2 + 3 * PB);     // [PB]
-    int* p_cell = p_rel + PB;                               // [PB]
+    using SM = SmemPlan<T, SC>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* halo = reinterpret_cast<T*>(smem_raw);                               // [3][SC]
+    PRec<T>* p_rec = reinterpret_cast<PRec<T>*>(smem_raw + SM::rec);        // [PB]
+    T* p_k = reinterpret_cast<T*>(smem_raw + SM::k);                        // [6][PB]: k1 (3), k2 (3)
+    T* wbuf = reinterpret_cast<T*>(smem_raw + SM::w);                       // [NW][2][24] weights
+    int* p_cell = reinterpret_cast<int*>(smem_raw + SM::cell);              // [PB]
 
     const int b = blockIdx.x;
     const int j0 = a.offsets[b], j1 = a.offsets[b + 1];
     if (j0 >= j1) return;
 
-    const int N = a.g.N, mask = a.g.mask;
+    const int mask = a.g.mask;
     const int nb1 = a.g.nb1, nb2 = a.g.nb2;
     const int bx = b % nb1, by = (b / nb1) % nb2, bz = b / (nb1 * nb2);
     const int o1 = bx * BLK - G, o2 = by * BLK - G, o3 = bz * BLK - G;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t np = a.np;
     const double inv_delta = a.g.inv_delta;
+    T* wv = wbuf + warp * 48;
+    T* wd = wv + 24;
 
-    LaneRows<T, I, DEG, D> R;
-    R.load(a.tab, lane);
+    WeightEval<T, I, DEG, D> W;
+    W.init(table<T>(a), lane);
+    Lane<T, I, D> L;
+    L.init(lane);
 
     const int nchunks = IS_STEP ? 1 : (a.f.C + 2) / 3;
+    const T dtid = (T)(a.dt * inv_delta);
+    const int rcomp = ((lane & 16) ? 2 : 0) + ((lane & 8) ? 1 : 0);   // component held after reduce4
+    const bool writer = (lane & 7) == 0 && rcomp < 3;                 // lanes 0, 8, 16
 
     for (int batch = j0; batch < j1; batch += PB) {
         const int nbat = min(PB, j1 - batch);
@@ -487,159 +592,148 @@ __global__ void __launch_bounds__(NT) k_block(const BlockArgs a)
         double X[3] = {0, 0, 0};
         float hr[3] = {0, 0, 0};
         int id = 0;
-        int c[3] = {0, 0, 0};
         if (tid < nbat) {
             const int j = batch + tid;
             const int src = a.perm[j];
             id = a.id_in ? a.id_in[src] : src;
             bool ok = true;
-            double t[3];
+            int c[3];
+            PRec<T> rec;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
+                double t;
                 X[ax] = a.pos_in[ax * np + src];
-                ok &= split_axis(X[ax], inv_delta, mask, c[ax], t[ax]);
-                p_t[ax * PB + tid] = (T)t[ax];
+                ok &= split_axis(X[ax], inv_delta, mask, c[ax], t);
+                rec.t[ax] = (T)t;
             }
             if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
             const int r1 = (c[0] - o1) & mask, r2 = (c[1] - o2) & mask, r3 = (c[2] - o3) & mask;
             // a particle always lies in its own block; the guard only keeps a
             // corrupted permutation from indexing outside the staged halo
-            const bool in = r1 >= LO && r1 <= H - 1 - I / 2 && r2 >= LO && r2 <= H - 1 - I / 2 &&
-                            r3 >= LO && r3 <= H - 1 - I / 2;
-            p_rel[tid] = in ? pack_rel(r1, r2, r3) : -1;
+            const bool in = r1 >= LO && r1 <= RMAX && r2 >= LO && r2 <= RMAX && r3 >= LO && r3 <= RMAX;
+            const int rp = in ? pack_rel(r1, r2, r3) : -1;
+            if constexpr (sizeof(T) == 4) rec.relf = __int_as_float(rp);
+            else rec.relf = __longlong_as_double((long long)rp);
+            p_rec[tid] = rec;
             p_cell[tid] = pack_cell(c[0], c[1], c[2]);
             if (MODE == MODE_AB2 && a.history_valid) {
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) hr[ax] = a.rhs_in[ax * np + src];
             }
         }
-        // ---------------- Q1: interpolation at X ----------------
+        // ---------------- Q: interpolation ----------------
         for (int ch = 0; ch < nchunks; ++ch) {
             if (batch == j0 || nchunks > 1) {
                 if (ch > 0 || batch != j0) __syncthreads();   // previous readers of the halo are done
-                load_halo<T, STORE, H, S2, S3, SC>(halo, a.f, 3 * ch, o1, o2, o3, N, mask);
+                if constexpr (IS_STEP)
+                    load_halo<T, STORE, H, G, S2, S3, SC, 3>(halo, a.f, 0, 3, o1, o2, o3);
+                else
+                    load_halo<T, STORE, H, G, S2, S3, SC, 0>(halo, a.f, 3 * ch, min(3, a.f.C - 3 * ch), o1, o2, o3);
             }
             __syncthreads();
             for (int q = warp; q < nbat; q += NW) {
-                const int rp = p_rel[q];
-                const T s1 = p_t[q] - (T)0.5, s2 = p_t[PB + q] - (T)0.5, s3 = p_t[2 * PB + q] - (T)0.5;
-                T acc[12];
+                const PRec<T> rec = p_rec[q];
+                int rp;
+                if constexpr (sizeof(T) == 4) rp = __float_as_int(rec.relf);
+                else rp = (int)__double_as_longlong(rec.relf);
+                const T t1 = rec.t[0], t2 = rec.t[1], t3 = rec.t[2];
+                const int r1 = rp & 255, r2 = (rp >> 8) & 255, r3 = (rp >> 16) & 255;
                 if (rp >= 0) {
-                    const int r1 = rp & 255, r2 = (rp >> 8) & 255, r3 = (rp >> 16) & 255;
-                    SmemLd<T, S2, S3, SC> ld{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)};
-                    gather<T, I, DEG, D>(ld, lane, a.tab, R, s1, s2, s3, acc);
+                    L.load(SL{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)});
                 } else {
                     const int pc = p_cell[q];
-                    GlobalLd<T, STORE, I> ld{a.f, pc & 1023, (pc >> 10) & 1023, (pc >> 20) & 1023, 3 * ch,
-                                             a.f.C - 1, N, mask};
-                    gather<T, I, DEG, D>(ld, lane, a.tab, R, s1, s2, s3, acc);
+                    L.load(GlobalLd<T, STORE, I>{a.f, pc & 1023, (pc >> 10) & 1023, (pc >> 20) & 1023, 3 * ch,
+                                                 a.f.C - 1, mask});
                 }
-                if constexpr (IS_STEP) {
-                    if (lane < 3) p_k1[lane * PB + q] = acc[lane];
-                } else {
-                    const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
-                    const int kc = min(3, a.f.C - 3 * ch);
-                    const int nout = D ? 3 * kc : kc;
-                    if (lane < nout) {
-                        // lane r -> output row: value k = r, or derivative (k, j) = (r/3, r%3)
-                        T v;
-                        int row;
-                        if (D) {
-                            v = 0;
+                W.eval(t1 - (T)0.5, t2 - (T)0.5, t3 - (T)0.5, wv, wd);
+                T acc[12];
+                L.contract(wv, wd, acc);
+                if constexpr (MODE == MODE_RK2) {
+                    // ---- stage 1 result in every lane
+                    const T m = reduce4(acc, lane);
+                    const T k1[3] = {__shfl_sync(0xffffffffu, m, 0), __shfl_sync(0xffffffffu, m, 8),
+                                     __shfl_sync(0xffffffffu, m, 16)};
+                    // ---- stage-2 point, cell-relative: t* = t + dt k1 / delta
+                    T ts[3] = {fma(dtid, k1[0], t1), fma(dtid, k1[1], t2), fma(dtid, k1[2], t3)};
+                    int dc[3];
 #pragma unroll
-                            for (int r = 0; r < 9; ++r)
-                                if (r == lane) v = acc[3 + r];
-                            v *= (T)inv_delta;
-                            row = 9 * ch + lane;
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const T fl = floor(ts[ax]);
+                        dc[ax] = (int)fl;
+                        ts[ax] -= fl;
+                    }
+                    if ((dc[0] | dc[1] | dc[2]) != 0 || rp < 0) {
+                        const int s1 = r1 + dc[0], s2 = r2 + dc[1], s3 = r3 + dc[2];
+                        const bool in = rp >= 0 && s1 >= LO && s1 <= RMAX && s2 >= LO && s2 <= RMAX && s3 >= LO &&
+                                        s3 <= RMAX;
+                        if (in) {
+                            L.load(SL{halo + (s3 - LO) * S3 + (s2 - LO) * S2 + (s1 - LO)});
                         } else {
-                            v = lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[2]);
-                            row = 3 * ch + lane;
+                            if (lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
+                            const int pc = p_cell[q];
+                            L.load(GlobalLd<T, STORE, I>{a.f, ((pc & 1023) + dc[0]) & mask,
+                                                         (((pc >> 10) & 1023) + dc[1]) & mask,
+                                                         (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2, mask});
                         }
-                        if (a.out_f64) reinterpret_cast<double*>(a.out)[(int64_t)row * np + qid] = (double)v;
-                        else reinterpret_cast<float*>(a.out)[(int64_t)row * np + qid] = (float)v;
+                    }
+                    W.eval(ts[0] - (T)0.5, ts[1] - (T)0.5, ts[2] - (T)0.5, wv, wd);
+                    L.contract(wv, wd, acc);
+                    const T m2 = reduce4(acc, lane);
+                    if (writer) {
+                        p_k[rcomp * PB + q] = rcomp == 0 ? k1[0] : (rcomp == 1 ? k1[1] : k1[2]);
+                        p_k[(3 + rcomp) * PB + q] = m2;
+                    }
+                } else if constexpr (MODE == MODE_AB2) {
+                    const T m = reduce4(acc, lane);
+                    if (writer) p_k[rcomp * PB + q] = m;
+                } else if constexpr (MODE == MODE_INTERP) {
+                    const T m = reduce4(acc, lane);
+                    const int kc = min(3, a.f.C - 3 * ch);
+                    if (writer && rcomp < kc) {
+                        const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
+                        const int64_t o = (int64_t)(3 * ch + rcomp) * np + qid;
+                        if (a.out_f64) reinterpret_cast<double*>(a.out)[o] = (double)m;
+                        else reinterpret_cast<float*>(a.out)[o] = (float)m;
+                    }
+                } else {
+                    // gradient: value index v = 8 bit4 + 4 bit3 + 2 bit2 + bit1; d u_k/d t_j at v = 3 + 3k + j
+                    const T m = reduce16(acc, lane);
+                    const int v = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                                  ((lane >> 1) & 1);
+                    const int kc = min(3, a.f.C - 3 * ch);
+                    if ((lane & 1) == 0 && v >= 3 && v < 3 + 3 * kc) {
+                        const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
+                        const int row = 9 * ch + (v - 3);
+                        const int64_t o = (int64_t)row * np + qid;
+                        const double g = (double)m * inv_delta;
+                        if (a.out_f64) reinterpret_cast<double*>(a.out)[o] = g;
+                        else reinterpret_cast<float*>(a.out)[o] = (float)g;
                     }
                 }
             }
         }
-        if constexpr (!IS_STEP) {
-            __syncthreads();
-            continue;
-        } else {
-            __syncthreads();
-            if constexpr (MODE == MODE_RK2) {
-                // ---------------- P2: stage-2 point ----------------
-                if (tid < nbat) {
-                    int cs[3];
-                    T ts[3];
-                    if constexpr (sizeof(T) == 4) {
-                        // cell-relative float32: t* = t + dt k1 / delta
-                        const float sc = (float)(a.dt * inv_delta);
-#pragma unroll
-                        for (int ax = 0; ax < 3; ++ax) {
-                            const float tt = fmaf(sc, (float)p_k1[ax * PB + tid], (float)p_t[ax * PB + tid]);
-                            const float fl = floorf(tt);
-                            cs[ax] = (c[ax] + (int)fl) & mask;
-                            ts[ax] = tt - fl;
-                        }
-                    } else {
-                        bool ok = true;
-#pragma unroll
-                        for (int ax = 0; ax < 3; ++ax) {
-                            const double xs = X[ax] + a.dt * (double)p_k1[ax * PB + tid];
-                            double tt;
-                            ok &= split_axis(xs, inv_delta, mask, cs[ax], tt);
-                            ts[ax] = (T)tt;
-                        }
-                        if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
-                    }
-                    const int r1 = (cs[0] - o1) & mask, r2 = (cs[1] - o2) & mask, r3 = (cs[2] - o3) & mask;
-                    const bool in = r1 >= LO && r1 <= H - 1 - I / 2 && r2 >= LO && r2 <= H - 1 - I / 2 &&
-                                    r3 >= LO && r3 <= H - 1 - I / 2;
-                    if (!in) atomicOr(a.flags + FLAG_CFL, 1);
-                    p_rel[tid] = in ? pack_rel(r1, r2, r3) : -1;
-                    p_cell[tid] = pack_cell(cs[0], cs[1], cs[2]);
-#pragma unroll
-                    for (int ax = 0; ax < 3; ++ax) p_t[ax * PB + tid] = ts[ax];
-                }
-                __syncthreads();
-                // ---------------- Q2: interpolation at X* ----------------
-                for (int q = warp; q < nbat; q += NW) {
-                    const int rp = p_rel[q];
-                    const T s1 = p_t[q] - (T)0.5, s2 = p_t[PB + q] - (T)0.5, s3 = p_t[2 * PB + q] - (T)0.5;
-                    T acc[12];
-                    if (rp >= 0) {
-                        const int r1 = rp & 255, r2 = (rp >> 8) & 255, r3 = (rp >> 16) & 255;
-                        SmemLd<T, S2, S3, SC> ld{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)};
-                        gather<T, I, DEG, D>(ld, lane, a.tab, R, s1, s2, s3, acc);
-                    } else {
-                        const int pc = p_cell[q];
-                        GlobalLd<T, STORE, I> ld{a.f, pc & 1023, (pc >> 10) & 1023, (pc >> 20) & 1023, 0, 2, N, mask};
-                        gather<T, I, DEG, D>(ld, lane, a.tab, R, s1, s2, s3, acc);
-                    }
-                    if (lane < 3) p_k2[lane * PB + q] = acc[lane];
-                }
-                __syncthreads();
-            }
+        __syncthreads();
+        if constexpr (IS_STEP) {
             // ---------------- P3: update, re-split, write ----------------
             if (tid < nbat) {
                 const int j = batch + tid;
-                double Xn[3];
                 int cn[3];
                 bool ok = true;
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
-                    const double k1 = (double)p_k1[ax * PB + tid];
+                    const double k1 = (double)p_k[ax * PB + tid];
+                    double xn;
                     if constexpr (MODE == MODE_RK2) {
-                        const double k2 = (double)p_k2[ax * PB + tid];
-                        Xn[ax] = X[ax] + (0.5 * a.dt) * (k1 + k2);
+                        const double k2 = (double)p_k[(3 + ax) * PB + tid];
+                        xn = X[ax] + (0.5 * a.dt) * (k1 + k2);
                     } else {
                         const double inc = a.history_valid ? (1.5 * k1 - 0.5 * (double)hr[ax]) : k1;
-                        Xn[ax] = X[ax] + a.dt * inc;
+                        xn = X[ax] + a.dt * inc;
                         a.rhs_out[ax * np + j] = (float)k1;
                     }
                     double tt;
-                    ok &= split_axis(Xn[ax], inv_delta, mask, cn[ax], tt);
-                    a.pos_out[ax * np + j] = Xn[ax];
+                    ok &= split_axis(xn, inv_delta, mask, cn[ax], tt);
+                    a.pos_out[ax * np + j] = xn;
                 }
                 if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
                 a.id_out[j] = id;
@@ -656,7 +750,7 @@ constexpr size_t block_smem_bytes()
     constexpr int MARGIN = (MODE == MODE_RK2) ? 1 : 0;
     constexpr int H = BLK + I - 1 + 2 * MARGIN;
     using Lay = Layout<I, H>;
-    return (size_t)(3 * Lay::SC + 9 * PB) * sizeof(T) + 2 * PB * sizeof(int);
+    return SmemPlan<T, Lay::SC>::total;
 }
 
 template <typename T, int I, int DEG, int MODE, int STORE>
@@ -679,8 +773,8 @@ template <int I, int DEG>
 cudaError_t dispatch_store_mode(int mode, const BlockArgs& a, int64_t nblocks, cudaStream_t st)
 {
     const int s = a.f.storage;
-#define TRK_CASE(M)                                                                   \
-    case M:                                                                           \
+#define TRK_CASE(M)                                                                        \
+    case M:                                                                                \
         if (s == ST_F64) return launch_block_t<double, I, DEG, M, ST_F64>(a, nblocks, st); \
         if (s == ST_F32) return launch_block_t<float, I, DEG, M, ST_F32>(a, nblocks, st);  \
         return launch_block_t<float, I, DEG, M, ST_BF16X2>(a, nblocks, st);

@@ -25,14 +25,34 @@ enum { MODE_INTERP = 0, MODE_INTERP_DERIV = 1, MODE_RK2 = 2, MODE_AB2 = 3 };
 constexpr int BLK = 8;        // cell-block edge used by the block kernels
 constexpr int LBLK = 3;       // log2(BLK)
 
+// The stored field is ghost-padded: PAD periodic copies on each side of every
+// axis, so a block's halo is a plain box (no wrap) and its rows can be read
+// with aligned 16-byte vector loads.  Component k, node (x1, x2, x3) with
+// x in [-PAD, N + PAD) lives at k * plane + ((x3 + PAD) * NP + (x2 + PAD)) * NP + (x1 + PAD).
+constexpr int PAD = 8;
+
 struct FieldView {
     int storage;              // ST_*
     int C;                    // components
-    int64_t plane;            // N^3 values per component
-    const double* f64;        // [C][N^3]                (ST_F64)
-    const float* f32;         // [C][N^3]                (ST_F32)
-    const __nv_bfloat16* hi;  // [C][N^3] high parts     (ST_BF16X2)
-    const __nv_bfloat16* lo;  // [C][N^3] low parts      (ST_BF16X2)
+    int NP;                   // padded extent N + 2 PAD
+    int64_t plane;            // NP^3 values per component
+    const double* f64;        // [C][NP^3]                (ST_F64)
+    const float* f32;         // [C][NP^3]                (ST_F32)
+    const __nv_bfloat16* hi;  // [C][NP^3] high parts     (ST_BF16X2)
+    const __nv_bfloat16* lo;  // [C][NP^3] low parts      (ST_BF16X2)
+};
+
+__host__ __device__ __forceinline__ int64_t padded_index(int NP, int x1, int x2, int x3)
+{
+    return ((int64_t)(x3 + PAD) * NP + (x2 + PAD)) * NP + (x1 + PAD);
+}
+
+// Kernel weights beta_i(s), s = t - 1/2, as polynomial coefficients, passed by
+// value so that the kernels read them as constant-bank operands.
+template <typename T>
+struct CoefTable {
+    T c[TRK_TAB_MAX_I][TRK_TAB_MAX_DEG];   // beta_i
+    T d[TRK_TAB_MAX_I][TRK_TAB_MAX_DEG];   // beta_i' (d/dt)
 };
 
 struct GridGeom {
@@ -46,7 +66,8 @@ struct GridGeom {
 struct BlockArgs {
     GridGeom g;
     FieldView f;
-    int tab;                  // coefficient table index
+    CoefTable<float> cf;      // weights for float32 arithmetic
+    CoefTable<double> cd;     // weights for float64 arithmetic
     int64_t np;               // particle count (stride of the [3][np] arrays)
     const int32_t* offsets;   // [nblocks + 1]
     const int32_t* perm;      // sorted position j -> index into the *_in arrays
@@ -110,7 +131,8 @@ cudaError_t launch_offsets(const uint32_t* keys_sorted, int64_t n, int64_t nbloc
 cudaError_t launch_unpermute_pos(int64_t np, const double* src, const int32_t* id, double* dst, cudaStream_t st);
 cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id, float* dst, cudaStream_t st);
 
-cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int64_t n, void* dst, cudaStream_t st);
+// Fill the ghost-padded storage from a dense field src[C][N][N][N] (periodic ghosts).
+cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int C, int N, void* dst, cudaStream_t st);
 
 // Block kernels, one entry per kernel width I (block_i4.cu, block_i6.cu, block_i8.cu).
 // deg_hi selects the degree-(I+1) instantiation (spline with m = I/2).

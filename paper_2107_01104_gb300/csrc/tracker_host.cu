@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 #include "tracker.h"
@@ -38,6 +39,8 @@ struct TableInfo {
     int family, I, m, deg;
 };
 const TableInfo kTables[TRK_NUM_TABLES] = TRK_TABLE_INFO;
+const double kCoef[TRK_NUM_TABLES][TRK_TAB_MAX_I][TRK_TAB_MAX_DEG] = TRK_COEF_INIT;
+const double kDCoef[TRK_NUM_TABLES][TRK_TAB_MAX_I][TRK_TAB_MAX_DEG] = TRK_DCOEF_INIT;
 
 int find_table(int family, int I, int m)
 {
@@ -99,9 +102,48 @@ struct tracker {
     float* rhs_s[2] = {nullptr, nullptr};
     int* d_flags = nullptr;
     int64_t launches = 0;
+    // instrumentation: event pairs per kernel class
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pairs[3];
+    int64_t prof_launches[3] = {0, 0, 0};
 };
 
 namespace {
+
+enum { PROF_STEP = 0, PROF_BIN = 1, PROF_OTHER = 2 };
+
+cudaEvent_t next_event(tracker* t)
+{
+    if (t->ev_used == t->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        t->ev_pool.push_back(e);
+    }
+    return t->ev_pool[t->ev_used++];
+}
+
+// Records an event pair around a region of kernel launches when profiling.
+struct ProfScope {
+    tracker* t;
+    int cls;
+    int64_t n;
+    cudaEvent_t a = nullptr;
+    ProfScope(tracker* t_, int cls_, int64_t n_ = 1) : t(t_), cls(cls_), n(n_)
+    {
+        if (t->prof && (a = next_event(t))) cudaEventRecord(a, t->stream);
+    }
+    ~ProfScope()
+    {
+        if (!a) return;
+        cudaEvent_t b = next_event(t);
+        if (!b) return;
+        cudaEventRecord(b, t->stream);
+        t->prof_pairs[cls].emplace_back(a, b);
+        t->prof_launches[cls] += n;
+    }
+};
 
 int set_geometry(tracker* t, int bx, int by, int bz)
 {
@@ -171,7 +213,8 @@ FieldView field_view(const tracker* t)
     FieldView f{};
     f.storage = t->storage;
     f.C = t->C;
-    f.plane = (int64_t)t->N * t->N * t->N;
+    f.NP = t->N + 2 * PAD;
+    f.plane = (int64_t)f.NP * f.NP * f.NP;
     if (t->storage == ST_F64) f.f64 = reinterpret_cast<const double*>(t->field);
     else if (t->storage == ST_F32) f.f32 = reinterpret_cast<const float*>(t->field);
     else {
@@ -183,6 +226,7 @@ FieldView field_view(const tracker* t)
 
 cudaError_t launch_block(tracker* t, int mode, const BlockArgs& a)
 {
+    ProfScope ps(t, PROF_STEP);
     t->launches += 1;
     switch (t->I) {
         case 4: return launch_block_i4(mode, a, t->nblocks, t->deg_hi, t->stream);
@@ -194,6 +238,7 @@ cudaError_t launch_block(tracker* t, int mode, const BlockArgs& a)
 // keys (caller order) -> sorted keys, perm, offsets
 int bin_into(tracker* t, int64_t np, const double* pos, uint32_t* keys, int32_t* perm, int32_t* offsets)
 {
+    ProfScope ps(t, PROF_BIN);
     CUDA_TRY(launch_keys(t->g, np, pos, keys, t->d_flags, t->stream));
     t->launches += 1;
     CUDA_TRY(radix_sort(keys, np, t->key_bits, t->keys_sorted, perm, t->sort_scratch, t->stream, &t->launches));
@@ -220,7 +265,13 @@ BlockArgs base_args(tracker* t)
     BlockArgs a{};
     a.g = t->g;
     a.f = field_view(t);
-    a.tab = t->tab;
+    for (int i = 0; i < TRK_TAB_MAX_I; ++i)
+        for (int d = 0; d < TRK_TAB_MAX_DEG; ++d) {
+            a.cd.c[i][d] = kCoef[t->tab][i][d];
+            a.cd.d[i][d] = kDCoef[t->tab][i][d];
+            a.cf.c[i][d] = (float)kCoef[t->tab][i][d];
+            a.cf.d[i][d] = (float)kDCoef[t->tab][i][d];
+        }
     a.offsets = t->offsets;
     a.flags = t->d_flags;
     return a;
@@ -294,7 +345,40 @@ int tracker_destroy(tracker* t)
         dev_free(t->rhs_s[i]);
     }
     dev_free(t->d_flags);
+    for (cudaEvent_t e : t->ev_pool) cudaEventDestroy(e);
     delete t;
+    return TRK_OK;
+}
+
+int tracker_profile(tracker* t, int enable)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (enable) {
+        CUDA_TRY(cudaStreamSynchronize(t->stream));
+        t->ev_used = 0;
+        for (int c = 0; c < 3; ++c) {
+            t->prof_pairs[c].clear();
+            t->prof_launches[c] = 0;
+        }
+    }
+    t->prof = enable != 0;
+    return TRK_OK;
+}
+
+int tracker_profile_read(tracker* t, double* ms, int64_t* launches)
+{
+    if (!t || !ms || !launches) return fail(TRK_EINVAL, "NULL argument");
+    CUDA_TRY(cudaStreamSynchronize(t->stream));
+    for (int c = 0; c < 3; ++c) {
+        double tot = 0;
+        for (auto& pr : t->prof_pairs[c]) {
+            float x = 0;
+            CUDA_TRY(cudaEventElapsedTime(&x, pr.first, pr.second));
+            tot += x;
+        }
+        ms[c] = tot;
+        launches[c] = t->prof_launches[c];
+    }
     return TRK_OK;
 }
 
@@ -324,14 +408,16 @@ int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src
     if (C < 1 || C > 16) return fail(TRK_EINVAL, "C=%d outside [1, 16]", C);
     if (src_dtype != TRK_DTYPE_F64 && src_dtype != TRK_DTYPE_F32) return fail(TRK_EINVAL, "unknown src_dtype %d", src_dtype);
     const int64_t n = (int64_t)C * t->N * t->N * t->N;
+    const int64_t NP = t->N + 2 * PAD;
+    const int64_t n_stored = (int64_t)C * NP * NP * NP;
     const size_t esz = t->storage == TRK_F64 ? 8 : 4;
     if (t->C != C || !t->field) {
         dev_free(t->field);
         t->field = nullptr;
         t->C = 0;
-        if (dev_alloc(&t->field, (size_t)n * esz) != cudaSuccess) {
+        if (dev_alloc(&t->field, (size_t)n_stored * esz) != cudaSuccess) {
             cudaGetLastError();
-            return fail(TRK_ENOMEM, "cannot allocate field storage (%zu bytes)", (size_t)n * esz);
+            return fail(TRK_ENOMEM, "cannot allocate field storage (%zu bytes)", (size_t)n_stored * esz);
         }
         t->C = C;
     }
@@ -346,7 +432,10 @@ int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src
         CUDA_TRY(cudaMemcpyAsync(staging, src, src_bytes, cudaMemcpyHostToDevice, t->stream));
         dsrc = staging;
     }
-    CUDA_TRY(launch_convert_field(t->storage, src_dtype == TRK_DTYPE_F64, dsrc, n, t->field, t->stream));
+    {
+        ProfScope ps(t, PROF_OTHER);
+        CUDA_TRY(launch_convert_field(t->storage, src_dtype == TRK_DTYPE_F64, dsrc, C, t->N, t->field, t->stream));
+    }
     t->launches += 1;
     if (staging) {
         CUDA_TRY(cudaStreamSynchronize(t->stream));
@@ -418,13 +507,20 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     if ((rc = ensure_state(t, np))) return rc;
     const int mode = scheme == TRK_RK2 ? MODE_RK2 : MODE_AB2;
     // initial keys from the caller's positions
-    CUDA_TRY(launch_keys(t->g, np, pos, t->keys, t->d_flags, t->stream));
-    t->launches += 1;
+    {
+        ProfScope ps(t, PROF_BIN);
+        CUDA_TRY(launch_keys(t->g, np, pos, t->keys, t->d_flags, t->stream));
+        t->launches += 1;
+    }
     int cur = 0;
     for (int s = 0; s < steps; ++s) {
-        CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream, &t->launches));
-        CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
-        t->launches += 1;
+        {
+            ProfScope ps(t, PROF_BIN);
+            CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
+                                &t->launches));
+            CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
+            t->launches += 1;
+        }
         BlockArgs a = base_args(t);
         a.np = np;
         a.perm = t->perm;
@@ -448,6 +544,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
         CUDA_TRY(launch_block(t, mode, a));
         cur = nxt;
     }
+    ProfScope ps(t, PROF_OTHER);
     CUDA_TRY(launch_unpermute_pos(np, t->pos_s[cur], t->id_s[cur], pos, t->stream));
     t->launches += 1;
     if (scheme == TRK_AB2) {

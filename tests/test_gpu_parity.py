@@ -4,11 +4,14 @@ Same-input comparisons give the oracle exactly the field values the library
 stores (float32, or hi + lo of the split-bf16 pair, promoted to float64), so
 the difference measures the library's arithmetic alone.  Tolerances:
   binning                     bit-exact keys, permutation and offsets
-  float64 storage             1e-12 x field rms (the separable float64 sum
-                              rounds in a different order than the oracle's
-                              direct quadruple loop)
-  float32 / split-bf16        2e-6 x field rms (float32 weights and sums)
-  split-bf16 vs the float64 field   1e-5 x field rms
+  float64 storage             1e-12 relative: max error <= 1e-12 x max|field|
+                              (the separable float64 sum rounds in a different
+                              order than the oracle's direct quadruple loop)
+  float32 / split-bf16        max error <= 2e-6 x field rms (float32 weights
+                              and sums, same input)
+  split-bf16 vs float64 field rms error <= 1e-5 x field rms (hi + lo keeps
+                              about 2^-18 of each value, so the max error over
+                              many particles can exceed 1e-5 where |u| ~ 4)
 """
 import math
 
@@ -49,11 +52,13 @@ def edge_positions(N, n, seed):
     rng = np.random.default_rng(seed)
     pos = rng.uniform(-L, 2 * L, (3, n))
     delta = L / N
-    k = rng.integers(-N, 2 * N, (3, n // 8))
-    pos[:, : n // 8] = k * delta                                      # on nodes
-    faces = rng.integers(0, N + 1, (3, n // 8)) * delta
-    pos[:, n // 8: n // 4] = np.nextafter(faces, np.where(rng.random((3, n // 8)) < 0.5, -np.inf, np.inf))
-    pos[:, n // 4: n // 4 + 16] = pos[:, :16]                         # duplicates
+    q = n // 8
+    k = rng.integers(-N, 2 * N, (3, q))
+    pos[:, :q] = k * delta                                            # on nodes
+    faces = rng.integers(0, N + 1, (3, q)) * delta
+    pos[:, q:2 * q] = np.nextafter(faces, np.where(rng.random((3, q)) < 0.5, -np.inf, np.inf))  # +-1 ulp of faces
+    if n >= 2 * q + 16:
+        pos[:, 2 * q:2 * q + 16] = pos[:, :16]                        # duplicates
     return pos
 
 
@@ -99,10 +104,13 @@ def test_interpolate_parity(family, I, m, storage):
     t.sync()
     ref = oracle.interp(stored(field, storage), pos, family, I, m)
     err = np.abs(out.cpu().numpy() - ref).max()
-    assert err <= TOL[storage] * 1.0, err          # field rms is 1
+    scale = np.abs(field).max() if storage == trk.TRK_F64 else np.sqrt(np.mean(field ** 2))
+    assert err <= TOL[storage] * scale, err
     if storage == trk.TRK_BF16X2:
         truth = oracle.interp(field, pos, family, I, m)
-        assert np.abs(out.cpu().numpy() - truth).max() <= 1e-5
+        d = out.cpu().numpy() - truth
+        assert np.sqrt(np.mean(d ** 2)) <= 1e-5 * np.sqrt(np.mean(field ** 2))
+        assert np.abs(d).max() <= 2.0 ** -17 * np.abs(field).max() * 2.0
 
 
 @pytest.mark.parametrize("C", [1, 2, 4, 9, 12])
