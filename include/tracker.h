@@ -226,6 +226,30 @@ int64_t tracker_launch_count(const tracker* t);
 int tracker_profile(tracker* t, int enable);
 int tracker_profile_read(tracker* t, double* ms, int64_t* launches);
 
+/* ---------------------------------------------------------------------- */
+/* Binning without allocation                                              */
+/* ---------------------------------------------------------------------- */
+
+/* The same stable block binning as tracker_bin, for callers that cannot
+ * allocate device memory (an allocator owned by another framework, code
+ * that must not allocate after start-up, drivers that only receive
+ * pre-allocated buffers).  It needs no tracker and allocates nothing: its
+ * scratch is one fixed device array of about 6.3 MB inside the library,
+ * reserved on every GPU that loads the library until the process exits.
+ * The paper has no counterpart; this is a deployment convenience.
+ *
+ * Arguments as in tracker_bin, plus the grid (N, L) and block shape
+ * (bx, by, bz) that a tracker would hold; nonfinite (device int32, may be
+ * NULL) receives 1 if a position was non-finite, else 0.  stream is a
+ * cudaStream_t.  np may not exceed 262144 (2^18): larger calls return
+ * TRK_EINVAL with a message.  The first call on a device looks up the
+ * array's device address, so make that first call before any stream
+ * capture.  Every call reuses the same array, which keeps the last call's
+ * contents; calls that overlap on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller. */
+int tracker_bin_static(int64_t np, const double* pos, int N, double L, int bx, int by, int bz, int32_t* keys,
+                       int32_t* perm, int32_t* offsets, int32_t* nonfinite, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

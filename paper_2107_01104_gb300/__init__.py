@@ -40,7 +40,7 @@ ABI_FUNCTIONS = (
     "tracker_create", "tracker_destroy", "tracker_last_error", "tracker_set_stream", "tracker_sync",
     "tracker_set_field", "tracker_set_block", "tracker_num_blocks", "tracker_bin", "tracker_interpolate",
     "tracker_advance", "tracker_advance_batched", "tracker_adjoint", "tracker_launch_count",
-    "tracker_profile", "tracker_profile_read",
+    "tracker_profile", "tracker_profile_read", "tracker_bin_static",
 )
 
 
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
             "tracker_launch_count": (c_i64, [vp]),
             "tracker_profile": (c_int, [vp, c_int]),
             "tracker_profile_read": (c_int, [vp, vp, vp]),
+            "tracker_bin_static": (c_int, [c_i64, vp, c_int, c_d, c_int, c_int, c_int, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -199,6 +200,23 @@ def tracker_bin(h, pos, keys=None, perm=None, offsets=None):
     nb = tracker_num_blocks(h)
     offsets = torch.empty(nb + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
     _check(load_library().tracker_bin(h, n, _ptr(pos), _ptr(keys), _ptr(perm), _ptr(offsets)))
+    return keys, perm, offsets
+
+
+def tracker_bin_static(pos, N, L=2 * math.pi, block=(8, 8, 8), keys=None, perm=None, offsets=None,
+                       nonfinite=None, stream=None):
+    """Allocation-free binning (see include/tracker.h); outputs are caller tensors."""
+    pos = _dev(pos, torch.float64, "pos", 3)
+    n = pos.shape[1]
+    dev = pos.device
+    nb = (N // block[0]) * (N // block[1]) * (N // block[2])
+    keys = torch.empty(n, dtype=torch.int32, device=dev) if keys is None else keys
+    perm = torch.empty(n, dtype=torch.int32, device=dev) if perm is None else perm
+    offsets = torch.empty(nb + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
+    st = ctypes.c_void_p(stream) if stream is not None else _stream_ptr()
+    _check(load_library().tracker_bin_static(n, _ptr(pos), int(N), float(L), int(block[0]), int(block[1]),
+                                             int(block[2]), _ptr(keys), _ptr(perm), _ptr(offsets), _ptr(nonfinite),
+                                             st))
     return keys, perm, offsets
 
 

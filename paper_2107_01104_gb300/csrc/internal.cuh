@@ -134,6 +134,9 @@ cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id
 // Fill the ghost-padded storage from a dense field src[C][N][N][N] (periodic ghosts).
 cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int C, int N, void* dst, cudaStream_t st);
 
+// Sets the thread-local message returned by tracker_last_error().
+void set_error_message(const char* msg);
+
 // Block kernels, one entry per kernel width I (block_i4.cu, block_i6.cu, block_i8.cu).
 // deg_hi selects the degree-(I+1) instantiation (spline with m = I/2).
 cudaError_t launch_block_i4(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);

@@ -76,6 +76,8 @@ void dev_free(void* p)
 
 }  // namespace
 
+void trk::set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
+
 struct tracker {
     int N = 0;
     double L = 0;
