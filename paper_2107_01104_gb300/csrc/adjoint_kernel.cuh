@@ -1,0 +1,270 @@
+// Discrete adjoint of one RK2 (Heun) step, per cell block.
+//
+// Forward map (Eq. tracers, RK2): X* = X + dt u(X), X' = X + dt/2 (u(X) + u(X*)).
+// Given lambda = dLoss/dX' per particle, with J = du/dX and W(X) the linear
+// map from the field to u(X) (weights beta x beta x beta of Eq. triple_sum):
+//   lambda* = dt/2 J(X*)^T lambda
+//   mu      = dt/2 lambda + dt lambda*
+//   lambda <- lambda + lambda* + J(X)^T mu                      (dLoss/dX)
+//   gfield += W(X)^T mu + W(X*)^T (dt/2 lambda)                (dLoss/dfield)
+// The paper has no adjoint; this is the transpose of its interpolation and
+// time step, written for gradient-based use of the tracker.
+//
+// Phases (one CTA per block, as the forward block kernel):
+//   P1  thread per particle: split X, load lambda (float64)
+//   Q1  warp per particle: gathers at X and X* with value and derivative
+//       weights -> u(X), J(X), J(X*)
+//   P2  thread per particle: the float64 lambda recurrence above
+//   Q2  warp per particle: W^T scatter into a shared-memory accumulator laid
+//       out like the halo (the halo buffer is re-used), then one float64
+//       atomic add per touched halo node into gfield.
+#pragma once
+
+#include "block_kernel.cuh"
+
+namespace trk {
+
+constexpr int PBA = 128;   // particles per adjoint batch (keeps the float64 I = 8 plan under 227 KB)
+
+template <typename T, int SC>
+struct AdjPlan {
+    static constexpr size_t rec = align32((size_t)3 * SC * sizeof(T));
+    static constexpr size_t rec2 = align32(rec + PBA * sizeof(PRec<T>));
+    static constexpr size_t jac = align32(rec2 + PBA * sizeof(PRec<T>));         // [PBA][18] J(X), J(X*)
+    static constexpr size_t mu = align32(jac + (size_t)PBA * 18 * sizeof(T));    // [PBA][6]  mu, dt/2 lambda
+    static constexpr size_t w = align32(mu + (size_t)PBA * 6 * sizeof(T));
+    static constexpr size_t cell = align32(w + (size_t)NW * 48 * sizeof(T));     // [PBA] cells at X
+    static constexpr size_t cell2 = cell + PBA * sizeof(int);                    // [PBA] cells at X*
+    static constexpr size_t total = cell2 + PBA * sizeof(int);
+    static_assert(total <= 232448, "adjoint shared-memory plan exceeds the per-block limit");
+};
+
+template <typename T, int I, int DEG, int STORE>
+__global__ void __launch_bounds__(NT, 1) k_adjoint(const __grid_constant__ AdjArgs a)
+{
+    constexpr int H = BLK + I - 1 + 2;
+    constexpr int G = I / 2;
+    constexpr int LO = I / 2 - 1;
+    constexpr int RMAX = H - 1 - I / 2;
+    using Lay = Layout<I, H>;
+    constexpr int S2 = Lay::S2, S3 = Lay::S3, SC = Lay::SC;
+    using SL = SmemLd<T, S2, S3, SC>;
+    using SM = AdjPlan<T, SC>;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* halo = reinterpret_cast<T*>(smem_raw);                     // field, then the W^T accumulator
+    PRec<T>* p_rec = reinterpret_cast<PRec<T>*>(smem_raw + SM::rec);
+    PRec<T>* p_rec2 = reinterpret_cast<PRec<T>*>(smem_raw + SM::rec2);
+    T* p_jac = reinterpret_cast<T*>(smem_raw + SM::jac);
+    T* p_mu = reinterpret_cast<T*>(smem_raw + SM::mu);
+    T* wbuf = reinterpret_cast<T*>(smem_raw + SM::w);
+    int* p_cell = reinterpret_cast<int*>(smem_raw + SM::cell);
+    int* p_cell2 = reinterpret_cast<int*>(smem_raw + SM::cell2);
+
+    const int b = blockIdx.x;
+    const int j0 = a.offsets[b], j1 = a.offsets[b + 1];
+    if (j0 >= j1) return;
+
+    const int N = a.g.N, mask = a.g.mask;
+    const int nb1 = a.g.nb1, nb2 = a.g.nb2;
+    const int bx = b % nb1, by = (b / nb1) % nb2, bz = b / (nb1 * nb2);
+    const int o1 = bx * BLK - G, o2 = by * BLK - G, o3 = bz * BLK - G;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t np = a.np;
+    const double inv_delta = a.g.inv_delta;
+    const double dt = a.dt;
+    T* wv = wbuf + warp * 48;
+    T* wd = wv + 24;
+    const T dtid = (T)(dt * inv_delta);
+
+    WeightEval<T, I, DEG, true> W;
+    W.init(table<T>(a), lane);
+    Lane<T, I, true> L;
+    L.init(lane);
+
+    for (int batch = j0; batch < j1; batch += PBA) {
+        const int nbat = min(PBA, j1 - batch);
+        // ---------------- P1 ----------------
+        double lam[3] = {0, 0, 0};
+        int id = 0;
+        if (tid < nbat) {
+            id = a.perm[batch + tid];
+            bool ok = true;
+            int c[3];
+            PRec<T> rec;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                double t;
+                ok &= split_axis(a.pos[ax * np + id], inv_delta, mask, c[ax], t);
+                rec.t[ax] = (T)t;
+                lam[ax] = a.lam_in[ax * np + id];
+            }
+            if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
+            const int r1 = (c[0] - o1) & mask, r2 = (c[1] - o2) & mask, r3 = (c[2] - o3) & mask;
+            const bool in = r1 >= LO && r1 <= RMAX && r2 >= LO && r2 <= RMAX && r3 >= LO && r3 <= RMAX;
+            const int rp = in ? pack_rel(r1, r2, r3) : -1;
+            if constexpr (sizeof(T) == 4) rec.relf = __int_as_float(rp);
+            else rec.relf = __longlong_as_double((long long)rp);
+            p_rec[tid] = rec;
+            p_cell[tid] = pack_cell(c[0], c[1], c[2]);
+        }
+        if (batch != j0) __syncthreads();   // the accumulator of the previous batch is flushed
+        load_halo<T, STORE, H, G, S2, S3, SC, 3>(halo, a.f, 0, 3, o1, o2, o3);
+        __syncthreads();
+        // ---------------- Q1: u(X), J(X), J(X*) ----------------
+        for (int q = warp; q < nbat; q += NW) {
+            const PRec<T> rec = p_rec[q];
+            int rp;
+            if constexpr (sizeof(T) == 4) rp = __float_as_int(rec.relf);
+            else rp = (int)__double_as_longlong(rec.relf);
+            const int r1 = rp & 255, r2 = (rp >> 8) & 255, r3 = (rp >> 16) & 255;
+            const int pc = p_cell[q];
+            const int c1 = pc & 1023, c2 = (pc >> 10) & 1023, c3 = (pc >> 20) & 1023;
+            if (rp >= 0) L.load(SL{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)});
+            else L.load(GlobalLd<T, STORE, I>{a.f, c1, c2, c3, 0, 2, mask});
+            W.eval(rec.t[0] - (T)0.5, rec.t[1] - (T)0.5, rec.t[2] - (T)0.5, wv, wd);
+            T acc[12];
+            L.contract(wv, wd, acc);
+            T m = reduce16(acc, lane);        // value v sits in lanes 2v and 2v + 1
+            const T k1[3] = {__shfl_sync(0xffffffffu, m, 0), __shfl_sync(0xffffffffu, m, 2),
+                             __shfl_sync(0xffffffffu, m, 4)};
+            const int v = lane >> 1;
+            if ((lane & 1) == 0 && v >= 3 && v < 12) p_jac[q * 18 + (v - 3)] = m * (T)inv_delta;
+            // stage-2 point, cell-relative: t* = t + dt k1 / delta
+            T ts[3] = {fma(dtid, k1[0], rec.t[0]), fma(dtid, k1[1], rec.t[1]), fma(dtid, k1[2], rec.t[2])};
+            int dc[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const T fl = floor(ts[ax]);
+                dc[ax] = (int)fl;
+                ts[ax] -= fl;
+            }
+            const int s1 = r1 + dc[0], s2 = r2 + dc[1], s3 = r3 + dc[2];
+            const bool in2 = rp >= 0 && s1 >= LO && s1 <= RMAX && s2 >= LO && s2 <= RMAX && s3 >= LO && s3 <= RMAX;
+            const int cs1 = (c1 + dc[0]) & mask, cs2 = (c2 + dc[1]) & mask, cs3 = (c3 + dc[2]) & mask;
+            if ((dc[0] | dc[1] | dc[2]) != 0 || rp < 0) {
+                if (in2) {
+                    L.load(SL{halo + (s3 - LO) * S3 + (s2 - LO) * S2 + (s1 - LO)});
+                } else {
+                    if (lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
+                    L.load(GlobalLd<T, STORE, I>{a.f, cs1, cs2, cs3, 0, 2, mask});
+                }
+            }
+            W.eval(ts[0] - (T)0.5, ts[1] - (T)0.5, ts[2] - (T)0.5, wv, wd);
+            L.contract(wv, wd, acc);
+            m = reduce16(acc, lane);
+            if ((lane & 1) == 0 && v >= 3 && v < 12) p_jac[q * 18 + 9 + (v - 3)] = m * (T)inv_delta;
+            if (lane == 0) {
+                PRec<T> r2c;
+                r2c.t[0] = ts[0];
+                r2c.t[1] = ts[1];
+                r2c.t[2] = ts[2];
+                const int rp2 = in2 ? pack_rel(s1, s2, s3) : -1;
+                if constexpr (sizeof(T) == 4) r2c.relf = __int_as_float(rp2);
+                else r2c.relf = __longlong_as_double((long long)rp2);
+                p_rec2[q] = r2c;
+                p_cell2[q] = pack_cell(cs1, cs2, cs3);
+            }
+        }
+        __syncthreads();
+        // ---------------- P2: lambda recurrence (float64) ----------------
+        if (tid < nbat) {
+            const T* Jx = p_jac + tid * 18;        // J(X)[k][j] at 3k + j
+            const T* Js = Jx + 9;                  // J(X*)
+            double ls[3], mu[3];
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) {
+                double s2 = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s2 += (double)Js[3 * k + jj] * lam[k];
+                ls[jj] = 0.5 * dt * s2;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) mu[k] = 0.5 * dt * lam[k] + dt * ls[k];
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) {
+                double s1 = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s1 += (double)Jx[3 * k + jj] * mu[k];
+                a.lam_out[jj * np + id] = lam[jj] + ls[jj] + s1;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                p_mu[tid * 6 + k] = (T)mu[k];
+                p_mu[tid * 6 + 3 + k] = (T)(0.5 * dt * lam[k]);
+            }
+        }
+        if (!a.gfield) {
+            __syncthreads();
+            continue;
+        }
+        // ---------------- Q2: W^T scatter ----------------
+        for (int e = tid; e < 3 * SC; e += NT) halo[e] = (T)0;
+        __syncthreads();
+        const int64_t NN3 = (int64_t)N * N * N;
+        for (int q = warp; q < nbat; q += NW) {
+#pragma unroll
+            for (int stage = 0; stage < 2; ++stage) {
+                const PRec<T> rec = stage == 0 ? p_rec[q] : p_rec2[q];
+                int rp;
+                if constexpr (sizeof(T) == 4) rp = __float_as_int(rec.relf);
+                else rp = (int)__double_as_longlong(rec.relf);
+                const T mu3[3] = {p_mu[q * 6 + 3 * stage + 0], p_mu[q * 6 + 3 * stage + 1],
+                                  p_mu[q * 6 + 3 * stage + 2]};
+                W.eval(rec.t[0] - (T)0.5, rec.t[1] - (T)0.5, rec.t[2] - (T)0.5, wv, wd);
+                if (rp >= 0) {
+                    T* base = halo + ((rp >> 16) & 255) * S3 - LO * S3 + ((rp >> 8) & 255) * S2 - LO * S2 +
+                              (rp & 255) - LO;
+                    L.scatter(wv, mu3, [&](int k, int a1, int a2, int a3, T val) {
+                        atomicAdd(base + k * SC + a3 * S3 + a2 * S2 + a1, val);
+                    });
+                } else {
+                    const int pc = stage == 0 ? p_cell[q] : p_cell2[q];
+                    const int c1 = pc & 1023, c2 = (pc >> 10) & 1023, c3 = (pc >> 20) & 1023;
+                    double* gf = a.gfield;
+                    L.scatter(wv, mu3, [&](int k, int a1, int a2, int a3, T val) {
+                        const int x1 = (c1 + a1 - LO) & mask, x2 = (c2 + a2 - LO) & mask, x3 = (c3 + a3 - LO) & mask;
+                        atomicAdd(gf + k * NN3 + ((int64_t)x3 * N + x2) * N + x1, (double)val);
+                    });
+                }
+            }
+        }
+        __syncthreads();
+        // flush the accumulator: one float64 atomic per touched halo node
+        for (int e = tid; e < 3 * H * H * H; e += NT) {
+            const int x = e % H, yz = e / H, y = yz % H, zk = yz / H, z = zk % H, k = zk / H;
+            const T val = halo[k * SC + z * S3 + y * S2 + x];
+            if (val != (T)0) {
+                const int64_t gi = ((int64_t)((o3 + z) & mask) * N + ((o2 + y) & mask)) * N + ((o1 + x) & mask);
+                atomicAdd(a.gfield + k * NN3 + gi, (double)val);
+            }
+        }
+    }
+}
+
+template <typename T, int I, int DEG, int STORE>
+cudaError_t launch_adjoint_t(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
+{
+    constexpr int H = BLK + I - 1 + 2;
+    constexpr size_t smem = AdjPlan<T, Layout<I, H>::SC>::total;
+    auto kern = k_adjoint<T, I, DEG, STORE>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (nblocks <= 0) return cudaSuccess;
+    kern<<<(unsigned)nblocks, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int I, int DEG>
+cudaError_t dispatch_adjoint(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
+{
+    if (a.f.storage == ST_F64) return launch_adjoint_t<double, I, DEG, ST_F64>(a, nblocks, st);
+    if (a.f.storage == ST_F32) return launch_adjoint_t<float, I, DEG, ST_F32>(a, nblocks, st);
+    return launch_adjoint_t<float, I, DEG, ST_BF16X2>(a, nblocks, st);
+}
+
+}  // namespace trk

@@ -106,9 +106,12 @@ struct Layout {
 // ---------------------------------------------------------------------------
 // Weight polynomials
 // ---------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ const CoefTable<T>& table(const BlockArgs& a);
-template <> __device__ __forceinline__ const CoefTable<float>& table<float>(const BlockArgs& a) { return a.cf; }
-template <> __device__ __forceinline__ const CoefTable<double>& table<double>(const BlockArgs& a) { return a.cd; }
+template <typename T, class A>
+__device__ __forceinline__ const CoefTable<T>& table(const A& a)
+{
+    if constexpr (sizeof(T) == 4) return a.cf;
+    else return a.cd;
+}
 
 template <typename T, int DEG>
 struct Row {
@@ -237,6 +240,22 @@ struct Lane<T, 8, D> {
 #pragma unroll
                 for (int i3 = 0; i3 < 8; ++i3) f[k][h][i3] = ld(k, i1, j + 4 * h, i3);
     }
+    // transpose of the gather: add w(node) mu_k into every node this lane gathers
+    template <class ADD>
+    __device__ __forceinline__ void scatter(const T* wv, const T (&mu)[3], const ADD& add) const
+    {
+        const T w1 = wv[i1];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const T a12 = w1 * wv[8 + j + 4 * h];
+#pragma unroll
+            for (int i3 = 0; i3 < 8; ++i3) {
+                const T w = a12 * wv[16 + i3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) add(k, i1, j + 4 * h, i3, w * mu[k]);
+            }
+        }
+    }
     __device__ __forceinline__ void contract(const T* wv, const T* wd, T (&acc)[12]) const
     {
         T w3[8], dw3[8];
@@ -304,6 +323,28 @@ struct Lane<T, 6, D> {
             f[k][7] = ld(k, i1, 5, 5);
         }
     }
+    template <class ADD>
+    __device__ __forceinline__ void scatter(const T* wv, const T (&mu)[3], const ADD& add) const
+    {
+        const T w1 = wv[i1], w25 = wv[13];
+        if (act) {
+            const T a12 = w1 * wv[8 + j];
+#pragma unroll
+            for (int i3 = 0; i3 < 6; ++i3) {
+                const T w = a12 * wv[16 + i3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) add(k, i1, j, i3, w * mu[k]);
+            }
+            const T wb = w1 * w25 * wv[16 + j];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) add(k, i1, 5, j, wb * mu[k]);
+        }
+        if (actc) {
+            const T wc = w1 * w25 * wv[21];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) add(k, i1, 5, 5, wc * mu[k]);
+        }
+    }
     __device__ __forceinline__ void contract(const T* wv, const T* wd, T (&acc)[12]) const
     {
         T w3[6], dw3[6];
@@ -364,6 +405,17 @@ struct Lane<T, 4, D> {
         for (int k = 0; k < 3; ++k) {
             f[k][0] = ld(k, i1, i2, p);
             f[k][1] = ld(k, i1, i2, p + 2);
+        }
+    }
+    template <class ADD>
+    __device__ __forceinline__ void scatter(const T* wv, const T (&mu)[3], const ADD& add) const
+    {
+        const T a12 = wv[i1] * wv[8 + i2];
+        const T wa = a12 * wv[16 + p], wb = a12 * wv[18 + p];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            add(k, i1, i2, p, wa * mu[k]);
+            add(k, i1, i2, p + 2, wb * mu[k]);
         }
     }
     __device__ __forceinline__ void contract(const T* wv, const T* wd, T (&acc)[12]) const

@@ -85,6 +85,23 @@ struct BlockArgs {
     int* flags;
 };
 
+// Arguments of the adjoint block kernel (one RK2 step, backwards).
+struct AdjArgs {
+    GridGeom g;
+    FieldView f;
+    CoefTable<float> cf;
+    CoefTable<double> cd;
+    int64_t np;
+    const int32_t* offsets;   // [nblocks + 1] of the binned positions
+    const int32_t* perm;      // sorted position j -> particle index
+    const double* pos;        // [3][np] X at the start of the step, particle order
+    const double* lam_in;     // [3][np] dLoss/dX' (particle order)
+    double* lam_out;          // [3][np] dLoss/dX   (particle order)
+    double* gfield;           // [3][N^3] dLoss/dfield (dense, added into) or null
+    double dt;
+    int* flags;
+};
+
 // ---------------------------------------------------------------------------
 // Cell split (Sec. 2.2 steps 1-3), bit-exact with the float64 reference:
 //   g = X * fl(N/L), c0 = floor(g), t = g - c0, c = c0 mod N.
@@ -133,6 +150,10 @@ cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id
 
 // Fill the ghost-padded storage from a dense field src[C][N][N][N] (periodic ghosts).
 cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int C, int N, void* dst, cudaStream_t st);
+
+cudaError_t launch_adjoint_i4(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
+cudaError_t launch_adjoint_i6(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
+cudaError_t launch_adjoint_i8(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 
 // Sets the thread-local message returned by tracker_last_error().
 void set_error_message(const char* msg);

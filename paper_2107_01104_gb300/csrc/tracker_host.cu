@@ -104,6 +104,9 @@ struct tracker {
     float* rhs_s[2] = {nullptr, nullptr};
     int* d_flags = nullptr;
     int64_t launches = 0;
+    // adjoint scratch: checkpoints, one segment of trajectory, lambda ping-pong
+    size_t adj_bytes = 0;
+    double* adj_buf = nullptr;
     // instrumentation: event pairs per kernel class
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -347,6 +350,7 @@ int tracker_destroy(tracker* t)
         dev_free(t->rhs_s[i]);
     }
     dev_free(t->d_flags);
+    dev_free(t->adj_buf);
     for (cudaEvent_t e : t->ev_pool) cudaEventDestroy(e);
     delete t;
     return TRK_OK;
@@ -556,6 +560,17 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     return TRK_OK;
 }
 
+static cudaError_t launch_adjoint(tracker* t, const AdjArgs& a)
+{
+    ProfScope ps(t, PROF_STEP);
+    t->launches += 1;
+    switch (t->I) {
+        case 4: return launch_adjoint_i4(a, t->nblocks, t->deg_hi, t->stream);
+        case 6: return launch_adjoint_i6(a, t->nblocks, t->deg_hi, t->stream);
+        default: return launch_adjoint_i8(a, t->nblocks, t->deg_hi, t->stream);
+    }
+}
+
 int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double dt, int steps, int history_valid)
 {
     (void)nsets;
@@ -570,16 +585,83 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
 int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* lambdaT, double dt, int steps,
                     int ckpt_every, double* grad_pos0, double* grad_field)
 {
-    (void)np;
-    (void)pos0;
-    (void)lambdaT;
-    (void)dt;
-    (void)steps;
-    (void)ckpt_every;
-    (void)grad_pos0;
-    (void)grad_field;
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
-    return fail(TRK_EINVAL, "tracker_adjoint: not available in this build");
+    int rc = check_np(np);
+    if (rc) return rc;
+    if (!t->field) return fail(TRK_ENOFIELD, "no field set");
+    if (t->C != 3) return fail(TRK_EINVAL, "the adjoint needs a 3-component field (C=%d)", t->C);
+    if (!std::isfinite(dt)) return fail(TRK_EINVAL, "dt must be finite");
+    if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
+    if (ckpt_every < 1) return fail(TRK_EINVAL, "ckpt_every=%d < 1", ckpt_every);
+    if (np > 0 && (!pos0 || !lambdaT || !grad_pos0)) return fail(TRK_EINVAL, "pos0, lambdaT and grad_pos0 must not be NULL");
+    if ((rc = check_block_kernel_shape(t))) return rc;
+    if (np == 0) return TRK_OK;
+    const size_t vec = (size_t)3 * np;                 // doubles per position / lambda array
+    if (steps == 0) {
+        CUDA_TRY(cudaMemcpyAsync(grad_pos0, lambdaT, vec * 8, cudaMemcpyDeviceToDevice, t->stream));
+        return TRK_OK;
+    }
+    if ((rc = ensure_sort(t, np))) return rc;
+    if ((rc = ensure_state(t, np))) return rc;
+    const int K = std::min(ckpt_every, steps);
+    const int nseg = (steps + K - 1) / K;
+    // layout: nseg checkpoints | K segment states | 2 lambdas
+    const size_t need = (size_t)(nseg + K + 2) * vec * 8;
+    if (need > t->adj_bytes) {
+        dev_free(t->adj_buf);
+        t->adj_buf = nullptr;
+        t->adj_bytes = 0;
+        if (dev_alloc(&t->adj_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TRK_ENOMEM, "cannot allocate adjoint checkpoints (%zu bytes)", need);
+        }
+        t->adj_bytes = need;
+    }
+    double* ckpt = t->adj_buf;
+    double* seg = ckpt + (size_t)nseg * vec;
+    double* lam[2] = {seg + (size_t)K * vec, seg + (size_t)(K + 1) * vec};
+    // forward sweep keeping a checkpoint every K steps
+    CUDA_TRY(cudaMemcpyAsync(ckpt, pos0, vec * 8, cudaMemcpyDeviceToDevice, t->stream));
+    for (int sg = 1; sg < nseg; ++sg) {
+        double* dst = ckpt + (size_t)sg * vec;
+        CUDA_TRY(cudaMemcpyAsync(dst, ckpt + (size_t)(sg - 1) * vec, vec * 8, cudaMemcpyDeviceToDevice, t->stream));
+        if ((rc = tracker_advance(t, np, dst, nullptr, dt, K, TRK_RK2, 0))) return rc;
+    }
+    // backward sweep: recompute each segment from its checkpoint, then step back through it
+    CUDA_TRY(cudaMemcpyAsync(lam[0], lambdaT, vec * 8, cudaMemcpyDeviceToDevice, t->stream));
+    int cur = 0;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int s0 = sg * K, s1 = std::min(steps, s0 + K);
+        CUDA_TRY(cudaMemcpyAsync(seg, ckpt + (size_t)sg * vec, vec * 8, cudaMemcpyDeviceToDevice, t->stream));
+        for (int i = 1; i < s1 - s0; ++i) {
+            double* dst = seg + (size_t)i * vec;
+            CUDA_TRY(cudaMemcpyAsync(dst, seg + (size_t)(i - 1) * vec, vec * 8, cudaMemcpyDeviceToDevice, t->stream));
+            if ((rc = tracker_advance(t, np, dst, nullptr, dt, 1, TRK_RK2, 0))) return rc;
+        }
+        for (int i = s1 - s0 - 1; i >= 0; --i) {
+            const double* X = seg + (size_t)i * vec;
+            if ((rc = bin_into(t, np, X, t->keys, t->perm, t->offsets))) return rc;
+            AdjArgs a{};
+            const BlockArgs b = base_args(t);
+            a.g = b.g;
+            a.f = b.f;
+            a.cf = b.cf;
+            a.cd = b.cd;
+            a.np = np;
+            a.offsets = t->offsets;
+            a.perm = t->perm;
+            a.pos = X;
+            a.lam_in = lam[cur];
+            a.lam_out = lam[cur ^ 1];
+            a.gfield = grad_field;
+            a.dt = dt;
+            a.flags = t->d_flags;
+            CUDA_TRY(launch_adjoint(t, a));
+            cur ^= 1;
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(grad_pos0, lam[cur], vec * 8, cudaMemcpyDeviceToDevice, t->stream));
+    return TRK_OK;
 }
 
 }  // extern "C"
