@@ -254,6 +254,13 @@ unsigned grid_for(int64_t n, int threads) { return (unsigned)ceil_div(n > 0 ? n 
 
 }  // namespace
 
+size_t scan_scratch_bytes_u32(int64_t len) { return scan_scratch_bytes(len); }
+
+cudaError_t scan_exclusive_u32(uint32_t* data, int64_t len, uint32_t* scratch, cudaStream_t st, int64_t* launches)
+{
+    return scan_exclusive(data, len, scratch, st, launches);
+}
+
 cudaError_t launch_keys(const GridGeom& g, int64_t np, const double* pos, uint32_t* keys, int* flags, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;

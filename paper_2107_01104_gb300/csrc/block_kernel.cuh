@@ -592,11 +592,17 @@ struct SmemPlan {
 // ---------------------------------------------------------------------------
 // The block kernel.
 // ---------------------------------------------------------------------------
+// Processes the sorted particles [j0, j1) of cell block b.  use_halo = false
+// skips the halo staging and gathers every stencil from global memory (the
+// direct path for sparse particle sets, where a halo would serve one or two
+// particles).  Must be called by all threads of the CTA.
 template <typename T, int I, int DEG, int MODE, int STORE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_block(const __grid_constant__ BlockArgs a)
+__device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0, int j1, bool use_halo,
+                                              unsigned char* smem_raw)
 {
-    constexpr bool IS_STEP = (MODE == MODE_RK2 || MODE == MODE_AB2);
-    constexpr bool D = (MODE == MODE_INTERP_DERIV);
+    constexpr bool IS_AB2 = (MODE == MODE_AB2 || MODE == MODE_AB2_D);
+    constexpr bool IS_STEP = (MODE == MODE_RK2 || IS_AB2);
+    constexpr bool D = (MODE == MODE_INTERP_DERIV || MODE == MODE_AB2_D);
     constexpr int MARGIN = (MODE == MODE_RK2) ? 1 : 0;     // halo margin for the stage-2 point
     constexpr int H = BLK + I - 1 + 2 * MARGIN;
     constexpr int G = I / 2 - 1 + MARGIN;                   // halo origin = block origin - G
@@ -607,15 +613,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_b
     using SL = SmemLd<T, S2, S3, SC>;
 
     using SM = SmemPlan<T, SC>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     T* halo = reinterpret_cast<T*>(smem_raw);                               // [3][SC]
     PRec<T>* p_rec = reinterpret_cast<PRec<T>*>(smem_raw + SM::rec);        // [PB]
     T* p_k = reinterpret_cast<T*>(smem_raw + SM::k);                        // [6][PB]: k1 (3), k2 (3)
     T* wbuf = reinterpret_cast<T*>(smem_raw + SM::w);                       // [NW][2][24] weights
     int* p_cell = reinterpret_cast<int*>(smem_raw + SM::cell);              // [PB]
 
-    const int b = blockIdx.x;
-    const int j0 = a.offsets[b], j1 = a.offsets[b + 1];
     if (j0 >= j1) return;
 
     const int mask = a.g.mask;
@@ -662,20 +665,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_b
             const int r1 = (c[0] - o1) & mask, r2 = (c[1] - o2) & mask, r3 = (c[2] - o3) & mask;
             // a particle always lies in its own block; the guard only keeps a
             // corrupted permutation from indexing outside the staged halo
-            const bool in = r1 >= LO && r1 <= RMAX && r2 >= LO && r2 <= RMAX && r3 >= LO && r3 <= RMAX;
+            const bool in = use_halo && r1 >= LO && r1 <= RMAX && r2 >= LO && r2 <= RMAX && r3 >= LO &&
+                            r3 <= RMAX;
             const int rp = in ? pack_rel(r1, r2, r3) : -1;
             if constexpr (sizeof(T) == 4) rec.relf = __int_as_float(rp);
             else rec.relf = __longlong_as_double((long long)rp);
             p_rec[tid] = rec;
             p_cell[tid] = pack_cell(c[0], c[1], c[2]);
-            if (MODE == MODE_AB2 && a.history_valid) {
+            if (IS_AB2 && a.history_valid) {
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) hr[ax] = a.rhs_in[ax * np + src];
             }
         }
         // ---------------- Q: interpolation ----------------
         for (int ch = 0; ch < nchunks; ++ch) {
-            if (batch == j0 || nchunks > 1) {
+            if (use_halo && (batch == j0 || nchunks > 1)) {
                 if (ch > 0 || batch != j0) __syncthreads();   // previous readers of the halo are done
                 if constexpr (IS_STEP)
                     load_halo<T, STORE, H, G, S2, S3, SC, 3>(halo, a.f, 0, 3, o1, o2, o3);
@@ -737,7 +741,22 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_b
                     }
                 } else if constexpr (MODE == MODE_AB2) {
                     const T m = reduce4(acc, lane);
-                    if (writer) p_k[rcomp * PB + q] = m;
+                    if (writer) {
+                        p_k[rcomp * PB + q] = m;
+                        if (a.out) {   // per-step output u(X) in caller order
+                            const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
+                            reinterpret_cast<float*>(a.out)[(int64_t)rcomp * np + qid] = (float)m;
+                        }
+                    }
+                } else if constexpr (MODE == MODE_AB2_D) {
+                    // value v sits in lanes 2v, 2v + 1: u_k at v = k, d u_k / d t_j at v = 3 + 3k + j
+                    const T m = reduce16(acc, lane);
+                    const int v = lane >> 1;
+                    if ((lane & 1) == 0 && v < 3) p_k[v * PB + q] = m;
+                    if ((lane & 1) == 0 && v >= 3 && v < 12 && a.out) {
+                        const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
+                        reinterpret_cast<float*>(a.out)[(int64_t)(v - 3) * np + qid] = (float)((double)m * inv_delta);
+                    }
                 } else if constexpr (MODE == MODE_INTERP) {
                     const T m = reduce4(acc, lane);
                     const int kc = min(3, a.f.C - 3 * ch);
@@ -778,7 +797,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_b
                     if constexpr (MODE == MODE_RK2) {
                         const double k2 = (double)p_k[(3 + ax) * PB + tid];
                         xn = X[ax] + (0.5 * a.dt) * (k1 + k2);
-                    } else {
+                    } else {   // AB2
                         const double inc = a.history_valid ? (1.5 * k1 - 0.5 * (double)hr[ax]) : k1;
                         xn = X[ax] + a.dt * inc;
                         a.rhs_out[ax * np + j] = (float)k1;
@@ -794,6 +813,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_b
             __syncthreads();
         }
     }
+}
+
+template <typename T, int I, int DEG, int MODE, int STORE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_block(const __grid_constant__ BlockArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int b = blockIdx.x;
+    process_block<T, I, DEG, MODE, STORE>(a, b, a.offsets[b], a.offsets[b + 1], true, smem_raw);
 }
 
 template <typename T, int I, int MODE>

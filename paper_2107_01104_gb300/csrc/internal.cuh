@@ -20,7 +20,8 @@ enum { FLAG_NONFINITE = 0, FLAG_CFL = 1, NUM_FLAGS = 4 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16X2 = 2 };
 
 // Block-kernel modes.
-enum { MODE_INTERP = 0, MODE_INTERP_DERIV = 1, MODE_RK2 = 2, MODE_AB2 = 3 };
+// MODE_AB2_D: AB2 step that also writes du_k/dX_j at the step's start.
+enum { MODE_INTERP = 0, MODE_INTERP_DERIV = 1, MODE_RK2 = 2, MODE_AB2 = 3, MODE_AB2_D = 4 };
 
 constexpr int BLK = 8;        // cell-block edge used by the block kernels
 constexpr int LBLK = 3;       // log2(BLK)
@@ -102,6 +103,15 @@ struct AdjArgs {
     int* flags;
 };
 
+// One particle set of a batched step, resident in device memory.
+struct BatchSet {
+    BlockArgs a;              // set's step arguments (field, weights, state buffers)
+    const int32_t* list;      // non-empty blocks in key order (halo path)
+    const int32_t* count;     // number of non-empty blocks (device, halo path)
+    int n_items;              // number of 256-particle chunks (direct path)
+    int I, deg_hi, deriv, direct;
+};
+
 // ---------------------------------------------------------------------------
 // Cell split (Sec. 2.2 steps 1-3), bit-exact with the float64 reference:
 //   g = X * fl(N/L), c0 = floor(g), t = g - c0, c = c0 mod N.
@@ -154,6 +164,18 @@ cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int 
 cudaError_t launch_adjoint_i4(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_adjoint_i6(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_adjoint_i8(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
+
+// Exclusive scan of a uint32 array in place; scratch is scan_scratch_bytes_u32(len).
+size_t scan_scratch_bytes_u32(int64_t len);
+cudaError_t scan_exclusive_u32(uint32_t* data, int64_t len, uint32_t* scratch, cudaStream_t st, int64_t* launches);
+
+// Compacted list of the non-empty blocks (in key order) and its length.
+size_t nonempty_scratch_bytes(int64_t nblocks);
+cudaError_t launch_nonempty_list(const int32_t* offsets, int64_t nblocks, int32_t* list, int32_t* count, void* scratch,
+                                 cudaStream_t st, int64_t* launches);
+
+// One persistent launch over all sets (float32 or split-bf16 storage); grid = 2 CTAs per SM.
+cudaError_t launch_batched(int storage, const BatchSet* sets, int nsets, int* ctr, int nsm, cudaStream_t st);
 
 // Sets the thread-local message returned by tracker_last_error().
 void set_error_message(const char* msg);

@@ -74,6 +74,34 @@ void dev_free(void* p)
     if (p) cudaFree(p);
 }
 
+constexpr int PB_HOST = 256;   // particles per direct-path work item (the block kernels' batch)
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t key = 0;
+    int64_t kernels = 0;
+};
+
+// Per-set buffers of tracker_advance_batched.
+struct SetState {
+    int64_t cap = 0;
+    uint32_t* keys = nullptr;
+    uint32_t* keys_sorted = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* offsets = nullptr;
+    int32_t* list = nullptr;
+    int32_t* count = nullptr;
+    double* pos_s[2] = {nullptr, nullptr};
+    int32_t* id_s[2] = {nullptr, nullptr};
+    float* rhs_s[2] = {nullptr, nullptr};
+};
+
+uint64_t mix(uint64_t h, uint64_t v)
+{
+    h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+    return h;
+}
+
 }  // namespace
 
 void trk::set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
@@ -107,6 +135,20 @@ struct tracker {
     // adjoint scratch: checkpoints, one segment of trajectory, lambda ping-pong
     size_t adj_bytes = 0;
     double* adj_buf = nullptr;
+    // CUDA-graph replay of step pairs, on a tracker-owned stream joined to the caller's
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    uint64_t gen = 1;                 // bumped whenever a buffer baked into a graph is reallocated
+    GraphCache adv_graph, batch_graph;
+    // batched sets
+    std::vector<SetState> sets;
+    void* ne_scratch = nullptr;       // non-empty-list scratch
+    int64_t ne_cap = 0;
+    BatchSet* d_desc = nullptr;       // [3][nsets] descriptors: first step, parity 0, parity 1
+    int* d_ctr = nullptr;             // [nsets] work counters
+    int desc_cap = 0;
+    std::vector<std::pair<uint64_t, int>> tune_cache;   // set signature -> direct path?
+    int nsm = 0;
     // instrumentation: event pairs per kernel class
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -165,6 +207,7 @@ int set_geometry(tracker* t, int bx, int by, int bz)
     t->key_bits = ilog2(t->nblocks);
     dev_free(t->offsets);
     t->offsets = nullptr;
+    t->gen += 1;
     CUDA_TRY(dev_alloc(&t->offsets, (size_t)(t->nblocks + 1) * sizeof(int32_t)));
     return TRK_OK;
 }
@@ -172,6 +215,7 @@ int set_geometry(tracker* t, int bx, int by, int bz)
 int ensure_sort(tracker* t, int64_t np)
 {
     if (np <= t->sort_cap) return TRK_OK;
+    t->gen += 1;
     dev_free(t->sort_scratch);
     dev_free(t->keys);
     dev_free(t->keys_sorted);
@@ -193,6 +237,7 @@ int ensure_sort(tracker* t, int64_t np)
 int ensure_state(tracker* t, int64_t np)
 {
     if (np <= t->state_cap) return TRK_OK;
+    t->gen += 1;
     for (int i = 0; i < 2; ++i) {
         dev_free(t->pos_s[i]);
         dev_free(t->id_s[i]);
@@ -282,6 +327,94 @@ BlockArgs base_args(tracker* t)
     return a;
 }
 
+// Runs body() (which issues the work of a step pair on t->stream) as a CUDA
+// graph on the tracker's own stream, capturing it the first time and whenever
+// key changes, then replaying it reps times.  The caller's stream and the
+// graph stream are joined with events both ways.
+template <class F>
+int replay_graph(tracker* t, GraphCache& gc, uint64_t key, int reps, F&& body)
+{
+    if (reps <= 0) return TRK_OK;
+    cudaStream_t user = t->stream;
+    CUDA_TRY(cudaEventRecord(t->gev[0], user));
+    CUDA_TRY(cudaStreamWaitEvent(t->gstream, t->gev[0], 0));
+    if (!gc.exec || gc.key != key) {
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        gc.exec = nullptr;
+        const int64_t l0 = t->launches;
+        t->stream = t->gstream;
+        cudaError_t e = cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal);
+        int rc = e == cudaSuccess ? body() : fail(TRK_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(t->gstream, &g) : cudaSuccess;
+        t->stream = user;
+        if (rc != TRK_OK || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc != TRK_OK ? rc : fail(TRK_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+        }
+        e = cudaGraphInstantiate(&gc.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            gc.exec = nullptr;
+            return fail(TRK_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        gc.kernels = t->launches - l0;
+        t->launches = l0;
+        gc.key = key;
+    }
+    for (int r = 0; r < reps; ++r) {
+        CUDA_TRY(cudaGraphLaunch(gc.exec, t->gstream));
+        t->launches += gc.kernels;
+    }
+    CUDA_TRY(cudaEventRecord(t->gev[1], t->gstream));
+    CUDA_TRY(cudaStreamWaitEvent(user, t->gev[1], 0));
+    return TRK_OK;
+}
+
+// One RK2/AB2 step of tracker_advance: re-bin, then the fused block kernel.
+// first: read the caller's arrays (identity ids, caller history flag).
+int advance_step(tracker* t, int64_t np, int mode, double dt, int cur, bool first, const double* pos,
+                 const float* rhs, int history_valid)
+{
+    {
+        ProfScope ps(t, PROF_BIN);
+        CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
+                            &t->launches));
+        CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
+        t->launches += 1;
+    }
+    BlockArgs a = base_args(t);
+    a.np = np;
+    a.perm = t->perm;
+    a.dt = dt;
+    const int nxt = cur ^ 1;
+    if (first) {
+        a.pos_in = pos;
+        a.id_in = nullptr;
+        a.rhs_in = rhs;
+        a.history_valid = history_valid;
+    } else {
+        a.pos_in = t->pos_s[cur];
+        a.id_in = t->id_s[cur];
+        a.rhs_in = t->rhs_s[cur];
+        a.history_valid = (mode == MODE_AB2) ? 1 : 0;
+    }
+    a.pos_out = t->pos_s[nxt];
+    a.id_out = t->id_s[nxt];
+    a.rhs_out = t->rhs_s[nxt];
+    a.key_out = t->keys;
+    CUDA_TRY(launch_block(t, mode, a));
+    return TRK_OK;
+}
+
+uint64_t dbits(double x)
+{
+    uint64_t u;
+    memcpy(&u, &x, 8);
+    return u;
+}
+
 }  // namespace
 
 extern "C" {
@@ -325,6 +458,15 @@ int tracker_create(tracker** out, int N, double L, int family, int I, int m, int
         rc = fail(TRK_ENOMEM, "cannot allocate device flags");
     if (rc == TRK_OK && cudaMemset(t->d_flags, 0, NUM_FLAGS * sizeof(int)) != cudaSuccess)
         rc = fail(TRK_ECUDA, "cudaMemset flags failed");
+    if (rc == TRK_OK && (cudaStreamCreateWithFlags(&t->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&t->gev[0], cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&t->gev[1], cudaEventDisableTiming) != cudaSuccess))
+        rc = fail(TRK_ECUDA, "cannot create the graph stream");
+    if (rc == TRK_OK) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (rc != TRK_OK) {
         tracker_destroy(t);
         return rc;
@@ -349,8 +491,23 @@ int tracker_destroy(tracker* t)
         dev_free(t->id_s[i]);
         dev_free(t->rhs_s[i]);
     }
+    if (t->gstream) cudaStreamSynchronize(t->gstream);
     dev_free(t->d_flags);
     dev_free(t->adj_buf);
+    if (t->adv_graph.exec) cudaGraphExecDestroy(t->adv_graph.exec);
+    if (t->batch_graph.exec) cudaGraphExecDestroy(t->batch_graph.exec);
+    for (SetState& ss : t->sets) {
+        for (void* p : {(void*)ss.keys, (void*)ss.keys_sorted, (void*)ss.perm, (void*)ss.offsets, (void*)ss.list,
+                        (void*)ss.count, (void*)ss.pos_s[0], (void*)ss.pos_s[1], (void*)ss.id_s[0], (void*)ss.id_s[1],
+                        (void*)ss.rhs_s[0], (void*)ss.rhs_s[1]})
+            dev_free(p);
+    }
+    dev_free(t->ne_scratch);
+    dev_free(t->d_desc);
+    dev_free(t->d_ctr);
+    if (t->gev[0]) cudaEventDestroy(t->gev[0]);
+    if (t->gev[1]) cudaEventDestroy(t->gev[1]);
+    if (t->gstream) cudaStreamDestroy(t->gstream);
     for (cudaEvent_t e : t->ev_pool) cudaEventDestroy(e);
     delete t;
     return TRK_OK;
@@ -518,37 +675,24 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
         CUDA_TRY(launch_keys(t->g, np, pos, t->keys, t->d_flags, t->stream));
         t->launches += 1;
     }
-    int cur = 0;
-    for (int s = 0; s < steps; ++s) {
-        {
-            ProfScope ps(t, PROF_BIN);
-            CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
-                                &t->launches));
-            CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
-            t->launches += 1;
-        }
-        BlockArgs a = base_args(t);
-        a.np = np;
-        a.perm = t->perm;
-        a.dt = dt;
-        const int nxt = cur ^ 1;
-        if (s == 0) {
-            a.pos_in = pos;
-            a.id_in = nullptr;
-            a.rhs_in = rhs;
-            a.history_valid = history_valid;
-        } else {
-            a.pos_in = t->pos_s[cur];
-            a.id_in = t->id_s[cur];
-            a.rhs_in = t->rhs_s[cur];
-            a.history_valid = (scheme == TRK_AB2) ? 1 : 0;
-        }
-        a.pos_out = t->pos_s[nxt];
-        a.id_out = t->id_s[nxt];
-        a.rhs_out = t->rhs_s[nxt];
-        a.key_out = t->keys;
-        CUDA_TRY(launch_block(t, mode, a));
-        cur = nxt;
+    // the first step reads the caller's arrays; the others ping-pong between
+    // the tracker's sorted state buffers, replayed as a two-step CUDA graph
+    if ((rc = advance_step(t, np, mode, dt, 0, true, pos, rhs, history_valid))) return rc;
+    int cur = 1;
+    int rest = steps - 1;
+    if (!t->prof && rest >= 2) {
+        uint64_t key = mix(mix(mix(mix(0, (uint64_t)np), (uint64_t)mode), t->gen), dbits(dt));
+        key = mix(key, (uint64_t)(uintptr_t)t->field);
+        rc = replay_graph(t, t->adv_graph, key, rest / 2, [&]() {
+            int r = advance_step(t, np, mode, dt, 1, false, nullptr, nullptr, 1);
+            return r ? r : advance_step(t, np, mode, dt, 0, false, nullptr, nullptr, 1);
+        });
+        if (rc) return rc;
+        rest -= 2 * (rest / 2);
+    }
+    for (; rest > 0; --rest) {
+        if ((rc = advance_step(t, np, mode, dt, cur, false, nullptr, nullptr, 1))) return rc;
+        cur ^= 1;
     }
     ProfScope ps(t, PROF_OTHER);
     CUDA_TRY(launch_unpermute_pos(np, t->pos_s[cur], t->id_s[cur], pos, t->stream));
@@ -571,15 +715,248 @@ static cudaError_t launch_adjoint(tracker* t, const AdjArgs& a)
     }
 }
 
+static int ensure_set(tracker* t, SetState& ss, int64_t np)
+{
+    if (np <= ss.cap) return TRK_OK;
+    t->gen += 1;
+    for (void* p : {(void*)ss.keys, (void*)ss.keys_sorted, (void*)ss.perm, (void*)ss.offsets, (void*)ss.list,
+                    (void*)ss.count, (void*)ss.pos_s[0], (void*)ss.pos_s[1], (void*)ss.id_s[0], (void*)ss.id_s[1],
+                    (void*)ss.rhs_s[0], (void*)ss.rhs_s[1]})
+        dev_free(p);
+    ss = SetState{};
+    bool ok = dev_alloc(&ss.keys, (size_t)np * 4) == cudaSuccess && dev_alloc(&ss.keys_sorted, (size_t)np * 4) == cudaSuccess &&
+              dev_alloc(&ss.perm, (size_t)np * 4) == cudaSuccess &&
+              dev_alloc(&ss.offsets, (size_t)(t->nblocks + 1) * 4) == cudaSuccess &&
+              dev_alloc(&ss.list, (size_t)t->nblocks * 4) == cudaSuccess && dev_alloc(&ss.count, 4) == cudaSuccess;
+    for (int i = 0; i < 2 && ok; ++i)
+        ok = dev_alloc(&ss.pos_s[i], (size_t)np * 24) == cudaSuccess && dev_alloc(&ss.id_s[i], (size_t)np * 4) == cudaSuccess &&
+             dev_alloc(&ss.rhs_s[i], (size_t)np * 12) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return fail(TRK_ENOMEM, "cannot allocate the buffers of a particle set (%lld particles)", (long long)np);
+    }
+    ss.cap = np;
+    return TRK_OK;
+}
+
+// Re-binning of one set: sorted keys, permutation, offsets, and (halo path) the non-empty block list.
+static int bin_set(tracker* t, SetState& ss, int64_t np, bool direct)
+{
+    ProfScope ps(t, PROF_BIN);
+    CUDA_TRY(radix_sort(ss.keys, np, t->key_bits, ss.keys_sorted, ss.perm, t->sort_scratch, t->stream, &t->launches));
+    CUDA_TRY(launch_offsets(ss.keys_sorted, np, t->nblocks, ss.offsets, t->stream));
+    t->launches += 1;
+    if (!direct) CUDA_TRY(launch_nonempty_list(ss.offsets, t->nblocks, ss.list, ss.count, t->ne_scratch, t->stream,
+                                               &t->launches));
+    return TRK_OK;
+}
+
+static int batched_launch(tracker* t, const BatchSet* d_desc, int nsets)
+{
+    ProfScope ps(t, PROF_STEP);
+    CUDA_TRY(cudaMemsetAsync(t->d_ctr, 0, (size_t)nsets * sizeof(int), t->stream));
+    CUDA_TRY(launch_batched(t->storage, d_desc, nsets, t->d_ctr, t->nsm, t->stream));
+    t->launches += 1;
+    return TRK_OK;
+}
+
 int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double dt, int steps, int history_valid)
 {
-    (void)nsets;
-    (void)sets;
-    (void)dt;
-    (void)steps;
-    (void)history_valid;
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
-    return fail(TRK_EINVAL, "tracker_advance_batched: not available in this build");
+    if (nsets < 0 || (nsets > 0 && !sets)) return fail(TRK_EINVAL, "bad set list");
+    if (!t->field) return fail(TRK_ENOFIELD, "no field set");
+    if (t->C != 3) return fail(TRK_EINVAL, "batched advection needs a 3-component field (C=%d)", t->C);
+    if (t->storage != TRK_F32 && t->storage != TRK_BF16X2)
+        return fail(TRK_EINVAL, "batched advection runs on float32 or split-bf16 field storage");
+    if (!std::isfinite(dt)) return fail(TRK_EINVAL, "dt must be finite");
+    if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
+    int rc = check_block_kernel_shape(t);
+    if (rc) return rc;
+    std::vector<int> tabs(nsets);
+    int64_t npmax = 0;
+    for (int s = 0; s < nsets; ++s) {
+        const trk_set& S = sets[s];
+        if ((rc = check_np(S.np))) return rc;
+        if (S.np > 0 && (!S.pos || !S.rhs)) return fail(TRK_EINVAL, "set %d: pos and rhs must not be NULL", s);
+        if (S.I != 4 && S.I != 6 && S.I != 8) return fail(TRK_EINVAL, "set %d: I=%d unsupported", s, S.I);
+        if (S.family != TRK_LAGRANGE && S.family != TRK_SPLINE) return fail(TRK_EINVAL, "set %d: bad family", s);
+        if (S.family == TRK_SPLINE && (S.m < 0 || S.m > S.I / 2)) return fail(TRK_EINVAL, "set %d: bad m=%d", s, S.m);
+        if (S.deriv != 0 && S.deriv != 1) return fail(TRK_EINVAL, "set %d: deriv must be 0 or 1", s);
+        tabs[s] = find_table(S.family, S.I, S.family == TRK_LAGRANGE ? 0 : S.m);
+        if (tabs[s] < 0) return fail(TRK_EINVAL, "set %d: no coefficient table", s);
+        npmax = std::max(npmax, S.np);
+    }
+    if (nsets == 0 || steps == 0 || npmax == 0) return TRK_OK;
+    if ((rc = ensure_sort(t, npmax))) return rc;
+    if ((int)t->sets.size() < nsets) t->sets.resize(nsets);
+    for (int s = 0; s < nsets; ++s)
+        if ((rc = ensure_set(t, t->sets[s], std::max<int64_t>(sets[s].np, 1)))) return rc;
+    if (t->ne_cap < t->nblocks) {
+        dev_free(t->ne_scratch);
+        t->ne_scratch = nullptr;
+        t->gen += 1;
+        if (dev_alloc(&t->ne_scratch, nonempty_scratch_bytes(t->nblocks)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TRK_ENOMEM, "cannot allocate the block-list scratch");
+        }
+        t->ne_cap = t->nblocks;
+    }
+    if (t->desc_cap < nsets) {
+        dev_free(t->d_desc);
+        dev_free(t->d_ctr);
+        t->d_desc = nullptr;
+        t->d_ctr = nullptr;
+        t->gen += 1;
+        if (dev_alloc(&t->d_desc, (size_t)3 * nsets * sizeof(BatchSet)) != cudaSuccess ||
+            dev_alloc(&t->d_ctr, (size_t)nsets * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TRK_ENOMEM, "cannot allocate the set descriptors");
+        }
+        t->desc_cap = nsets;
+    }
+    // host-side descriptors: [0] first step, [1] parity 0 -> 1, [2] parity 1 -> 0
+    std::vector<BatchSet> h(3 * (size_t)nsets);
+    const BlockArgs base = base_args(t);
+    std::vector<int> direct(nsets, 0);
+    for (int s = 0; s < nsets; ++s) {
+        const trk_set& S = sets[s];
+        SetState& ss = t->sets[s];
+        BlockArgs a = base;
+        for (int i = 0; i < TRK_TAB_MAX_I; ++i)
+            for (int d = 0; d < TRK_TAB_MAX_DEG; ++d) {
+                a.cd.c[i][d] = kCoef[tabs[s]][i][d];
+                a.cd.d[i][d] = kDCoef[tabs[s]][i][d];
+                a.cf.c[i][d] = (float)kCoef[tabs[s]][i][d];
+                a.cf.d[i][d] = (float)kDCoef[tabs[s]][i][d];
+            }
+        a.np = S.np;
+        a.perm = ss.perm;
+        a.offsets = ss.offsets;
+        a.dt = dt;
+        a.key_out = ss.keys;
+        a.out = S.out;
+        for (int v = 0; v < 3; ++v) {
+            BatchSet& B = h[(size_t)v * nsets + s];
+            B.a = a;
+            const int cur = v == 2 ? 1 : 0;
+            if (v == 0) {
+                B.a.pos_in = S.pos;
+                B.a.id_in = nullptr;
+                B.a.rhs_in = S.rhs;
+                B.a.history_valid = history_valid;
+            } else {
+                B.a.pos_in = ss.pos_s[cur];
+                B.a.id_in = ss.id_s[cur];
+                B.a.rhs_in = ss.rhs_s[cur];
+                B.a.history_valid = 1;
+            }
+            B.a.pos_out = ss.pos_s[cur ^ 1];
+            B.a.id_out = ss.id_s[cur ^ 1];
+            B.a.rhs_out = ss.rhs_s[cur ^ 1];
+            B.list = ss.list;
+            B.count = ss.count;
+            B.n_items = (int)((S.np + PB_HOST - 1) / PB_HOST);
+            B.I = S.I;
+            B.deg_hi = kTables[tabs[s]].deg > S.I - 1;
+            B.deriv = S.deriv;
+            B.direct = 0;
+        }
+    }
+    // per-set path: halo-staged blocks or direct gathers, chosen by timing both once
+    for (int s = 0; s < nsets; ++s) {
+        const trk_set& S = sets[s];
+        if (S.np == 0) {   // empty set: no items (the direct path reads n_items = 0)
+            direct[s] = 1;
+            for (int v = 0; v < 3; ++v) h[(size_t)v * nsets + s].direct = 1;
+            continue;
+        }
+        const uint64_t sig = mix(mix(mix(mix(mix(0, (uint64_t)S.np), (uint64_t)S.I), (uint64_t)S.deriv),
+                                     (uint64_t)tabs[s]), (uint64_t)t->N);
+        int choice = -1;
+        for (auto& kv : t->tune_cache)
+            if (kv.first == sig) choice = kv.second;
+        if (choice < 0) {
+            SetState& ss = t->sets[s];
+            const size_t vb = (size_t)S.np * 24;
+            CUDA_TRY(cudaMemcpyAsync(ss.pos_s[1], S.pos, vb, cudaMemcpyDeviceToDevice, t->stream));
+            CUDA_TRY(launch_keys(t->g, S.np, ss.pos_s[1], ss.keys, t->d_flags, t->stream));
+            if ((rc = bin_set(t, ss, S.np, false))) return rc;
+            BatchSet probe = h[(size_t)nsets + s];           // parity-0 layout: reads pos_s[0] ...
+            probe.a.pos_in = ss.pos_s[1];                     // ... so point it at the copy
+            probe.a.id_in = nullptr;
+            probe.a.rhs_in = nullptr;
+            probe.a.history_valid = 0;
+            probe.a.pos_out = ss.pos_s[0];
+            probe.a.id_out = ss.id_s[0];
+            probe.a.rhs_out = ss.rhs_s[0];
+            probe.a.out = nullptr;
+            float best[2] = {0, 0};
+            cudaEvent_t e0, e1;
+            CUDA_TRY(cudaEventCreate(&e0));
+            CUDA_TRY(cudaEventCreate(&e1));
+            for (int variant = 0; variant < 2; ++variant) {
+                probe.direct = variant;
+                CUDA_TRY(cudaMemcpyAsync(t->d_desc, &probe, sizeof(BatchSet), cudaMemcpyHostToDevice, t->stream));
+                for (int rep = 0; rep < 2; ++rep) {
+                    CUDA_TRY(cudaEventRecord(e0, t->stream));
+                    if ((rc = batched_launch(t, t->d_desc, 1))) return rc;
+                    CUDA_TRY(cudaEventRecord(e1, t->stream));
+                    CUDA_TRY(cudaEventSynchronize(e1));
+                    CUDA_TRY(cudaEventElapsedTime(&best[variant], e0, e1));
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            choice = best[1] < best[0] ? 1 : 0;
+            t->tune_cache.emplace_back(sig, choice);
+        }
+        direct[s] = choice;
+        for (int v = 0; v < 3; ++v) h[(size_t)v * nsets + s].direct = choice;
+    }
+    CUDA_TRY(cudaMemcpyAsync(t->d_desc, h.data(), h.size() * sizeof(BatchSet), cudaMemcpyHostToDevice, t->stream));
+    CUDA_TRY(cudaStreamSynchronize(t->stream));   // h may be released after this
+    auto step = [&](int v) -> int {
+        for (int s = 0; s < nsets; ++s) {
+            if (sets[s].np == 0) continue;
+            if (v == 0) {
+                CUDA_TRY(launch_keys(t->g, sets[s].np, sets[s].pos, t->sets[s].keys, t->d_flags, t->stream));
+                t->launches += 1;
+            }
+            int r = bin_set(t, t->sets[s], sets[s].np, direct[s]);
+            if (r) return r;
+        }
+        return batched_launch(t, t->d_desc + (size_t)v * nsets, nsets);
+    };
+    if ((rc = step(0))) return rc;
+    int cur = 1;
+    int rest = steps - 1;
+    if (!t->prof && rest >= 2) {
+        uint64_t key = mix(mix(mix(0, t->gen), (uint64_t)nsets), dbits(dt));
+        for (int s = 0; s < nsets; ++s)
+            key = mix(mix(mix(mix(mix(key, (uint64_t)sets[s].np), (uint64_t)sets[s].I), (uint64_t)tabs[s]),
+                          (uint64_t)direct[s] * 2 + sets[s].deriv),
+                      (uint64_t)(uintptr_t)sets[s].out);
+        // the state is in buffer 1 after the first step: parity 1 -> 0, then 0 -> 1
+        rc = replay_graph(t, t->batch_graph, key, rest / 2, [&]() {
+            int r = step(2);
+            return r ? r : step(1);
+        });
+        if (rc) return rc;
+        rest -= 2 * (rest / 2);
+    }
+    for (; rest > 0; --rest) {
+        if ((rc = step(cur == 1 ? 2 : 1))) return rc;
+        cur ^= 1;
+    }
+    ProfScope ps(t, PROF_OTHER);
+    for (int s = 0; s < nsets; ++s) {
+        if (sets[s].np == 0) continue;
+        SetState& ss = t->sets[s];
+        CUDA_TRY(launch_unpermute_pos(sets[s].np, ss.pos_s[cur], ss.id_s[cur], sets[s].pos, t->stream));
+        CUDA_TRY(launch_unpermute_rhs(sets[s].np, ss.rhs_s[cur], ss.id_s[cur], sets[s].rhs, t->stream));
+        t->launches += 2;
+    }
+    return TRK_OK;
 }
 
 int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* lambdaT, double dt, int steps,
