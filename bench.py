@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the float64 and split-bf16 forms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
+                    help="2: the headline workload (default); 1 small, 3 precision, 4 batching, 5 adjoint")
     return ap.parse_args()
 
 
@@ -379,12 +381,225 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# other configurations (single GPU; one JSON line each, same keys)
+# --------------------------------------------------------------------------
+def _events():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _line(metric, value, unit, args, ms_step, workload, extra, dtype="f32", hib=True):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+         "ms_per_step": ms_step, "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+         "data": "synthetic", "config": {"workload": workload}}
+    d.update(extra)
+    print(json.dumps(d), flush=True)
+
+
+def run_config1(args):
+    """32^3 float64 field |k| <= 8, 1e4 tracers, Lagrange I=4, one RK2 step (launch-bound small case)."""
+    import torch
+
+    import paper_2107_01104_gb300 as trk
+    import synth
+
+    field = synth.velocity_field_np(32, 8, 1000)
+    pos = synth.uniform_particles_np(10_000, 1)
+    t = trk.Tracker(32, family=trk.TRK_LAGRANGE, I=4, storage=trk.TRK_F64)
+    t.set_field(torch.from_numpy(field).cuda())
+    p0 = torch.from_numpy(pos).cuda()
+    p = p0.clone()
+    for _ in range(args.warmup):
+        t.advance(p, 1e-3, 1)
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        t.interpolate(p, out_dtype=torch.float64)
+        t.advance(p, 1e-3, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    _line("particle-steps/s", 10_000 / (ms * 1e-3), "particle-steps/s", args, ms,
+          "32^3 f64 velocity |k|<=8, 1e4 tracers, Lagrange I=4, interpolate + one RK2 step dt=1e-3",
+          {"note": "launch-bound (about 13 kernels for 1e4 particles)"}, dtype="f64")
+
+
+def run_config3(args):
+    """1024^3, u (3) + grad u (9, spectral), float32 and split bf16 storage, 2^27 tracers, I = 8."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2107_01104_gb300 as trk
+    import synth
+
+    N, KM, NPART, NSUB, I8, M8 = 1024, 340, 1 << 27, 100_000, 8, 3
+    dev = torch.device("cuda")
+    pos = synth.uniform_particles_torch(NPART, 3, device=dev)
+    sub = pos[:, :NSUB].cpu().numpy()
+    cell, frac = oracle.split(sub, N)
+    rel = np.arange(1 - I8 // 2, I8 // 2 + 1)
+    c1 = (cell[0][:, None] + rel[None, :]) % N
+    c2 = (cell[1][:, None] + rel[None, :]) % N
+    c3 = (cell[2][:, None] + rel[None, :]) % N
+    idx = ((c3[:, :, None, None] * N + c2[:, None, :, None]) * N + c1[:, None, None, :]).reshape(NSUB, -1)
+    idx_t = torch.from_numpy(idx).to(dev)
+    f12 = torch.empty((12, N, N, N), dtype=torch.float32, device=dev)
+    stencil = np.empty((NSUB, 12, I8 ** 3), np.float64)
+    for i, comp in enumerate(synth.velocity_components_torch(N, KM, 1002, device=dev)):
+        f12[i] = comp.to(torch.float32)
+        stencil[:, i, :] = comp.reshape(-1)[idx_t].cpu().numpy()
+        del comp
+    del idx_t
+    torch.cuda.empty_cache()
+    truth = oracle.interp_stencil(frac, stencil.reshape(NSUB, 12, I8, I8, I8), oracle.SPLINE, I8, M8)
+    del stencil
+    rms_u = float(np.sqrt(np.mean(truth[:3] ** 2)))
+    rms_g = float(np.sqrt(np.mean(truth[3:] ** 2)))
+    results, roof = {}, None
+    peak, peak_kind = measured_peaks()
+    for sname, storage in (("f32", trk.TRK_F32), ("bf16x2", trk.TRK_BF16X2)):
+        for C in (3, 12):
+            t = trk.Tracker(N, family=trk.TRK_SPLINE, I=I8, m=M8, storage=storage)
+            t.set_field(f12[:C])
+            out = torch.empty((C, NPART), dtype=torch.float32, device=dev)
+            for _ in range(max(1, args.warmup)):
+                t.interpolate(pos, out=out)
+            torch.cuda.synchronize()
+            trk.tracker_profile(t.h, True)
+            e0, e1 = _events()
+            reps = max(1, min(args.steps, 3))
+            e0.record()
+            for _ in range(reps):
+                t.interpolate(pos, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            prof = trk.tracker_profile_read(t.h)
+            trk.tracker_profile(t.h, False)
+            ms = e0.elapsed_time(e1) / reps
+            err = out[:, :NSUB].double().cpu().numpy() - truth[:C]
+            key = f"{sname}_{'u' if C == 3 else 'u+grad'}"
+            results[key] = {"particles_per_s": NPART / (ms * 1e-3), "ms": ms,
+                            "kernel_ms": prof["step"][0] / reps, "binning_ms": prof["bin"][0] / reps,
+                            "rms_err_u_over_rms_u": float(np.sqrt(np.mean(err[:3] ** 2))) / rms_u}
+            if C == 12:
+                results[key]["rms_err_grad_over_rms_grad"] = float(np.sqrt(np.mean(err[3:] ** 2))) / rms_g
+            if storage == trk.TRK_F32 and C == 3:
+                alg = 3 * N ** 3 * 4 + NPART * 36
+                ach = alg / (prof["step"][0] / reps * 1e-3) / 1e9
+                roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "kernel": "k_block<float,8,7,INTERP,F32>", "alg_bytes_per_launch": alg,
+                        "peak_kind": peak_kind}
+            t.close()
+            del out
+            torch.cuda.empty_cache()
+    head = results["f32_u"]
+    _line("particles/s", head["particles_per_s"], "particles/s", args, head["ms"],
+          "1024^3 u (3) + grad u (9, spectral), fp32 and split-bf16 storage, |k|<=340, 2^27 tracers, spline I=8 m=3,"
+          " interpolation; error vs the fp64 oracle on 1e5 tracers", {"results": results, "roofline": roof})
+
+
+def run_config4(args):
+    """512^3 float32 u, 8 sets 1e3..2e7 tracers, I cycling 4/6/8, 3 or 9 outputs, 50 AB2 steps per call."""
+    import torch
+
+    import paper_2107_01104_gb300 as trk
+    import synth
+
+    N, dt, steps = 512, 2e-3, 50
+    dev = torch.device("cuda")
+    u = synth.velocity_field_torch(N, 170, 1003, out_dtype=torch.float32)
+    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    t.set_field(u)
+    del u
+    sizes = [1000, 10_000, 30_000, 100_000, 1_000_000, 3_000_000, 10_000_000, 20_000_000]
+    sets = []
+    for s, n in enumerate(sizes):
+        I = (4, 6, 8)[s % 3]
+        sets.append(dict(pos=synth.uniform_particles_torch(n, 10 + s, device=dev),
+                         rhs=torch.zeros((3, n), dtype=torch.float32, device=dev),
+                         out=torch.zeros((9 if s % 2 else 3, n), dtype=torch.float32, device=dev),
+                         family=trk.TRK_SPLINE, I=I, m=I // 2 - 1, deriv=s % 2))
+    total = sum(sizes)
+    for _ in range(args.warmup):
+        t.advance_batched(sets, dt, steps, history_valid=True)
+    torch.cuda.synchronize()
+    l0 = t.launch_count
+    trk.tracker_profile(t.h, True)
+    trk.tracker_profile(t.h, False)   # graph replay stays on (profiling would disable it)
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(args.steps):
+        t.advance_batched(sets, dt, steps, history_valid=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    _line("particle-steps/s", total * steps / (ms * 1e-3), "particle-steps/s", args, ms,
+          "512^3 fp32 u |k|<=170, 8 sets (1e3..2e7, sum 3.414e7), I cycling 4/6/8, 3- or 9-component outputs,"
+          " 50 AB2 steps per call, one persistent launch per step under a CUDA graph",
+          {"gpu_launches": t.launch_count - l0, "per_set_path": "direct or halo, chosen by timing"})
+
+
+def run_config5(args):
+    """256^3 float32 u, 2^22 tracers, spline I=6, 20 RK2 steps, adjoint with checkpoints every 5."""
+    import numpy as np
+    import torch
+
+    import paper_2107_01104_gb300 as trk
+    import synth
+
+    N, n, dt, steps = 256, 1 << 22, 5e-3, 20
+    dev = torch.device("cuda")
+    field = synth.velocity_field_np(N, 85, 1004).astype(np.float32)
+    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    t.set_field(torch.from_numpy(field).to(dev))
+    p0 = synth.uniform_particles_torch(n, 5, device=dev)
+    gf = torch.zeros((3, N, N, N), dtype=torch.float64, device=dev)
+    x = p0.clone()
+    for _ in range(args.warmup):
+        x.copy_(p0)
+        t.advance(x, dt, steps)
+        t.adjoint(p0, 2 * x, dt, steps, 5, grad_field=gf)
+    torch.cuda.synchronize()
+    fwd = bwd = 0.0
+    for _ in range(args.steps):
+        x.copy_(p0)
+        a0, a1 = _events()
+        b1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        t.advance(x, dt, steps)
+        a1.record()
+        t.adjoint(p0, 2 * x, dt, steps, 5, grad_field=gf)
+        b1.record()
+        torch.cuda.synchronize()
+        fwd += a0.elapsed_time(a1)
+        bwd += a1.elapsed_time(b1)
+    fwd /= args.steps
+    bwd /= args.steps
+    _line("particle-steps/s", n * steps / ((fwd + bwd) * 1e-3), "particle-steps/s", args, fwd + bwd,
+          "256^3 fp32 u |k|<=85, 2^22 tracers, spline I=6 m=2, 20 RK2 steps, loss sum |X_T|^2, backward by the"
+          " discrete adjoint (field scatter-add + position Jacobians) with checkpoints every 5 steps",
+          {"forward": {"ms": fwd, "particle_steps_per_s": n * steps / (fwd * 1e-3)},
+           "backward": {"ms": bwd, "particle_steps_per_s": n * steps / (bwd * 1e-3)}})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.config == 2:
         run_gb300(args)
+    else:
+        import torch
+
+        from paper_2107_01104_gb300 import build as lib_build
+
+        torch.cuda.set_device(0)
+        lib_build.build()
+        {1: run_config1, 3: run_config3, 4: run_config4, 5: run_config5}[args.config](args)
 
 
 if __name__ == "__main__":

@@ -124,6 +124,56 @@ def velocity_field_torch(N: int, kmax: float, seed: int, device="cuda", with_gra
     return u, grad
 
 
+def velocity_components_torch(N: int, kmax: float, seed: int, device="cuda", with_grad: bool = True):
+    """Yield the float64 components of :func:`velocity_field_torch` one at a time.
+
+    Order: u1, u2, u3, then d u_k / d x_j as 3k + j.  Same spectrum, seed and
+    scaling as velocity_field_torch, so the values agree with it; only one
+    real-space component is held at a time (for grids whose float64 copy does
+    not fit at once).
+    """
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    k_full = torch.fft.fftfreq(N, 1.0 / N, device=device, dtype=torch.float64)
+    k_half = torch.fft.rfftfreq(N, 1.0 / N, device=device, dtype=torch.float64)
+    k3 = k_full[:, None, None]
+    k2 = k_full[None, :, None]
+    k1 = k_half[None, None, :]
+    kk = k1 * k1 + k2 * k2 + k3 * k3
+    shell = (kk >= 1.0) & (kk <= kmax * kmax)
+    ksafe = torch.where(kk > 0, kk, torch.ones_like(kk))
+    shape = (N, N, N // 2 + 1)
+    uh = []
+    for _ in range(3):
+        re = torch.randn(shape, generator=g, device=device, dtype=torch.float64)
+        im = torch.randn(shape, generator=g, device=device, dtype=torch.float64)
+        uh.append(torch.complex(re, im))
+    kvec = (k1, k2, k3)
+    kdotu = k1 * uh[0] + k2 * uh[1] + k3 * uh[2]
+    for a in range(3):
+        uh[a] = uh[a] - kvec[a] * kdotu / ksafe
+    del kdotu
+    amp = torch.where(shell, ksafe ** (-11.0 / 12.0), torch.zeros_like(ksafe))
+    del kk, shell, ksafe
+    for a in range(3):
+        uh[a] = uh[a] * amp
+    del amp
+    sumsq = 0.0
+    for a in range(3):
+        ua = torch.fft.irfftn(uh[a], s=(N, N, N))
+        sumsq += float((ua * ua).sum())
+        del ua
+    scale = 1.0 / math.sqrt(sumsq / (3.0 * N ** 3))
+    for a in range(3):
+        yield torch.fft.irfftn(uh[a], s=(N, N, N)) * scale
+    if with_grad:
+        for k in range(3):
+            for j in range(3):
+                yield torch.fft.irfftn(1j * kvec[j] * uh[k], s=(N, N, N)) * scale
+
+
 def uniform_particles_np(n: int, seed: int) -> np.ndarray:
     """Tracer positions pos[3][n] (float64), uniform in [0, 2pi)^3."""
     rng = np.random.default_rng(seed)
