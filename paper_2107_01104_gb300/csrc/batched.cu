@@ -16,8 +16,13 @@ namespace {
 template <int I, int DEG, int STORE>
 __device__ __noinline__ void run_item(const BatchSet& S, int b, int j0, int j1, unsigned char* smem)
 {
-    if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE>(S.a, b, j0, j1, !S.direct, smem);
-    else process_block<float, I, DEG, MODE_AB2, STORE>(S.a, b, j0, j1, !S.direct, smem);
+    if (S.direct) {
+        if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, false>(S.a, b, j0, j1, smem);
+        else process_block<float, I, DEG, MODE_AB2, STORE, false>(S.a, b, j0, j1, smem);
+    } else {
+        if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, true>(S.a, b, j0, j1, smem);
+        else process_block<float, I, DEG, MODE_AB2, STORE, true>(S.a, b, j0, j1, smem);
+    }
 }
 
 template <int STORE>

@@ -149,8 +149,10 @@ __device__ __forceinline__ T horner_c(const T (&row)[TRK_TAB_MAX_DEG], T s)
 // ---------------------------------------------------------------------------
 // Loaders: ld(k, a1, a2, a3) = component k of node c + a - (I/2 - 1)
 // ---------------------------------------------------------------------------
-template <typename T, int S2, int S3, int SC>
+template <typename T, int S2_, int S3_, int SC_>
 struct SmemLd {
+    static constexpr int S2 = S2_, S3 = S3_, SC = SC_;
+    static constexpr bool kShared = true;
     const T* base;
     __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
     {
@@ -170,6 +172,7 @@ __device__ __forceinline__ T fetch(const FieldView& f, int k, int64_t idx)
 // Global-memory loader with periodic wrap (stencils outside the staged halo).
 template <typename T, int STORE, int I>
 struct GlobalLd {
+    static constexpr bool kShared = false;
     FieldView f;
     int c1, c2, c3, k0, kmax, mask;
     __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
@@ -202,12 +205,14 @@ struct WeightEval {
     }
     __device__ __forceinline__ void eval(T s1, T s2, T s3, T* wv, T* wd) const
     {
+        // every lane evaluates (idle lanes on a valid row) and only active lanes store
+        const T s = ax == 0 ? s1 : (ax == 1 ? s2 : s3);
+        const T w = horner(r, s);
+        T dw = 0;
+        if (D) dw = horner(dr, s);
         __syncwarp();                        // previous readers of the buffer are done
-        if (act) {
-            const T s = ax == 0 ? s1 : (ax == 1 ? s2 : s3);
-            wv[ax * 8 + i] = horner(r, s);
-            if (D) wd[ax * 8 + i] = horner(dr, s);
-        }
+        if (act) wv[ax * 8 + i] = w;
+        if (D && act) wd[ax * 8 + i] = dw;
         __syncwarp();
     }
 };
@@ -233,12 +238,23 @@ struct Lane<T, 8, D> {
     template <class LD>
     __device__ __forceinline__ void load(const LD& ld)
     {
+        if constexpr (LD::kShared) {
+            // one lane pointer, then compile-time offsets
+            const T* pa = ld.base + (i1 + j * LD::S2);
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+            for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+                for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int i3 = 0; i3 < 8; ++i3) f[k][h][i3] = ld(k, i1, j + 4 * h, i3);
+                    for (int i3 = 0; i3 < 8; ++i3) f[k][h][i3] = pa[k * LD::SC + 4 * h * LD::S2 + i3 * LD::S3];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int i3 = 0; i3 < 8; ++i3) f[k][h][i3] = ld(k, i1, j + 4 * h, i3);
+        }
     }
     // transpose of the gather: add w(node) mu_k into every node this lane gathers
     template <class ADD>
@@ -315,12 +331,25 @@ struct Lane<T, 6, D> {
     template <class LD>
     __device__ __forceinline__ void load(const LD& ld)
     {
+        if constexpr (LD::kShared) {
+            const T* pa = ld.base + (i1 + j * LD::S2);                  // pass A: row (i1, j)
+            const T* pb = ld.base + (i1 + 5 * LD::S2 + j * LD::S3);     // pass B: node (i1, 5, j)
+            const T* pc = ld.base + (i1 + 5 * LD::S2 + 5 * LD::S3);     // pass C: node (i1, 5, 5)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < 3; ++k) {
 #pragma unroll
-            for (int i3 = 0; i3 < 6; ++i3) f[k][i3] = ld(k, i1, j, i3);
-            f[k][6] = ld(k, i1, 5, j);
-            f[k][7] = ld(k, i1, 5, 5);
+                for (int i3 = 0; i3 < 6; ++i3) f[k][i3] = pa[k * LD::SC + i3 * LD::S3];
+                f[k][6] = pb[k * LD::SC];
+                f[k][7] = pc[k * LD::SC];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+#pragma unroll
+                for (int i3 = 0; i3 < 6; ++i3) f[k][i3] = ld(k, i1, j, i3);
+                f[k][6] = ld(k, i1, 5, j);
+                f[k][7] = ld(k, i1, 5, 5);
+            }
         }
     }
     template <class ADD>
@@ -401,10 +430,19 @@ struct Lane<T, 4, D> {
     template <class LD>
     __device__ __forceinline__ void load(const LD& ld)
     {
+        if constexpr (LD::kShared) {
+            const T* pa = ld.base + (i1 + i2 * LD::S2 + p * LD::S3);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            f[k][0] = ld(k, i1, i2, p);
-            f[k][1] = ld(k, i1, i2, p + 2);
+            for (int k = 0; k < 3; ++k) {
+                f[k][0] = pa[k * LD::SC];
+                f[k][1] = pa[k * LD::SC + 2 * LD::S3];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                f[k][0] = ld(k, i1, i2, p);
+                f[k][1] = ld(k, i1, i2, p + 2);
+            }
         }
     }
     template <class ADD>
@@ -526,41 +564,52 @@ __device__ __forceinline__ void load_vec(const FieldView& f, int64_t g, T (&vals
     }
 }
 
-// KC > 0: compile-time component count (loads batched UNR deep so they are in
-// flight together); KC = 0: runtime count kc.
+// The halo is kc * H planes (component k, z) of H rows of NV 16-byte vectors.
+// Thread t owns one (row y, vector v) slot of one of PPI planes per iteration;
+// that slot, its global/shared offsets inside a plane and its edge predicates
+// are fixed for the whole loop, and only the plane index advances (one
+// division by the constant H per iteration).  Iterations are batched UNR deep
+// so their loads are in flight together.  KC > 0: compile-time component
+// count; KC = 0: runtime count kc.
 template <typename T, int STORE, int H, int G, int S2, int S3, int SC, int KC>
 __device__ __forceinline__ void load_halo(T* halo, const FieldView& f, int k0, int kc, int o1, int o2, int o3)
 {
     constexpr int VEC = VecOf<STORE>::n;
     constexpr int OFF = ((PAD - G) % VEC + VEC) % VEC;   // block origins are multiples of 8
     constexpr int NV = (OFF + H + VEC - 1) / VEC;        // vectors per halo row
+    constexpr int SLOTS = H * NV;                        // vector slots per plane
+    constexpr int PPI = NT / SLOTS;                      // planes per iteration
+    static_assert(PPI >= 1, "a halo plane needs more vector slots than threads");
     constexpr int UNR = 4;
-    const int nq = (KC > 0 ? KC : kc) * H * H * NV;
+    const int nplanes = (KC > 0 ? KC : kc) * H;
     const int NP = f.NP;
-    const int xa = o1 + PAD - OFF;                        // aligned padded x of the row start
-    const int64_t gbase = (int64_t)k0 * f.plane + ((int64_t)(o3 + PAD) * NP + (o2 + PAD)) * NP + xa;
-    for (int q0 = threadIdx.x; q0 < nq; q0 += UNR * NT) {
+    const int64_t NP2 = (int64_t)NP * NP;
+    const int pslot = threadIdx.x / SLOTS;
+    const int q = threadIdx.x - pslot * SLOTS;
+    const int y = q / NV, v = q - (q / NV) * NV;
+    if (pslot >= PPI) return;                            // idle threads of the last partial plane group
+    const int64_t gslot = (int64_t)k0 * f.plane + (int64_t)(o3 + PAD) * NP2 + (int64_t)(o2 + PAD + y) * NP +
+                          (o1 + PAD - OFF) + v * VEC;
+    const int sslot = y * S2 + v * VEC - OFF;
+    bool ok[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) ok[e] = v * VEC + e - OFF >= 0 && v * VEC + e - OFF < H;
+    for (int p0 = pslot; p0 < nplanes; p0 += UNR * PPI) {
         T vals[UNR][VEC];
-        int dsto[UNR], vv[UNR];
+        int soff[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int q = q0 + u * NT;
-            const int row = q / NV, v = q - row * NV;
-            const int y = row % H, zk = row / H;
-            const int z = zk % H, k = zk / H;
-            vv[u] = v;
-            dsto[u] = k * SC + z * S3 + y * S2;
-            if (q < nq) load_vec<T, STORE, VEC>(f, gbase + (int64_t)k * f.plane + ((int64_t)z * NP + y) * NP + v * VEC,
-                                                vals[u]);
+            const int p = p0 + u * PPI;
+            const int k = p / H, z = p - (p / H) * H;
+            soff[u] = k * SC + z * S3 + sslot;
+            if (p < nplanes) load_vec<T, STORE, VEC>(f, gslot + (int64_t)k * f.plane + (int64_t)z * NP2, vals[u]);
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            if (q0 + u * NT < nq) {
+            if (p0 + u * PPI < nplanes) {
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    const int x = vv[u] * VEC + e - OFF;
-                    if (x >= 0 && x < H) halo[dsto[u] + x] = vals[u][e];
-                }
+                for (int e = 0; e < VEC; ++e)
+                    if (ok[e]) halo[soff[u] + e] = vals[u][e];
             }
         }
     }
@@ -592,13 +641,12 @@ struct SmemPlan {
 // ---------------------------------------------------------------------------
 // The block kernel.
 // ---------------------------------------------------------------------------
-// Processes the sorted particles [j0, j1) of cell block b.  use_halo = false
-// skips the halo staging and gathers every stencil from global memory (the
-// direct path for sparse particle sets, where a halo would serve one or two
+// Processes the sorted particles [j0, j1) of cell block b.  HALO = false skips
+// the halo staging and gathers every stencil from global memory (the direct
+// path for sparse particle sets, where a halo would serve one or two
 // particles).  Must be called by all threads of the CTA.
-template <typename T, int I, int DEG, int MODE, int STORE>
-__device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0, int j1, bool use_halo,
-                                              unsigned char* smem_raw)
+template <typename T, int I, int DEG, int MODE, int STORE, bool HALO>
+__device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0, int j1, unsigned char* smem_raw)
 {
     constexpr bool IS_AB2 = (MODE == MODE_AB2 || MODE == MODE_AB2_D);
     constexpr bool IS_STEP = (MODE == MODE_RK2 || IS_AB2);
@@ -644,42 +692,34 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     for (int batch = j0; batch < j1; batch += PB) {
         const int nbat = min(PB, j1 - batch);
         // ---------------- P1: split ----------------
-        double X[3] = {0, 0, 0};
-        float hr[3] = {0, 0, 0};
-        int id = 0;
+        // (nothing is kept in registers across Q: P3 re-reads its inputs)
         if (tid < nbat) {
             const int j = batch + tid;
             const int src = a.perm[j];
-            id = a.id_in ? a.id_in[src] : src;
             bool ok = true;
             int c[3];
             PRec<T> rec;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 double t;
-                X[ax] = a.pos_in[ax * np + src];
-                ok &= split_axis(X[ax], inv_delta, mask, c[ax], t);
+                ok &= split_axis(a.pos_in[ax * np + src], inv_delta, mask, c[ax], t);
                 rec.t[ax] = (T)t;
             }
             if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
-            const int r1 = (c[0] - o1) & mask, r2 = (c[1] - o2) & mask, r3 = (c[2] - o3) & mask;
-            // a particle always lies in its own block; the guard only keeps a
-            // corrupted permutation from indexing outside the staged halo
-            const bool in = use_halo && r1 >= LO && r1 <= RMAX && r2 >= LO && r2 <= RMAX && r3 >= LO &&
-                            r3 <= RMAX;
-            const int rp = in ? pack_rel(r1, r2, r3) : -1;
+            // a particle always lies in its own block (its key came from the same
+            // split); the clamp only keeps a corrupted permutation inside the halo
+            const int r1 = min(max((c[0] - o1) & mask, LO), RMAX);
+            const int r2 = min(max((c[1] - o2) & mask, LO), RMAX);
+            const int r3 = min(max((c[2] - o3) & mask, LO), RMAX);
+            const int rp = HALO ? pack_rel(r1, r2, r3) : -1;
             if constexpr (sizeof(T) == 4) rec.relf = __int_as_float(rp);
             else rec.relf = __longlong_as_double((long long)rp);
             p_rec[tid] = rec;
             p_cell[tid] = pack_cell(c[0], c[1], c[2]);
-            if (IS_AB2 && a.history_valid) {
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax) hr[ax] = a.rhs_in[ax * np + src];
-            }
         }
         // ---------------- Q: interpolation ----------------
         for (int ch = 0; ch < nchunks; ++ch) {
-            if (use_halo && (batch == j0 || nchunks > 1)) {
+            if (HALO && (batch == j0 || nchunks > 1)) {
                 if (ch > 0 || batch != j0) __syncthreads();   // previous readers of the halo are done
                 if constexpr (IS_STEP)
                     load_halo<T, STORE, H, G, S2, S3, SC, 3>(halo, a.f, 0, 3, o1, o2, o3);
@@ -694,7 +734,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                 else rp = (int)__double_as_longlong(rec.relf);
                 const T t1 = rec.t[0], t2 = rec.t[1], t3 = rec.t[2];
                 const int r1 = rp & 255, r2 = (rp >> 8) & 255, r3 = (rp >> 16) & 255;
-                if (rp >= 0) {
+                if constexpr (HALO) {
                     L.load(SL{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)});
                 } else {
                     const int pc = p_cell[q];
@@ -788,18 +828,22 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
             // ---------------- P3: update, re-split, write ----------------
             if (tid < nbat) {
                 const int j = batch + tid;
+                const int src = a.perm[j];
+                const int id = a.id_in ? a.id_in[src] : src;
                 int cn[3];
                 bool ok = true;
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
                     const double k1 = (double)p_k[ax * PB + tid];
+                    const double x0 = a.pos_in[ax * np + src];
                     double xn;
                     if constexpr (MODE == MODE_RK2) {
                         const double k2 = (double)p_k[(3 + ax) * PB + tid];
-                        xn = X[ax] + (0.5 * a.dt) * (k1 + k2);
+                        xn = x0 + (0.5 * a.dt) * (k1 + k2);
                     } else {   // AB2
-                        const double inc = a.history_valid ? (1.5 * k1 - 0.5 * (double)hr[ax]) : k1;
-                        xn = X[ax] + a.dt * inc;
+                        const double inc =
+                            a.history_valid ? (1.5 * k1 - 0.5 * (double)a.rhs_in[ax * np + src]) : k1;
+                        xn = x0 + a.dt * inc;
                         a.rhs_out[ax * np + j] = (float)k1;
                     }
                     double tt;
@@ -815,12 +859,17 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     }
 }
 
+#ifndef TRK_F32_MIN_BLOCKS
+#define TRK_F32_MIN_BLOCKS 3   // resident CTAs per SM the float32 kernels are register-capped for (I = 4, 6)
+#endif
+
 template <typename T, int I, int DEG, int MODE, int STORE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : 3) : 1) k_block(const __grid_constant__ BlockArgs a)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN_BLOCKS) : 1)
+    k_block(const __grid_constant__ BlockArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int b = blockIdx.x;
-    process_block<T, I, DEG, MODE, STORE>(a, b, a.offsets[b], a.offsets[b + 1], true, smem_raw);
+    process_block<T, I, DEG, MODE, STORE, true>(a, b, a.offsets[b], a.offsets[b + 1], smem_raw);
 }
 
 template <typename T, int I, int MODE>
