@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint(const __grid_constant__ AdjAr
             p_cell[tid] = pack_cell(c[0], c[1], c[2]);
         }
         if (batch != j0) __syncthreads();   // the accumulator of the previous batch is flushed
-        load_halo<T, STORE, H, G, S2, S3, SC, 3>(halo, a.f, 0, 3, o1, o2, o3);
+        stage_halo<T, STORE, H, G, S2, S3, SC, 3, true>(halo, a.f, 0, 3, o1, o2, o3);
         __syncthreads();
         // ---------------- Q1: u(X), J(X), J(X*) ----------------
         for (int q = warp; q < nbat; q += NW) {

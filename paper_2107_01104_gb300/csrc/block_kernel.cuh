@@ -615,6 +615,78 @@ __device__ __forceinline__ void load_halo(T* halo, const FieldView& f, int k0, i
     }
 }
 
+// cp.async copies of one 4- or 8-byte element, global -> shared (cached in L1,
+// which the overlapping halos of neighbouring blocks re-use).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(uint32_t dst, const T* src)
+{
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Asynchronous halo staging for float32 / float64 storage (the shared-memory
+// element type equals the stored type).  Every element is copied global ->
+// shared by cp.async, so nothing passes through registers and the thread is
+// free for other work while the copies land.  Lanes run along x1: thread t
+// copies column x = t mod H of rows t / H + r * RP (RP = NT / H rows per pass),
+// so a warp's copies cover about two contiguous rows.  Components k0 .. k0+kc-1
+// (KC > 0: compile-time count).  The caller completes the copies with
+// cp_async_wait_all() before the barrier that publishes the halo.
+template <typename T, int STORE, int H, int S2, int S3, int SC, int KC>
+__device__ __forceinline__ void load_halo_async(T* halo, const FieldView& f, int k0, int kc, int x0, int y0, int z0)
+{
+    static_assert(STORE == ST_F32 || STORE == ST_F64, "split-bf16 halos are converted through registers");
+    static_assert(sizeof(T) == (STORE == ST_F64 ? 8 : 4), "element type must equal the stored type");
+    constexpr int RP = NT / H;                           // rows per pass
+    constexpr int NPASS = (H + RP - 1) / RP;
+    static_assert(RP >= 1, "halo row longer than the thread count");
+    const int x = threadIdx.x % H, yr = threadIdx.x / H;
+    if (yr >= (RP < H ? RP : H)) return;
+    const T* gbase;
+    if constexpr (STORE == ST_F64) gbase = f.f64;
+    else gbase = f.f32;
+    const int64_t NP2 = (int64_t)f.NP * f.NP;
+    const T* g = gbase + (int64_t)k0 * f.plane + (int64_t)z0 * NP2 + (int64_t)(y0 + yr) * f.NP + (x0 + x);
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(halo) + (uint32_t)((yr * S2 + x) * (int)sizeof(T));
+    // one pass row at a time; the plane loop walks a pointer (unrolling it
+    // whole would hoist every plane's address into registers)
+#pragma unroll
+    for (int k = 0; k < (KC > 0 ? KC : 3); ++k) {
+        if (KC == 0 && k >= kc) break;
+#pragma unroll
+        for (int r = 0; r < NPASS; ++r) {
+            if (NPASS > 1 && yr + r * RP >= H) break;
+            const T* gz = g + (int64_t)k * f.plane + (int64_t)(r * RP) * f.NP;
+            uint32_t sz = s + (uint32_t)((k * SC + r * RP * S2) * (int)sizeof(T));
+#pragma unroll 5
+            for (int z = 0; z < H; ++z) {
+                cp_async_elem<T>(sz, gz);
+                gz += NP2;
+                sz += S3 * (int)sizeof(T);
+            }
+        }
+    }
+}
+
+// Stage components k0 .. k0+kc-1 (KC > 0: compile-time count) of the halo
+// whose origin is the cell (o1, o2, o3): cp.async for float32 / float64
+// storage, registers (with the bf16 hi + lo sum) for split bf16.  With
+// WAIT = false the float32 / float64 copies may still be in flight on return.
+template <typename T, int STORE, int H, int G, int S2, int S3, int SC, int KC, bool WAIT>
+__device__ __forceinline__ void stage_halo(T* halo, const FieldView& f, int k0, int kc, int o1, int o2, int o3)
+{
+    if constexpr (STORE == ST_BF16X2) {
+        load_halo<T, STORE, H, G, S2, S3, SC, KC>(halo, f, k0, kc, o1, o2, o3);
+    } else {
+        load_halo_async<T, STORE, H, S2, S3, SC, KC>(halo, f, k0, kc, o1 + PAD, o2 + PAD, o3 + PAD);
+        if (WAIT) cp_async_wait_all();
+    }
+}
+
 __device__ __forceinline__ int pack_rel(int r1, int r2, int r3) { return r1 | (r2 << 8) | (r3 << 16); }
 __device__ __forceinline__ int pack_cell(int c1, int c2, int c3) { return c1 | (c2 << 10) | (c3 << 20); }
 
@@ -629,14 +701,26 @@ struct alignas(4 * sizeof(T)) PRec {
 // particle records are read and written as 16- or 32-byte vectors).
 constexpr size_t align32(size_t x) { return (x + 31) & ~size_t(31); }
 
-template <typename T, int SC>
+// STAGE: what P1 keeps for later phases besides the records: 0 = caller ids
+// (outputs in caller order), 1 = ids + float64 positions (RK2 update),
+// 2 = ids + positions + previous right-hand sides (AB2 update).
+template <typename T, int SC, int STAGE>
 struct SmemPlan {
     static constexpr size_t rec = align32((size_t)3 * SC * sizeof(T));
     static constexpr size_t k = align32(rec + PB * sizeof(PRec<T>));
     static constexpr size_t w = align32(k + (size_t)6 * PB * sizeof(T));
     static constexpr size_t cell = align32(w + (size_t)NW * 48 * sizeof(T));
-    static constexpr size_t total = cell + PB * sizeof(int);
+    static constexpr size_t id = align32(cell + PB * sizeof(int));
+    static constexpr size_t x = align32(id + PB * sizeof(int));
+    static constexpr size_t rhs = align32(x + (STAGE >= 1 ? (size_t)3 * PB * sizeof(double) : 0));
+    static constexpr size_t total = rhs + (STAGE >= 2 ? (size_t)3 * PB * sizeof(float) : 0);
 };
+
+template <int MODE>
+__host__ __device__ constexpr int stage_of()
+{
+    return MODE == MODE_RK2 ? 1 : ((MODE == MODE_AB2 || MODE == MODE_AB2_D) ? 2 : 0);
+}
 
 // ---------------------------------------------------------------------------
 // The block kernel.
@@ -660,12 +744,15 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     constexpr int S2 = Lay::S2, S3 = Lay::S3, SC = Lay::SC;
     using SL = SmemLd<T, S2, S3, SC>;
 
-    using SM = SmemPlan<T, SC>;
+    using SM = SmemPlan<T, SC, stage_of<MODE>()>;
     T* halo = reinterpret_cast<T*>(smem_raw);                               // [3][SC]
     PRec<T>* p_rec = reinterpret_cast<PRec<T>*>(smem_raw + SM::rec);        // [PB]
     T* p_k = reinterpret_cast<T*>(smem_raw + SM::k);                        // [6][PB]: k1 (3), k2 (3)
     T* wbuf = reinterpret_cast<T*>(smem_raw + SM::w);                       // [NW][2][24] weights
     int* p_cell = reinterpret_cast<int*>(smem_raw + SM::cell);              // [PB]
+    int* p_id = reinterpret_cast<int*>(smem_raw + SM::id);                  // [PB] caller ids
+    double* p_x = reinterpret_cast<double*>(smem_raw + SM::x);              // [3][PB] positions (steps)
+    float* p_rhs = reinterpret_cast<float*>(smem_raw + SM::rhs);            // [3][PB] previous rhs (AB2)
 
     if (j0 >= j1) return;
 
@@ -689,10 +776,17 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     const int rcomp = ((lane & 16) ? 2 : 0) + ((lane & 8) ? 1 : 0);   // component held after reduce4
     const bool writer = (lane & 7) == 0 && rcomp < 3;                 // lanes 0, 8, 16
 
+    // the halo of component chunk ch (all three velocity components for the steps)
+    constexpr bool ASYNC = STORE != ST_BF16X2;
+    auto issue_halo = [&](int ch) {
+        if constexpr (IS_STEP) stage_halo<T, STORE, H, G, S2, S3, SC, 3, false>(halo, a.f, 0, 3, o1, o2, o3);
+        else stage_halo<T, STORE, H, G, S2, S3, SC, 0, false>(halo, a.f, 3 * ch, min(3, a.f.C - 3 * ch), o1, o2, o3);
+    };
+
     for (int batch = j0; batch < j1; batch += PB) {
         const int nbat = min(PB, j1 - batch);
-        // ---------------- P1: split ----------------
-        // (nothing is kept in registers across Q: P3 re-reads its inputs)
+        if (ASYNC && HALO && batch == j0) issue_halo(0);   // copies in flight while P1 runs
+        // ---------------- P1: split, stage what P3 and the writers need ----------------
         if (tid < nbat) {
             const int j = batch + tid;
             const int src = a.perm[j];
@@ -701,10 +795,14 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
             PRec<T> rec;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
+                const double x = a.pos_in[ax * np + src];
                 double t;
-                ok &= split_axis(a.pos_in[ax * np + src], inv_delta, mask, c[ax], t);
+                ok &= split_axis(x, inv_delta, mask, c[ax], t);
                 rec.t[ax] = (T)t;
+                if constexpr (IS_STEP) p_x[ax * PB + tid] = x;
+                if constexpr (IS_AB2) p_rhs[ax * PB + tid] = a.history_valid ? a.rhs_in[ax * np + src] : 0.0f;
             }
+            p_id[tid] = a.id_in ? a.id_in[src] : src;
             if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
             // a particle always lies in its own block (its key came from the same
             // split); the clamp only keeps a corrupted permutation inside the halo
@@ -719,13 +817,12 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
         }
         // ---------------- Q: interpolation ----------------
         for (int ch = 0; ch < nchunks; ++ch) {
-            if (HALO && (batch == j0 || nchunks > 1)) {
-                if (ch > 0 || batch != j0) __syncthreads();   // previous readers of the halo are done
-                if constexpr (IS_STEP)
-                    load_halo<T, STORE, H, G, S2, S3, SC, 3>(halo, a.f, 0, 3, o1, o2, o3);
-                else
-                    load_halo<T, STORE, H, G, S2, S3, SC, 0>(halo, a.f, 3 * ch, min(3, a.f.C - 3 * ch), o1, o2, o3);
+            if (HALO && !ASYNC && batch == j0 && ch == 0) issue_halo(0);
+            if (HALO && nchunks > 1 && (ch > 0 || batch != j0)) {
+                __syncthreads();   // previous readers of the halo are done
+                issue_halo(ch);
             }
+            if constexpr (HALO && ASYNC) cp_async_wait_all();
             __syncthreads();
             for (int q = warp; q < nbat; q += NW) {
                 const PRec<T> rec = p_rec[q];
@@ -784,7 +881,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                     if (writer) {
                         p_k[rcomp * PB + q] = m;
                         if (a.out) {   // per-step output u(X) in caller order
-                            const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
+                            const int qid = p_id[q];
                             reinterpret_cast<float*>(a.out)[(int64_t)rcomp * np + qid] = (float)m;
                         }
                     }
@@ -794,14 +891,14 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                     const int v = lane >> 1;
                     if ((lane & 1) == 0 && v < 3) p_k[v * PB + q] = m;
                     if ((lane & 1) == 0 && v >= 3 && v < 12 && a.out) {
-                        const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
+                        const int qid = p_id[q];
                         reinterpret_cast<float*>(a.out)[(int64_t)(v - 3) * np + qid] = (float)((double)m * inv_delta);
                     }
                 } else if constexpr (MODE == MODE_INTERP) {
                     const T m = reduce4(acc, lane);
                     const int kc = min(3, a.f.C - 3 * ch);
                     if (writer && rcomp < kc) {
-                        const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
+                        const int qid = p_id[q];
                         const int64_t o = (int64_t)(3 * ch + rcomp) * np + qid;
                         if (a.out_f64) reinterpret_cast<double*>(a.out)[o] = (double)m;
                         else reinterpret_cast<float*>(a.out)[o] = (float)m;
@@ -813,7 +910,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                                   ((lane >> 1) & 1);
                     const int kc = min(3, a.f.C - 3 * ch);
                     if ((lane & 1) == 0 && v >= 3 && v < 3 + 3 * kc) {
-                        const int qid = a.id_in ? a.id_in[a.perm[batch + q]] : a.perm[batch + q];
+                        const int qid = p_id[q];
                         const int row = 9 * ch + (v - 3);
                         const int64_t o = (int64_t)row * np + qid;
                         const double g = (double)m * inv_delta;
@@ -828,21 +925,20 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
             // ---------------- P3: update, re-split, write ----------------
             if (tid < nbat) {
                 const int j = batch + tid;
-                const int src = a.perm[j];
-                const int id = a.id_in ? a.id_in[src] : src;
+                const int id = p_id[tid];
                 int cn[3];
                 bool ok = true;
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
                     const double k1 = (double)p_k[ax * PB + tid];
-                    const double x0 = a.pos_in[ax * np + src];
+                    const double x0 = p_x[ax * PB + tid];
                     double xn;
                     if constexpr (MODE == MODE_RK2) {
                         const double k2 = (double)p_k[(3 + ax) * PB + tid];
                         xn = x0 + (0.5 * a.dt) * (k1 + k2);
                     } else {   // AB2
                         const double inc =
-                            a.history_valid ? (1.5 * k1 - 0.5 * (double)a.rhs_in[ax * np + src]) : k1;
+                            a.history_valid ? (1.5 * k1 - 0.5 * (double)p_rhs[ax * PB + tid]) : k1;
                         xn = x0 + a.dt * inc;
                         a.rhs_out[ax * np + j] = (float)k1;
                     }
@@ -878,13 +974,14 @@ constexpr size_t block_smem_bytes()
     constexpr int MARGIN = (MODE == MODE_RK2) ? 1 : 0;
     constexpr int H = BLK + I - 1 + 2 * MARGIN;
     using Lay = Layout<I, H>;
-    return SmemPlan<T, Lay::SC>::total;
+    return SmemPlan<T, Lay::SC, stage_of<MODE>()>::total;
 }
 
 template <typename T, int I, int DEG, int MODE, int STORE>
 cudaError_t launch_block_t(const BlockArgs& a, int64_t nblocks, cudaStream_t st)
 {
     constexpr size_t smem = block_smem_bytes<T, I, MODE>();
+    static_assert(smem <= 232448, "block shared-memory plan exceeds the per-block limit");
     auto kern = k_block<T, I, DEG, MODE, STORE>;
     static bool attr_set = false;
     if (!attr_set) {
