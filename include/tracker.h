@@ -64,6 +64,8 @@ typedef enum { TRK_RK2 = 0, TRK_AB2 = 1 } trk_scheme;
 
 typedef enum { TRK_DTYPE_F64 = 0, TRK_DTYPE_F32 = 1 } trk_dtype;
 
+typedef enum { TRK_STEP_AUTO = 0, TRK_STEP_BLOCK = 1, TRK_STEP_COLUMN = 2 } trk_step_kernel;
+
 /* ---------------------------------------------------------------------- */
 /* Lifetime                                                                */
 /* ---------------------------------------------------------------------- */
@@ -167,6 +169,23 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
  * Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
 int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, int steps, int scheme,
                     int history_valid);
+
+/* Step kernel used by tracker_advance (trk_step_kernel):
+ *   TRK_STEP_COLUMN: a persistent kernel that walks column segments of cell
+ *     blocks along x3 (the x3 slabs of Sec. 3.3.1): the field halo stays in a
+ *     ring of x3 planes, so a slab brings in only the planes it does not
+ *     share with the previous one, and the next slab's planes and particles
+ *     are copied in while the current slab is interpolated.  The sort
+ *     permutation is applied to the particle state by a gather kernel first.
+ *     Available for TRK_F32 storage with I = 4 or 6 in the 8 x 8 x 8 block
+ *     shape.
+ *   TRK_STEP_BLOCK: one thread block per cell block, reading the state
+ *     through the sort permutation (all storages and kernels).
+ *   TRK_STEP_AUTO (default): COLUMN where available, else BLOCK.
+ * Both kernels perform the same floating-point operations in the same
+ * order, so their results are bit-identical.  TRK_STEP_COLUMN on a tracker
+ * without a column kernel is TRK_EINVAL.  Errors: TRK_EINVAL. */
+int tracker_set_step_kernel(tracker* t, int kind);
 
 /* ---------------------------------------------------------------------- */
 /* Batched advection: many particle sets, one persistent launch per step  */

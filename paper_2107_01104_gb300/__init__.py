@@ -31,6 +31,7 @@ TRK_LAGRANGE, TRK_SPLINE = 0, 1
 TRK_F64, TRK_F32, TRK_BF16X2 = 0, 1, 2
 TRK_RK2, TRK_AB2 = 0, 1
 TRK_DTYPE_F64, TRK_DTYPE_F32 = 0, 1
+TRK_STEP_AUTO, TRK_STEP_BLOCK, TRK_STEP_COLUMN = 0, 1, 2
 
 _STATUS = {TRK_EINVAL: "EINVAL", TRK_ENOMEM: "ENOMEM", TRK_ECUDA: "ECUDA", TRK_ENONFINITE: "ENONFINITE",
            TRK_ENOFIELD: "ENOFIELD", TRK_ECFL: "ECFL"}
@@ -40,7 +41,7 @@ ABI_FUNCTIONS = (
     "tracker_create", "tracker_destroy", "tracker_last_error", "tracker_set_stream", "tracker_sync",
     "tracker_set_field", "tracker_set_block", "tracker_num_blocks", "tracker_bin", "tracker_interpolate",
     "tracker_advance", "tracker_advance_batched", "tracker_adjoint", "tracker_launch_count",
-    "tracker_profile", "tracker_profile_read", "tracker_bin_static",
+    "tracker_profile", "tracker_profile_read", "tracker_bin_static", "tracker_set_step_kernel",
 )
 
 
@@ -89,6 +90,7 @@ def load_library(path: str = LIB_PATH):
             "tracker_profile": (c_int, [vp, c_int]),
             "tracker_profile_read": (c_int, [vp, vp, vp]),
             "tracker_bin_static": (c_int, [c_i64, vp, c_int, c_d, c_int, c_int, c_int, vp, vp, vp, vp, vp]),
+            "tracker_set_step_kernel": (c_int, [vp, c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -169,6 +171,10 @@ def tracker_set_field(h, field: torch.Tensor):
 
 def tracker_set_block(h, bx, by, bz):
     _check(load_library().tracker_set_block(h, int(bx), int(by), int(bz)))
+
+
+def tracker_set_step_kernel(h, kind):
+    _check(load_library().tracker_set_step_kernel(h, int(kind)))
 
 
 def tracker_num_blocks(h) -> int:
@@ -308,6 +314,10 @@ class Tracker:
         self._stream()
         tracker_set_field(self.h, field)
         self.C = int(field.shape[0])
+
+    def set_step_kernel(self, kind):
+        """TRK_STEP_AUTO, TRK_STEP_BLOCK or TRK_STEP_COLUMN (see tracker_set_step_kernel)."""
+        tracker_set_step_kernel(self.h, kind)
 
     def bin(self, pos):
         self._stream()

@@ -210,6 +210,23 @@ __global__ void k_unpermute_pos(int64_t np, const double* __restrict__ src, cons
     for (int a = 0; a < 3; ++a) dst[a * np + p] = src[a * np + j];
 }
 
+// Applies the sort permutation to the particle state (sorted order j).
+__global__ void k_gather_state(int64_t np, const int32_t* __restrict__ perm, const double* __restrict__ pos_in,
+                               const int32_t* __restrict__ id_in, const float* __restrict__ rhs_in,
+                               double* __restrict__ pos_out, int32_t* __restrict__ id_out, float* __restrict__ rhs_out)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const int64_t src = perm[j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pos_out[a * np + j] = pos_in[a * np + src];
+    id_out[j] = id_in ? id_in[src] : (int32_t)src;
+    if (rhs_in) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rhs_out[a * np + j] = rhs_in[a * np + src];
+    }
+}
+
 __global__ void k_unpermute_rhs(int64_t np, const float* __restrict__ src, const int32_t* __restrict__ id,
                                 float* __restrict__ dst)
 {
@@ -327,6 +344,14 @@ cudaError_t launch_unpermute_pos(int64_t np, const double* src, const int32_t* i
 {
     if (np <= 0) return cudaSuccess;
     k_unpermute_pos<<<grid_for(np, 256), 256, 0, st>>>(np, src, id, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_state(int64_t np, const int32_t* perm, const double* pos_in, const int32_t* id_in,
+                                const float* rhs_in, double* pos_out, int32_t* id_out, float* rhs_out, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_gather_state<<<grid_for(np, 256), 256, 0, st>>>(np, perm, pos_in, id_in, rhs_in, pos_out, id_out, rhs_out);
     return cudaGetLastError();
 }
 

@@ -112,6 +112,19 @@ struct BatchSet {
     int I, deg_hi, deriv, direct;
 };
 
+// Arguments of the column step kernel (RK2 / AB2 over column segments of cell
+// blocks, float32 fields, I = 4 or 6).  The state arrays a.pos_out / a.rhs_out
+// hold the sorted particles and are updated in place; a.perm and a.id_* are
+// unused (the gather kernel has applied the permutation).
+constexpr int MAXSEG = 64;    // largest column segment (slabs per work item)
+
+struct ColumnArgs {
+    BlockArgs a;
+    int nseg;                 // slabs per work item (divides nb3, <= MAXSEG)
+    int64_t nitems;           // work items: nb1 * nb2 * (nb3 / nseg)
+    int* ctr;                 // work counter, zero at launch
+};
+
 // ---------------------------------------------------------------------------
 // Cell split (Sec. 2.2 steps 1-3), bit-exact with the float64 reference:
 //   g = X * fl(N/L), c0 = floor(g), t = g - c0, c = c0 mod N.
@@ -182,6 +195,12 @@ void set_error_message(const char* msg);
 
 // Block kernels, one entry per kernel width I (block_i4.cu, block_i6.cu, block_i8.cu).
 // deg_hi selects the degree-(I+1) instantiation (spline with m = I/2).
+cudaError_t launch_column_i4(int mode, const ColumnArgs& ca, int deg_hi, int nsm, cudaStream_t st);
+cudaError_t launch_column_i6(int mode, const ColumnArgs& ca, int deg_hi, int nsm, cudaStream_t st);
+// sorted state: pos_out[:, j] = pos_in[:, perm[j]], id_out[j] = id_in ? id_in[perm[j]] : perm[j],
+// rhs_out likewise when rhs_in is not null
+cudaError_t launch_gather_state(int64_t np, const int32_t* perm, const double* pos_in, const int32_t* id_in,
+                                const float* rhs_in, double* pos_out, int32_t* id_out, float* rhs_out, cudaStream_t st);
 cudaError_t launch_block_i4(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_block_i6(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_block_i8(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);

@@ -149,6 +149,8 @@ struct tracker {
     int desc_cap = 0;
     std::vector<std::pair<uint64_t, int>> tune_cache;   // set signature -> direct path?
     int nsm = 0;
+    int step_kernel = TRK_STEP_AUTO;  // trk_step_kernel
+    int* d_colctr = nullptr;          // work counter of the column kernel
     // instrumentation: event pairs per kernel class
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -372,23 +374,59 @@ int replay_graph(tracker* t, GraphCache& gc, uint64_t key, int reps, F&& body)
     return TRK_OK;
 }
 
-// One RK2/AB2 step of tracker_advance: re-bin, then the fused block kernel.
+bool column_available(const tracker* t)
+{
+    return t->storage == ST_F32 && (t->I == 4 || t->I == 6) && t->g.lb1 == LBLK && t->g.lb2 == LBLK &&
+           t->g.lb3 == LBLK;
+}
+
+bool use_column(const tracker* t) { return t->step_kernel != TRK_STEP_BLOCK && column_available(t); }
+
+// One RK2/AB2 step of tracker_advance: re-bin, then the fused step kernel
+// (column kernel over the gathered state, or block kernel through perm).
 // first: read the caller's arrays (identity ids, caller history flag).
 int advance_step(tracker* t, int64_t np, int mode, double dt, int cur, bool first, const double* pos,
                  const float* rhs, int history_valid)
 {
+    const bool col = use_column(t);
+    const int nxt = cur ^ 1;
     {
         ProfScope ps(t, PROF_BIN);
         CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
                             &t->launches));
         CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
         t->launches += 1;
+        if (col) {
+            const bool hv = mode == MODE_AB2 && (first ? history_valid != 0 : true);
+            const float* rin = hv ? (first ? rhs : t->rhs_s[cur]) : nullptr;
+            CUDA_TRY(launch_gather_state(np, t->perm, first ? pos : t->pos_s[cur], first ? nullptr : t->id_s[cur],
+                                         rin, t->pos_s[nxt], t->id_s[nxt], t->rhs_s[nxt], t->stream));
+            t->launches += 1;
+        }
+    }
+    if (col) {
+        ColumnArgs ca{};
+        ca.a = base_args(t);
+        ca.a.np = np;
+        ca.a.dt = dt;
+        ca.a.pos_out = t->pos_s[nxt];
+        ca.a.rhs_out = t->rhs_s[nxt];
+        ca.a.key_out = t->keys;
+        ca.a.history_valid = mode == MODE_AB2 ? (first ? history_valid : 1) : 0;
+        ca.nseg = std::min(t->g.nb3, 8);
+        ca.nitems = (int64_t)t->g.nb1 * t->g.nb2 * (t->g.nb3 / ca.nseg);
+        ca.ctr = t->d_colctr;
+        CUDA_TRY(cudaMemsetAsync(t->d_colctr, 0, sizeof(int), t->stream));
+        ProfScope ps(t, PROF_STEP);
+        t->launches += 1;
+        if (t->I == 4) CUDA_TRY(launch_column_i4(mode, ca, t->deg_hi, t->nsm, t->stream));
+        else CUDA_TRY(launch_column_i6(mode, ca, t->deg_hi, t->nsm, t->stream));
+        return TRK_OK;
     }
     BlockArgs a = base_args(t);
     a.np = np;
     a.perm = t->perm;
     a.dt = dt;
-    const int nxt = cur ^ 1;
     if (first) {
         a.pos_in = pos;
         a.id_in = nullptr;
@@ -454,6 +492,8 @@ int tracker_create(tracker** out, int N, double L, int family, int I, int m, int
     t->g.mask = N - 1;
     t->g.inv_delta = (double)N / L;
     int rc = set_geometry(t, BLK, BLK, BLK);
+    if (rc == TRK_OK && dev_alloc(&t->d_colctr, sizeof(int)) != cudaSuccess)
+        rc = fail(TRK_ENOMEM, "cannot allocate the column work counter");
     if (rc == TRK_OK && dev_alloc(&t->d_flags, NUM_FLAGS * sizeof(int)) != cudaSuccess)
         rc = fail(TRK_ENOMEM, "cannot allocate device flags");
     if (rc == TRK_OK && cudaMemset(t->d_flags, 0, NUM_FLAGS * sizeof(int)) != cudaSuccess)
@@ -505,6 +545,7 @@ int tracker_destroy(tracker* t)
     dev_free(t->ne_scratch);
     dev_free(t->d_desc);
     dev_free(t->d_ctr);
+    dev_free(t->d_colctr);
     if (t->gev[0]) cudaEventDestroy(t->gev[0]);
     if (t->gev[1]) cudaEventDestroy(t->gev[1]);
     if (t->gstream) cudaStreamDestroy(t->gstream);
@@ -614,6 +655,17 @@ int tracker_set_block(tracker* t, int bx, int by, int bz)
 }
 
 int64_t tracker_num_blocks(const tracker* t) { return t ? t->nblocks : -1; }
+
+int tracker_set_step_kernel(tracker* t, int kind)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (kind != TRK_STEP_AUTO && kind != TRK_STEP_BLOCK && kind != TRK_STEP_COLUMN)
+        return fail(TRK_EINVAL, "unknown step kernel %d", kind);
+    if (kind == TRK_STEP_COLUMN && !column_available(t))
+        return fail(TRK_EINVAL, "no column kernel for this tracker (needs F32 storage, I = 4 or 6, 8x8x8 blocks)");
+    t->step_kernel = kind;
+    return TRK_OK;
+}
 
 int64_t tracker_launch_count(const tracker* t) { return t ? t->launches : -1; }
 
