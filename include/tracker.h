@@ -175,10 +175,12 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     blocks along x3 (the x3 slabs of Sec. 3.3.1): the field halo stays in a
  *     ring of x3 planes, so a slab brings in only the planes it does not
  *     share with the previous one, and the next slab's planes and particles
- *     are copied in while the current slab is interpolated.  The sort
- *     permutation is applied to the particle state by a gather kernel first.
- *     Available for TRK_F32 storage with I = 4 or 6 in the 8 x 8 x 8 block
- *     shape.
+ *     are copied in while the current slab is interpolated.  Its re-binning
+ *     is a counting sort: the update phase counts the new block keys, a scan
+ *     gives the offsets, and a scatter moves the particle state into its
+ *     blocks (the order inside a block is not reproducible; no result
+ *     depends on it).  Available for TRK_F32 storage with I = 4 or 6 in the
+ *     8 x 8 x 8 block shape.
  *   TRK_STEP_BLOCK: one thread block per cell block, reading the state
  *     through the sort permutation (all storages and kernels).
  *   TRK_STEP_AUTO (default): COLUMN where available, else BLOCK.

@@ -28,7 +28,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 __global__ void k_keys(GridGeom g, int64_t np, const double* __restrict__ pos, uint32_t* __restrict__ keys,
-                       int* flags)
+                       int* flags, uint32_t* __restrict__ counts)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
@@ -40,7 +40,103 @@ __global__ void k_keys(GridGeom g, int64_t np, const double* __restrict__ pos, u
         ok &= split_axis(pos[a * np + p], g.inv_delta, g.mask, c[a], t);
     }
     if (!ok) atomicOr(flags + FLAG_NONFINITE, 1);
-    keys[p] = block_key(g, c[0], c[1], c[2]);
+    const uint32_t key = block_key(g, c[0], c[1], c[2]);
+    keys[p] = key;
+    if (counts) atomicAdd(counts + key, 1u);
+}
+
+// Block counts -> offsets (exclusive scan, offsets[nblocks] = total) and the
+// scatter cursors (a copy of the offsets); the counts are zeroed for the next
+// step.  One CTA of CS_THREADS threads walks the counts in tiles of
+// CS_THREADS * CS_PER elements, each thread CS_PER consecutive ones.
+constexpr int CS_THREADS = 1024, CS_PER = 4;
+
+__global__ void __launch_bounds__(CS_THREADS) k_count_scan(uint32_t* __restrict__ counts, int64_t nblocks,
+                                                           int32_t* __restrict__ offsets, int32_t* __restrict__ cursor)
+{
+    __shared__ uint32_t warp_tot[CS_THREADS / 32];
+    __shared__ uint32_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nblocks; base += (int64_t)CS_THREADS * CS_PER) {
+        uint32_t v[CS_PER], sum = 0;
+        const int64_t i0 = base + (int64_t)tid * CS_PER;
+#pragma unroll
+        for (int e = 0; e < CS_PER; ++e) {
+            v[e] = i0 + e < nblocks ? counts[i0 + e] : 0u;
+            sum += v[e];
+        }
+        // inclusive scan of the per-thread sums within the warp
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) warp_tot[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t x = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            warp_tot[lane] = x;                      // inclusive over warps
+        }
+        __syncthreads();
+        uint32_t run = s_carry + (w > 0 ? warp_tot[w - 1] : 0u) + inc - sum;
+#pragma unroll
+        for (int e = 0; e < CS_PER; ++e) {
+            if (i0 + e < nblocks) {
+                offsets[i0 + e] = (int32_t)run;
+                cursor[i0 + e] = (int32_t)run;
+                counts[i0 + e] = 0u;
+            }
+            run += v[e];
+        }
+        __syncthreads();                             // everyone has read s_carry and warp_tot
+        if (tid == 0) s_carry += warp_tot[CS_THREADS / 32 - 1];
+        __syncthreads();
+    }
+    if (tid == 0) offsets[nblocks] = (int32_t)s_carry;
+}
+
+// Counting-sort scatter of the particle state: particle j goes to the next
+// free slot of its block.  Lanes of a warp with the same key take one
+// cursor increment together (the state arrives grouped by the previous
+// step's blocks, so most of a warp shares a key) and are ranked by lane, so
+// their writes are contiguous.  The order of the groups inside a block
+// follows the atomics (not reproducible); every particle's arithmetic is
+// independent of the order, so the step results do not depend on it.
+__global__ void k_scatter_state(int64_t np, const uint32_t* __restrict__ keys, int32_t* __restrict__ cursor,
+                                const double* __restrict__ pos_in, const int32_t* __restrict__ id_in,
+                                const float* __restrict__ rhs_in, double* __restrict__ pos_out,
+                                int32_t* __restrict__ id_out, float* __restrict__ rhs_out, int* flags)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned valid = __ballot_sync(0xffffffffu, j < np);
+    if (j >= np) return;
+    const uint32_t key = keys[j];
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(valid, key);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cursor + key, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int64_t d = (int64_t)base + __popc(peers & ((1u << lane) - 1u));
+    if (d < 0 || d >= np) {
+        atomicOr(flags + FLAG_BINNING, 1);
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pos_out[a * np + d] = pos_in[a * np + j];
+    id_out[d] = id_in ? id_in[j] : (int32_t)j;
+    if (rhs_in) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rhs_out[a * np + d] = rhs_in[a * np + j];
+    }
 }
 
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
@@ -210,23 +306,6 @@ __global__ void k_unpermute_pos(int64_t np, const double* __restrict__ src, cons
     for (int a = 0; a < 3; ++a) dst[a * np + p] = src[a * np + j];
 }
 
-// Applies the sort permutation to the particle state (sorted order j).
-__global__ void k_gather_state(int64_t np, const int32_t* __restrict__ perm, const double* __restrict__ pos_in,
-                               const int32_t* __restrict__ id_in, const float* __restrict__ rhs_in,
-                               double* __restrict__ pos_out, int32_t* __restrict__ id_out, float* __restrict__ rhs_out)
-{
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= np) return;
-    const int64_t src = perm[j];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) pos_out[a * np + j] = pos_in[a * np + src];
-    id_out[j] = id_in ? id_in[src] : (int32_t)src;
-    if (rhs_in) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) rhs_out[a * np + j] = rhs_in[a * np + src];
-    }
-}
-
 __global__ void k_unpermute_rhs(int64_t np, const float* __restrict__ src, const int32_t* __restrict__ id,
                                 float* __restrict__ dst)
 {
@@ -281,7 +360,31 @@ cudaError_t scan_exclusive_u32(uint32_t* data, int64_t len, uint32_t* scratch, c
 cudaError_t launch_keys(const GridGeom& g, int64_t np, const double* pos, uint32_t* keys, int* flags, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
-    k_keys<<<grid_for(np, 256), 256, 0, st>>>(g, np, pos, keys, flags);
+    k_keys<<<grid_for(np, 256), 256, 0, st>>>(g, np, pos, keys, flags, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys_count(const GridGeom& g, int64_t np, const double* pos, uint32_t* keys, uint32_t* counts,
+                              int* flags, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_keys<<<grid_for(np, 256), 256, 0, st>>>(g, np, pos, keys, flags, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor, cudaStream_t st)
+{
+    k_count_scan<<<1, CS_THREADS, 0, st>>>(counts, nblocks, offsets, cursor);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,
+                                 const int32_t* id_in, const float* rhs_in, double* pos_out, int32_t* id_out,
+                                 float* rhs_out, int* flags, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_scatter_state<<<grid_for(np, 256), 256, 0, st>>>(np, keys, cursor, pos_in, id_in, rhs_in, pos_out, id_out,
+                                                      rhs_out, flags);
     return cudaGetLastError();
 }
 
@@ -344,14 +447,6 @@ cudaError_t launch_unpermute_pos(int64_t np, const double* src, const int32_t* i
 {
     if (np <= 0) return cudaSuccess;
     k_unpermute_pos<<<grid_for(np, 256), 256, 0, st>>>(np, src, id, dst);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gather_state(int64_t np, const int32_t* perm, const double* pos_in, const int32_t* id_in,
-                                const float* rhs_in, double* pos_out, int32_t* id_out, float* rhs_out, cudaStream_t st)
-{
-    if (np <= 0) return cudaSuccess;
-    k_gather_state<<<grid_for(np, 256), 256, 0, st>>>(np, perm, pos_in, id_in, rhs_in, pos_out, id_out, rhs_out);
     return cudaGetLastError();
 }
 

@@ -37,9 +37,10 @@
 // k values): REC[tau % 2] (particle warp arrives, interpolation warps wait)
 // and KV[tau % 2] (interpolation warps arrive, particle warp waits).
 //
-// Particle state is read from and written back to the same sorted arrays (the
-// sort permutation has been applied by a gather kernel beforehand), so each
-// task's inputs are contiguous.  Input buffers rotate over three slots.
+// Particle state is read from and written back to the same arrays, grouped
+// by block beforehand (counting-sort scatter), so each task's inputs are
+// contiguous.  Input buffers rotate over three slots.  The update phase also
+// counts the new block keys for the next binning.
 #pragma once
 
 #include <algorithm>
@@ -247,6 +248,7 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
 #pragma unroll
                 for (int h = 0; h < PBC / 32; ++h) {
                     const int i = lane + 32 * h;
+                    const unsigned valid = __ballot_sync(0xffffffffu, i < t.n);
                     if (i >= t.n) continue;
                     const int64_t j = (int64_t)t.j0 + i;
                     int cn[3];
@@ -271,7 +273,12 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
                         a.pos_out[ax * np + j] = xn;
                     }
                     if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
-                    a.key_out[j] = block_key(a.g, cn[0], cn[1], cn[2]);
+                    const uint32_t key = block_key(a.g, cn[0], cn[1], cn[2]);
+                    a.key_out[j] = key;
+                    if (ca.counts) {   // block counts of the next binning, one add per group of equal keys
+                        const unsigned peers = __match_any_sync(valid, key);
+                        if (lane == __ffs(peers) - 1) atomicAdd(ca.counts + key, (uint32_t)__popc(peers));
+                    }
                 }
             };
 

@@ -14,7 +14,9 @@ namespace trk {
 // Device error flags (one int each in a small device array owned by the
 // tracker).  Set with atomicOr, read and cleared by tracker_sync().
 // ---------------------------------------------------------------------------
-enum { FLAG_NONFINITE = 0, FLAG_CFL = 1, NUM_FLAGS = 4 };
+// FLAG_BINNING: a counting-sort scatter found a block fuller than its count
+// (cannot happen when every step counts what it writes; guarded anyway).
+enum { FLAG_NONFINITE = 0, FLAG_CFL = 1, FLAG_BINNING = 2, NUM_FLAGS = 4 };
 
 // Storage codes (same values as trk_storage in tracker.h).
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16X2 = 2 };
@@ -114,8 +116,8 @@ struct BatchSet {
 
 // Arguments of the column step kernel (RK2 / AB2 over column segments of cell
 // blocks, float32 fields, I = 4 or 6).  The state arrays a.pos_out / a.rhs_out
-// hold the sorted particles and are updated in place; a.perm and a.id_* are
-// unused (the gather kernel has applied the permutation).
+// hold the particles grouped by block and are updated in place; a.perm and
+// a.id_* are unused (the scatter kernel has grouped the state).
 constexpr int MAXSEG = 64;    // largest column segment (slabs per work item)
 
 struct ColumnArgs {
@@ -123,6 +125,7 @@ struct ColumnArgs {
     int nseg;                 // slabs per work item (divides nb3, <= MAXSEG)
     int64_t nitems;           // work items: nb1 * nb2 * (nb3 / nseg)
     int* ctr;                 // work counter, zero at launch
+    uint32_t* counts;         // [nblocks] block counts of the new keys (added into) or null
 };
 
 // ---------------------------------------------------------------------------
@@ -197,10 +200,14 @@ void set_error_message(const char* msg);
 // deg_hi selects the degree-(I+1) instantiation (spline with m = I/2).
 cudaError_t launch_column_i4(int mode, const ColumnArgs& ca, int deg_hi, int nsm, cudaStream_t st);
 cudaError_t launch_column_i6(int mode, const ColumnArgs& ca, int deg_hi, int nsm, cudaStream_t st);
-// sorted state: pos_out[:, j] = pos_in[:, perm[j]], id_out[j] = id_in ? id_in[perm[j]] : perm[j],
-// rhs_out likewise when rhs_in is not null
-cudaError_t launch_gather_state(int64_t np, const int32_t* perm, const double* pos_in, const int32_t* id_in,
-                                const float* rhs_in, double* pos_out, int32_t* id_out, float* rhs_out, cudaStream_t st);
+// counting-sort binning of the step path: keys with block counts; counts ->
+// offsets + cursors (counts zeroed); scatter of the state into its blocks
+cudaError_t launch_keys_count(const GridGeom& g, int64_t np, const double* pos, uint32_t* keys, uint32_t* counts,
+                              int* flags, cudaStream_t st);
+cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor, cudaStream_t st);
+cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,
+                                 const int32_t* id_in, const float* rhs_in, double* pos_out, int32_t* id_out,
+                                 float* rhs_out, int* flags, cudaStream_t st);
 cudaError_t launch_block_i4(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_block_i6(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_block_i8(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);

@@ -151,6 +151,8 @@ struct tracker {
     int nsm = 0;
     int step_kernel = TRK_STEP_AUTO;  // trk_step_kernel
     int* d_colctr = nullptr;          // work counter of the column kernel
+    uint32_t* d_counts = nullptr;     // [nblocks] block counts (counting-sort binning of the column path)
+    int32_t* d_cursor = nullptr;      // [nblocks] scatter cursors
     // instrumentation: event pairs per kernel class
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -208,9 +210,16 @@ int set_geometry(tracker* t, int bx, int by, int bz)
     t->nblocks = (int64_t)t->g.nb1 * t->g.nb2 * t->g.nb3;
     t->key_bits = ilog2(t->nblocks);
     dev_free(t->offsets);
+    dev_free(t->d_counts);
+    dev_free(t->d_cursor);
     t->offsets = nullptr;
+    t->d_counts = nullptr;
+    t->d_cursor = nullptr;
     t->gen += 1;
     CUDA_TRY(dev_alloc(&t->offsets, (size_t)(t->nblocks + 1) * sizeof(int32_t)));
+    CUDA_TRY(dev_alloc(&t->d_counts, (size_t)t->nblocks * sizeof(uint32_t)));
+    CUDA_TRY(dev_alloc(&t->d_cursor, (size_t)t->nblocks * sizeof(int32_t)));
+    CUDA_TRY(cudaMemset(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t)));
     return TRK_OK;
 }
 
@@ -382,8 +391,11 @@ bool column_available(const tracker* t)
 
 bool use_column(const tracker* t) { return t->step_kernel != TRK_STEP_BLOCK && column_available(t); }
 
-// One RK2/AB2 step of tracker_advance: re-bin, then the fused step kernel
-// (column kernel over the gathered state, or block kernel through perm).
+// One RK2/AB2 step of tracker_advance: re-bin, then the fused step kernel.
+// Column path: counting-sort binning (block counts from the previous step's
+// update or from the initial keys, scan, scatter of the state into its
+// blocks), then the column kernel, which counts the new keys.  Block path:
+// stable radix sort, then the block kernel reading through perm.
 // first: read the caller's arrays (identity ids, caller history flag).
 int advance_step(tracker* t, int64_t np, int mode, double dt, int cur, bool first, const double* pos,
                  const float* rhs, int history_valid)
@@ -392,15 +404,18 @@ int advance_step(tracker* t, int64_t np, int mode, double dt, int cur, bool firs
     const int nxt = cur ^ 1;
     {
         ProfScope ps(t, PROF_BIN);
-        CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
-                            &t->launches));
-        CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
-        t->launches += 1;
         if (col) {
             const bool hv = mode == MODE_AB2 && (first ? history_valid != 0 : true);
             const float* rin = hv ? (first ? rhs : t->rhs_s[cur]) : nullptr;
-            CUDA_TRY(launch_gather_state(np, t->perm, first ? pos : t->pos_s[cur], first ? nullptr : t->id_s[cur],
-                                         rin, t->pos_s[nxt], t->id_s[nxt], t->rhs_s[nxt], t->stream));
+            CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->stream));
+            CUDA_TRY(launch_scatter_state(np, t->keys, t->d_cursor, first ? pos : t->pos_s[cur],
+                                          first ? nullptr : t->id_s[cur], rin, t->pos_s[nxt], t->id_s[nxt],
+                                          t->rhs_s[nxt], t->d_flags, t->stream));
+            t->launches += 2;
+        } else {
+            CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
+                                &t->launches));
+            CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
             t->launches += 1;
         }
     }
@@ -416,6 +431,7 @@ int advance_step(tracker* t, int64_t np, int mode, double dt, int cur, bool firs
         ca.nseg = std::min(t->g.nb3, 8);
         ca.nitems = (int64_t)t->g.nb1 * t->g.nb2 * (t->g.nb3 / ca.nseg);
         ca.ctr = t->d_colctr;
+        ca.counts = t->d_counts;
         CUDA_TRY(cudaMemsetAsync(t->d_colctr, 0, sizeof(int), t->stream));
         ProfScope ps(t, PROF_STEP);
         t->launches += 1;
@@ -546,6 +562,8 @@ int tracker_destroy(tracker* t)
     dev_free(t->d_desc);
     dev_free(t->d_ctr);
     dev_free(t->d_colctr);
+    dev_free(t->d_counts);
+    dev_free(t->d_cursor);
     if (t->gev[0]) cudaEventDestroy(t->gev[0]);
     if (t->gev[1]) cudaEventDestroy(t->gev[1]);
     if (t->gstream) cudaStreamDestroy(t->gstream);
@@ -601,6 +619,7 @@ int tracker_sync(tracker* t)
     CUDA_TRY(cudaMemcpy(h, t->d_flags, sizeof(h), cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemset(t->d_flags, 0, sizeof(h)));
     if (h[FLAG_NONFINITE]) return fail(TRK_ENONFINITE, "a position was non-finite or beyond 2^51 cells");
+    if (h[FLAG_BINNING]) return fail(TRK_ECUDA, "internal error: block counts did not match the binned particles");
     if (h[FLAG_CFL]) return fail(TRK_ECFL, "a particle moved more than one cell in one stage (result computed exactly)");
     return TRK_OK;
 }
@@ -664,6 +683,7 @@ int tracker_set_step_kernel(tracker* t, int kind)
     if (kind == TRK_STEP_COLUMN && !column_available(t))
         return fail(TRK_EINVAL, "no column kernel for this tracker (needs F32 storage, I = 4 or 6, 8x8x8 blocks)");
     t->step_kernel = kind;
+    t->gen += 1;                      // captured step graphs hold the other kernels
     return TRK_OK;
 }
 
@@ -721,10 +741,15 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     if ((rc = ensure_sort(t, np))) return rc;
     if ((rc = ensure_state(t, np))) return rc;
     const int mode = scheme == TRK_RK2 ? MODE_RK2 : MODE_AB2;
-    // initial keys from the caller's positions
+    // initial keys from the caller's positions (with block counts on the column path)
     {
         ProfScope ps(t, PROF_BIN);
-        CUDA_TRY(launch_keys(t->g, np, pos, t->keys, t->d_flags, t->stream));
+        if (use_column(t)) {
+            CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
+            CUDA_TRY(launch_keys_count(t->g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
+        } else {
+            CUDA_TRY(launch_keys(t->g, np, pos, t->keys, t->d_flags, t->stream));
+        }
         t->launches += 1;
     }
     // the first step reads the caller's arrays; the others ping-pong between
