@@ -47,60 +47,67 @@ __global__ void k_keys(GridGeom g, int64_t np, const double* __restrict__ pos, u
 
 // Block counts -> offsets (exclusive scan, offsets[nblocks] = total) and the
 // scatter cursors (a copy of the offsets); the counts are zeroed for the next
-// step.  One CTA of CS_THREADS threads walks the counts in tiles of
-// CS_THREADS * CS_PER elements, each thread CS_PER consecutive ones.
-constexpr int CS_THREADS = 1024, CS_PER = 4;
+// step.  One CTA: thread t owns the contiguous range [t P, (t + 1) P) with P
+// a multiple of 4 (16-byte vectors when nblocks is a multiple of 4); a first
+// pass sums each range (all loads of a thread independent), one block-wide
+// scan of the sums, and a second pass writes the prefixes.
+constexpr int CS_THREADS = 1024;
 
 __global__ void __launch_bounds__(CS_THREADS) k_count_scan(uint32_t* __restrict__ counts, int64_t nblocks,
                                                            int32_t* __restrict__ offsets, int32_t* __restrict__ cursor)
 {
     __shared__ uint32_t warp_tot[CS_THREADS / 32];
-    __shared__ uint32_t s_carry;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < nblocks; base += (int64_t)CS_THREADS * CS_PER) {
-        uint32_t v[CS_PER], sum = 0;
-        const int64_t i0 = base + (int64_t)tid * CS_PER;
-#pragma unroll
-        for (int e = 0; e < CS_PER; ++e) {
-            v[e] = i0 + e < nblocks ? counts[i0 + e] : 0u;
-            sum += v[e];
+    const int64_t per = ((nblocks + CS_THREADS - 1) / CS_THREADS + 3) / 4 * 4;
+    const int64_t i0 = (int64_t)tid * per, i1 = min(i0 + per, nblocks);
+    const bool vec = (nblocks & 3) == 0;      // every range then starts and ends on a 16-byte boundary
+    uint32_t sum = 0;
+    if (vec) {
+        for (int64_t i = i0; i < i1; i += 4) {
+            const uint4 c = *reinterpret_cast<const uint4*>(counts + i);
+            sum += c.x + c.y + c.z + c.w;
         }
-        // inclusive scan of the per-thread sums within the warp
-        uint32_t inc = sum;
+    } else {
+        for (int64_t i = i0; i < i1; ++i) sum += counts[i];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = warp_tot[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        if (lane == 31) warp_tot[w] = inc;
-        __syncthreads();
-        if (w == 0) {
-            uint32_t x = warp_tot[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            warp_tot[lane] = x;                      // inclusive over warps
-        }
-        __syncthreads();
-        uint32_t run = s_carry + (w > 0 ? warp_tot[w - 1] : 0u) + inc - sum;
-#pragma unroll
-        for (int e = 0; e < CS_PER; ++e) {
-            if (i0 + e < nblocks) {
-                offsets[i0 + e] = (int32_t)run;
-                cursor[i0 + e] = (int32_t)run;
-                counts[i0 + e] = 0u;
-            }
-            run += v[e];
-        }
-        __syncthreads();                             // everyone has read s_carry and warp_tot
-        if (tid == 0) s_carry += warp_tot[CS_THREADS / 32 - 1];
-        __syncthreads();
+        warp_tot[lane] = x;                          // inclusive over warps
     }
-    if (tid == 0) offsets[nblocks] = (int32_t)s_carry;
+    __syncthreads();
+    uint32_t run = (w > 0 ? warp_tot[w - 1] : 0u) + inc - sum;
+    if (vec) {
+        for (int64_t i = i0; i < i1; i += 4) {
+            const uint4 c = *reinterpret_cast<const uint4*>(counts + i);
+            const int4 o = make_int4((int)run, (int)(run + c.x), (int)(run + c.x + c.y), (int)(run + c.x + c.y + c.z));
+            *reinterpret_cast<int4*>(offsets + i) = o;
+            *reinterpret_cast<int4*>(cursor + i) = o;
+            *reinterpret_cast<uint4*>(counts + i) = make_uint4(0u, 0u, 0u, 0u);
+            run += c.x + c.y + c.z + c.w;
+        }
+    } else {
+        for (int64_t i = i0; i < i1; ++i) {
+            const uint32_t c = counts[i];
+            offsets[i] = (int32_t)run;
+            cursor[i] = (int32_t)run;
+            counts[i] = 0u;
+            run += c;
+        }
+    }
+    if (tid == CS_THREADS - 1) offsets[nblocks] = (int32_t)warp_tot[CS_THREADS / 32 - 1];
 }
 
 // Counting-sort scatter of the particle state: particle j goes to the next
