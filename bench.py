@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the float64 and split-bf16 forms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "block", "column"],
+                    help="step kernel of the headline workload (default: the column kernel)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="2: the headline workload (default); 1 small, 3 precision, 4 batching, 5 adjoint")
     return ap.parse_args()
@@ -129,14 +131,16 @@ def field_and_particles():
     return field, pos
 
 
-STEP_KERNEL = "k_column<6,5,RK2> (float32 field)"
-TRAFFIC_KEY = "k_column_rk2_f32_i6"
+STEP_KERNELS = {"column": ("k_column<6,5,RK2> (float32 field)", "k_column_rk2_f32_i6",
+                            ("column_kernel.cuh", "column_i6.cu", "block_kernel.cuh", "internal.cuh", "coeffs.inc")),
+                "block": ("k_block<float,6,5,RK2,F32>", "k_block_rk2_f32_i6",
+                          ("block_kernel.cuh", "block_i6.cu", "internal.cuh", "coeffs.inc"))}
 
 
-def kernel_source_sha():
+def kernel_source_sha(kind="column"):
     """Hash of the sources of the step kernel the headline workload runs."""
     h = hashlib.sha256()
-    for f in ("column_kernel.cuh", "column_i6.cu", "block_kernel.cuh", "internal.cuh", "coeffs.inc"):
+    for f in STEP_KERNELS[kind][2]:
         with open(os.path.join(ROOT, "paper_2107_01104_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -151,14 +155,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(sha):
+def ncu_traffic(sha, kind="column"):
     """DRAM bytes per launch of the step kernel from the committed ncu summary, if it matches the source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    e = d.get(TRAFFIC_KEY)
+    e = d.get(STEP_KERNELS[kind][1])
     if not e or e.get("source_sha") != sha:
         return None
     return e.get("dram_bytes_per_launch")
@@ -175,6 +179,21 @@ def sync_flags(tr, trk, notes):
         notes["cfl_slow_path_used"] = True
 
 
+def oracle_cost(f64, pos):
+    """Seconds per particle-step of the oracle on this host (calibrated on a
+    sample large enough that its fixed per-call cost does not dominate)."""
+    import oracle
+
+    n = 256
+    while True:
+        t0 = time.perf_counter()
+        oracle.advance(f64, pos[:, :n], DT, 2, oracle.SPLINE, I, M)
+        el = time.perf_counter() - t0
+        if el > 0.5 or n >= NP:
+            return el / (n * 2)
+        n = min(NP, n * 8)
+
+
 def cpu_baseline(field, pos, seconds):
     """The oracle as it stands, on this host's cores, on a bounded particle sample."""
     import numpy as np
@@ -182,9 +201,7 @@ def cpu_baseline(field, pos, seconds):
     import oracle
 
     f64 = field.astype(np.float64)
-    t0 = time.perf_counter()
-    oracle.advance(f64, pos[:, :256], DT, 2, oracle.SPLINE, I, M)
-    cal = (time.perf_counter() - t0) / (256 * 2)
+    cal = oracle_cost(f64, pos)
     n = int(max(512, min(NP, seconds / max(cal, 1e-9) / INNER)))
     t0 = time.perf_counter()
     oracle.advance(f64, pos[:, :n], DT, INNER, oracle.SPLINE, I, M)
@@ -208,9 +225,7 @@ def run_reference(args):
     field, pos = field_and_particles()
     f64 = field.astype(np.float64)
     # bounded sample per step, sized so the whole run stays within a few minutes
-    t0 = time.perf_counter()
-    oracle.advance(f64, pos[:, :256], DT, 2, oracle.SPLINE, I, M)
-    cal = (time.perf_counter() - t0) / (256 * 2)
+    cal = oracle_cost(f64, pos)
     per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
     n = int(max(256, min(NP, per_step_s / max(cal, 1e-9) / args.inner)))
     p = pos[:, :n].copy()
@@ -260,6 +275,8 @@ def run_gb300(args):
 
     field, pos = field_and_particles()
     tr = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
+    tr.set_step_kernel({"auto": trk.TRK_STEP_AUTO, "block": trk.TRK_STEP_BLOCK,
+                        "column": trk.TRK_STEP_COLUMN}[args.step_kernel])
     tr.set_field(torch.from_numpy(field).to(dev))
     p = torch.from_numpy(pos).to(dev)
     stream = torch.cuda.current_stream()
@@ -318,7 +335,8 @@ def run_gb300(args):
     alg_bytes = field_bytes + 52 * NP                 # field once + fp64 positions read and written + key
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    sha = kernel_source_sha()
+    kind = "block" if args.step_kernel == "block" else "column"
+    sha = kernel_source_sha(kind)
     gather_bytes = NP * 2 * I ** 3 * 3 * 4            # two stencil gathers per RK2 step, float32
     sm_mhz = clk.get("sm_mhz") or 1900.0
     smem_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * sm_mhz * 1e6 / 1e9
@@ -377,7 +395,7 @@ def run_gb300(args):
                        "positions": "f64", "l2": "inputs larger than L2 (201 MB field vs 129 MB L2)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": ncu_traffic(sha), "kernel": STEP_KERNEL,
+                         "traffic": ncu_traffic(sha, kind), "kernel": STEP_KERNELS[kind][0],
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                          "launches_timed": step_n, "peak_kind": peak_kind, "source_sha": sha},
             "smem_roofline": {"achieved": gather_bytes / avg_launch_s / 1e9, "peak": smem_peak, "unit": "GB/s",
