@@ -16,8 +16,10 @@
 //       weights -> u(X), J(X), J(X*)
 //   P2  thread per particle: the float64 lambda recurrence above
 //   Q2  warp per particle: W^T scatter into a shared-memory accumulator laid
-//       out like the halo (the halo buffer is re-used), then one float64
-//       atomic add per touched halo node into gfield.
+//       out like the halo (the halo buffer is re-used), then either plain
+//       stores of the accumulator into the block's slab of gscratch (summed
+//       per node afterwards by k_adj_gather, deterministic) or, without
+//       scratch, one float64 atomic add per touched halo node into gfield.
 #pragma once
 
 #include "block_kernel.cuh"
@@ -40,7 +42,7 @@ struct AdjPlan {
 };
 
 template <typename T, int I, int DEG, int STORE>
-__global__ void __launch_bounds__(NT, 1) k_adjoint(const __grid_constant__ AdjArgs a)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __grid_constant__ AdjArgs a)
 {
     constexpr int H = BLK + I - 1 + 2;
     constexpr int G = I / 2;
@@ -230,6 +232,16 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint(const __grid_constant__ AdjAr
             }
         }
         __syncthreads();
+        if (a.gscratch) {
+            // the block's partial sums, [3][H][H][H]; later batches of a crowded block add in
+            T* sb = reinterpret_cast<T*>(a.gscratch) + (int64_t)b * 3 * H * H * H;
+            for (int e = tid; e < 3 * H * H * H; e += NT) {
+                const int x = e % H, yz = e / H, y = yz % H, zk = yz / H, z = zk % H, k = zk / H;
+                const T val = halo[k * SC + z * S3 + y * S2 + x];
+                sb[e] = batch == j0 ? val : sb[e] + val;
+            }
+            continue;
+        }
         // flush the accumulator: one float64 atomic per touched halo node
         for (int e = tid; e < 3 * H * H * H; e += NT) {
             const int x = e % H, yz = e / H, y = yz % H, zk = yz / H, z = zk % H, k = zk / H;
@@ -240,6 +252,46 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint(const __grid_constant__ AdjAr
             }
         }
     }
+}
+
+// dLoss/dfield[k][node] += sum over the non-empty blocks whose halo holds the
+// node of their partial sums, in a fixed order (deterministic).  Along each
+// axis the blocks are those with integer index bi in
+// [ceil((x + G - H + 1) / BLK), floor((x + G) / BLK)], at halo offset
+// x + G - BLK bi in [0, H), taken mod nb (periodic images of the same block
+// included).
+template <typename T, int H>
+__global__ void k_adj_gather(const __grid_constant__ AdjArgs a)
+{
+    constexpr int G = (H - BLK - 1) / 2;                     // I / 2 for H = BLK + I + 1
+    const int N = a.g.N;
+    const int64_t NN3 = (int64_t)N * N * N;
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= NN3) return;
+    const int x1 = (int)(node % N), x2 = (int)((node / N) % N), x3 = (int)(node / ((int64_t)N * N));
+    auto fdiv = [](int p, int q) { return p >= 0 ? p / q : -((-p + q - 1) / q); };   // floor
+    auto cdiv = [&](int p, int q) { return -fdiv(-p, q); };                           // ceiling
+    auto pmod = [](int p, int q) { return ((p % q) + q) % q; };
+    double s0 = 0, s1 = 0, s2 = 0;
+    constexpr int H3 = H * H * H;
+    for (int bzi = cdiv(x3 + G - H + 1, BLK); bzi <= fdiv(x3 + G, BLK); ++bzi) {
+        const int hz = x3 + G - BLK * bzi, bz = pmod(bzi, a.g.nb3);
+        for (int byi = cdiv(x2 + G - H + 1, BLK); byi <= fdiv(x2 + G, BLK); ++byi) {
+            const int hy = x2 + G - BLK * byi, by = pmod(byi, a.g.nb2);
+            for (int bxi = cdiv(x1 + G - H + 1, BLK); bxi <= fdiv(x1 + G, BLK); ++bxi) {
+                const int hx = x1 + G - BLK * bxi, bx = pmod(bxi, a.g.nb1);
+                const int64_t b = ((int64_t)bz * a.g.nb2 + by) * a.g.nb1 + bx;
+                if (a.offsets[b + 1] == a.offsets[b]) continue;      // empty block: no partials
+                const T* sb = reinterpret_cast<const T*>(a.gscratch) + b * 3 * H3 + (hz * H + hy) * H + hx;
+                s0 += (double)sb[0];
+                s1 += (double)sb[H3];
+                s2 += (double)sb[2 * H3];
+            }
+        }
+    }
+    a.gfield[node] += s0;
+    a.gfield[NN3 + node] += s1;
+    a.gfield[2 * NN3 + node] += s2;
 }
 
 template <typename T, int I, int DEG, int STORE>

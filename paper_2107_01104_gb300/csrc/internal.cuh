@@ -101,6 +101,8 @@ struct AdjArgs {
     const double* lam_in;     // [3][np] dLoss/dX' (particle order)
     double* lam_out;          // [3][np] dLoss/dX   (particle order)
     double* gfield;           // [3][N^3] dLoss/dfield (dense, added into) or null
+    void* gscratch;           // [nblocks][3][H^3] per-block W^T partial sums (float, or double for
+                              // float64 storage), or null: float64 atomics instead
     double dt;
     int* flags;
 };
@@ -177,6 +179,11 @@ cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id
 // Fill the ghost-padded storage from a dense field src[C][N][N][N] (periodic ghosts).
 cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int C, int N, void* dst, cudaStream_t st);
 
+// dLoss/dfield from the per-block partial sums: every node adds, in a fixed
+// order, the partials of the non-empty blocks whose halo holds it
+cudaError_t launch_adjoint_gather(int I, const AdjArgs& a, cudaStream_t st);
+// halo edge of the adjoint kernel for kernel width I (stage-2 margin included)
+constexpr int adj_halo(int I) { return BLK + I - 1 + 2; }
 cudaError_t launch_adjoint_i4(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_adjoint_i6(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_adjoint_i8(const AdjArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);

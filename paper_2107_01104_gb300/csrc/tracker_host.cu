@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -135,6 +136,8 @@ struct tracker {
     // adjoint scratch: checkpoints, one segment of trajectory, lambda ping-pong
     size_t adj_bytes = 0;
     double* adj_buf = nullptr;
+    size_t adj_scratch_bytes = 0;    // per-block W^T partial sums of the field gradient
+    void* adj_scratch = nullptr;
     // CUDA-graph replay of step pairs, on a tracker-owned stream joined to the caller's
     cudaStream_t gstream = nullptr;
     cudaEvent_t gev[2] = {nullptr, nullptr};
@@ -550,6 +553,7 @@ int tracker_destroy(tracker* t)
     if (t->gstream) cudaStreamSynchronize(t->gstream);
     dev_free(t->d_flags);
     dev_free(t->adj_buf);
+    dev_free(t->adj_scratch);
     if (t->adv_graph.exec) cudaGraphExecDestroy(t->adv_graph.exec);
     if (t->batch_graph.exec) cudaGraphExecDestroy(t->batch_graph.exec);
     for (SetState& ss : t->sets) {
@@ -1071,6 +1075,25 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
         }
         t->adj_bytes = need;
     }
+    // deterministic field gradient: per-block partial sums + a gather per node,
+    // while the scratch stays below 8 GB (else float64 atomics per halo node)
+    void* gscratch = nullptr;
+    if (grad_field) {
+        const int H = adj_halo(t->I);
+        const size_t sb = (size_t)t->nblocks * 3 * H * H * H * (t->storage == TRK_F64 ? 8 : 4);
+        size_t cap = (size_t)8 << 30;
+        if (const char* env = getenv("TRK_ADJ_SCRATCH_BYTES")) cap = (size_t)strtoull(env, nullptr, 10);
+        if (sb <= cap) {
+            if (sb > t->adj_scratch_bytes) {
+                dev_free(t->adj_scratch);
+                t->adj_scratch = nullptr;
+                t->adj_scratch_bytes = 0;
+                if (dev_alloc(&t->adj_scratch, sb) == cudaSuccess) t->adj_scratch_bytes = sb;
+                else cudaGetLastError();
+            }
+            gscratch = t->adj_scratch;
+        }
+    }
     double* ckpt = t->adj_buf;
     double* seg = ckpt + (size_t)nseg * vec;
     double* lam[2] = {seg + (size_t)K * vec, seg + (size_t)(K + 1) * vec};
@@ -1108,9 +1131,15 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
             a.lam_in = lam[cur];
             a.lam_out = lam[cur ^ 1];
             a.gfield = grad_field;
+            a.gscratch = grad_field ? gscratch : nullptr;
             a.dt = dt;
             a.flags = t->d_flags;
             CUDA_TRY(launch_adjoint(t, a));
+            if (a.gscratch) {
+                ProfScope ps(t, PROF_STEP);
+                t->launches += 1;
+                CUDA_TRY(launch_adjoint_gather(t->I, a, t->stream));
+            }
             cur ^= 1;
         }
     }
