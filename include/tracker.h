@@ -226,6 +226,14 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
  *   lambda* = dt/2 J(X*)^T lambda,  mu = dt/2 lambda + dt lambda*,
  *   grad_field += W(X)^T mu + W(X*)^T (dt/2 lambda),
  *   lambda <- lambda + lambda* + J(X)^T mu.
+ * The field gradient is accumulated per cell block (shared memory) and then
+ * summed per grid node over the blocks whose halo holds it, in a fixed
+ * order, without global atomics.  That needs nblocks * 3 * (I + 9)^3 values
+ * of scratch (float32, float64 for TRK_F64 storage; 1.3 GB at N = 256,
+ * I = 6); when this exceeds the byte count in the environment variable
+ * TRK_ADJ_SCRATCH_BYTES (default 8 GiB) or cannot be allocated, each block
+ * adds its partial sums with float64 atomics instead (same values up to
+ * rounding order).
  * Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
 int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* lambdaT, double dt, int steps,
                     int ckpt_every, double* grad_pos0, double* grad_field);
