@@ -64,6 +64,26 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, device):
+    """The largest x over the ranks of the initialised process group (x itself
+    without one); device: where the collective's tensor lives (cuda for nccl,
+    cpu for gloo)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, ws, ms):
+    """Whole-job throughput: every rank's units (replicas: the same count on
+    each rank) over the slowest rank's time in milliseconds."""
+    return units_per_rank * ws / (ms * 1e-3)
+
+
 # --------------------------------------------------------------------------
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------
@@ -307,13 +327,9 @@ def run_gb300(args):
     clk = clocks.stop()
     launches = tr.launch_count - launches0
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     sync_flags(tr, trk, notes)
-    total_ps = NP * args.inner * args.steps * ws
-    value = total_ps / (ms * 1e-3)
+    value = job_value(NP * args.inner * args.steps, ws, ms)
 
     # ---------------- per-kernel times: a separate, profiled pass ----------------
     # (tracker_profile records events around every launch, which turns the
@@ -354,11 +370,9 @@ def run_gb300(args):
     w1.record(stream)
     barrier_sync()
     e2e_ms = w0.elapsed_time(w1)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": total_ps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": host.numel() * 8,
+    e2e_ms = max_over_ranks(e2e_ms, dev)
+    e2e = {"value": job_value(NP * args.inner * args.steps, ws, e2e_ms), "unit": UNIT,
+           "h2d_bytes_per_step": host.numel() * 8,
            "d2h_bytes_per_step": back.numel() * 8}
 
     # ---------------- other precision forms of the same workload ----------------
