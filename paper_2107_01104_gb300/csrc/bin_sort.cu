@@ -5,8 +5,12 @@
 //
 // The paper orders particles by x3 slice with an incomplete quicksort and
 // keeps an offset[] array of group starts.  Here the groups are blocks of
-// cells and the order is a stable radix sort, so the permutation is unique
-// and reproducible (ties keep the incoming order).
+// cells.  tracker_bin and the block-kernel steps use a stable radix sort, so
+// the permutation is unique and reproducible (ties keep the incoming order).
+// The column-kernel steps re-bin with a counting sort (block counts from the
+// update phase, one scan, one scatter of the state): the blocks and their
+// offsets are the same, the order inside a block is not reproducible, and no
+// result depends on it.
 #include <algorithm>
 
 #include "internal.cuh"

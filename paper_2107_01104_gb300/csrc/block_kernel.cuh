@@ -1,20 +1,26 @@
 // Block kernels: one CTA per cell block of BLK^3 cells (the block grouping of
-// Sec. 3.3.1, with the paper's x3 slices generalised to cubes).
+// Sec. 3.3.1, with the paper's x3 slices generalised to cubes).  They serve
+// interpolation, the batched steps, and the time steps of the storages and
+// kernel widths the column kernel (column_kernel.cuh) does not cover; this
+// file also holds the pieces both share (lane maps, weights, reductions).
 //
-// A CTA stages the block's field halo in shared memory once (16-byte vector
-// loads from the ghost-padded field) and then runs the per-particle work in
-// phases separated by __syncthreads():
+// A CTA stages the block's field halo in shared memory once (cp.async element
+// copies for float32/float64 storage, issued before P1 and completed before
+// the first barrier; 16-byte vector loads through registers for split bf16)
+// and runs the per-particle work in phases separated by __syncthreads():
 //
 //   P1  one thread per particle: read X through the sort permutation, split it
-//       into cell c and offset t (float64, Sec. 2.2 steps 1-3);
+//       into cell c and offset t (float64, Sec. 2.2 steps 1-3), keep X, the
+//       caller id and the AB2 history in shared memory for P3;
 //   Q   one warp per particle: evaluate the 1-D weights beta_i per axis, gather
 //       the I x I x I stencil from shared memory into registers and contract it
 //       (Eq. triple_sum, separably as in Sec. 3.3), reduce across the warp.
 //       For RK2 the warp then forms the stage-2 point in cell-relative
 //       coordinates, t* = t + dt u(X) / delta, and contracts again, re-using
 //       the stencil registers when X* lies in the same cell;
-//   P3  one thread per particle: float64 position update (RK2 or AB2), new cell
-//       split and block key for the next re-binning, coalesced write-out.
+//   P3  one thread per particle: float64 position update (RK2 or AB2) from the
+//       staged X, new cell split and block key for the next re-binning,
+//       coalesced write-out.
 //
 // Warp-per-particle lane maps (every warp-wide shared load hits 32 distinct
 // banks, see Layout):
