@@ -50,10 +50,9 @@
 namespace trk {
 
 constexpr int PBC = 64;              // particles per task
-constexpr int NQW = 8;               // interpolation warps
+constexpr int NQW = 10;              // interpolation warps
 constexpr int NQT = NQW * 32;        // interpolation threads
 constexpr int NTC = NQT + 32;        // threads per CTA: interpolation warps + the particle warp
-static_assert(NQW == NW, "the interpolation warps use the block kernel's per-warp weight buffers");
 
 template <int I, int H>
 struct RingGeom {
