@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(CS_THREADS) k_count_scan(uint32_t* __restrict_
     const bool vec = (nblocks & 3) == 0;      // every range then starts and ends on a 16-byte boundary
     uint32_t sum = 0;
     if (vec) {
-        for (int64_t i = i0; i < i1; i += 4) {
+#pragma unroll 8
+        for (int64_t i = i0; i < i1; i += 4) {   // unrolled: the loads are in flight together
             const uint4 c = *reinterpret_cast<const uint4*>(counts + i);
             sum += c.x + c.y + c.z + c.w;
         }
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_count_scan(uint32_t* __restrict_
     __syncthreads();
     uint32_t run = (w > 0 ? warp_tot[w - 1] : 0u) + inc - sum;
     if (vec) {
+#pragma unroll 8
         for (int64_t i = i0; i < i1; i += 4) {
             const uint4 c = *reinterpret_cast<const uint4*>(counts + i);
             const int4 o = make_int4((int)run, (int)(run + c.x), (int)(run + c.x + c.y), (int)(run + c.x + c.y + c.z));
