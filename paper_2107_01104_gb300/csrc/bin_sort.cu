@@ -51,69 +51,68 @@ __global__ void k_keys(GridGeom g, int64_t np, const double* __restrict__ pos, u
 
 // Block counts -> offsets (exclusive scan, offsets[nblocks] = total) and the
 // scatter cursors (a copy of the offsets); the counts are zeroed for the next
-// step.  One CTA: thread t owns the contiguous range [t P, (t + 1) P) with P
-// a multiple of 4 (16-byte vectors when nblocks is a multiple of 4); a first
-// pass sums each range (all loads of a thread independent), one block-wide
-// scan of the sums, and a second pass writes the prefixes.
+// step.  One CTA of CS_THREADS threads; warp w owns a contiguous chunk of the
+// counts and walks it with consecutive lanes (coalesced): a first pass sums
+// the chunk, one scan of the warp totals, and a second pass scans 32 counts
+// at a time with shuffles, carrying the running prefix.
 constexpr int CS_THREADS = 1024;
 
 __global__ void __launch_bounds__(CS_THREADS) k_count_scan(uint32_t* __restrict__ counts, int64_t nblocks,
                                                            int32_t* __restrict__ offsets, int32_t* __restrict__ cursor)
 {
-    __shared__ uint32_t warp_tot[CS_THREADS / 32];
+    constexpr int NWS = CS_THREADS / 32;
+    __shared__ uint32_t warp_pre[NWS];
+    __shared__ uint32_t s_total;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int64_t per = ((nblocks + CS_THREADS - 1) / CS_THREADS + 3) / 4 * 4;
-    const int64_t i0 = (int64_t)tid * per, i1 = min(i0 + per, nblocks);
-    const bool vec = (nblocks & 3) == 0;      // every range then starts and ends on a 16-byte boundary
+    const int64_t chunk = ((nblocks + NWS - 1) / NWS + 31) / 32 * 32;
+    const int64_t c0 = min((int64_t)w * chunk, nblocks), c1 = min(c0 + chunk, nblocks);
     uint32_t sum = 0;
-    if (vec) {
 #pragma unroll 8
-        for (int64_t i = i0; i < i1; i += 4) {   // unrolled: the loads are in flight together
-            const uint4 c = *reinterpret_cast<const uint4*>(counts + i);
-            sum += c.x + c.y + c.z + c.w;
-        }
-    } else {
-        for (int64_t i = i0; i < i1; ++i) sum += counts[i];
-    }
-    uint32_t inc = sum;
+    for (int64_t i = c0 + lane; i < c1; i += 32) sum += counts[i];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) warp_tot[w] = inc;
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) warp_pre[w] = sum;
     __syncthreads();
     if (w == 0) {
-        uint32_t x = warp_tot[lane];
+        const uint32_t x = warp_pre[lane];
+        uint32_t inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
-        warp_tot[lane] = x;                          // inclusive over warps
+        warp_pre[lane] = inc - x;                    // exclusive prefix of warp lane's chunk
+        if (lane == 31) s_total = inc;
     }
     __syncthreads();
-    uint32_t run = (w > 0 ? warp_tot[w - 1] : 0u) + inc - sum;
-    if (vec) {
-#pragma unroll 8
-        for (int64_t i = i0; i < i1; i += 4) {
-            const uint4 c = *reinterpret_cast<const uint4*>(counts + i);
-            const int4 o = make_int4((int)run, (int)(run + c.x), (int)(run + c.x + c.y), (int)(run + c.x + c.y + c.z));
-            *reinterpret_cast<int4*>(offsets + i) = o;
-            *reinterpret_cast<int4*>(cursor + i) = o;
-            *reinterpret_cast<uint4*>(counts + i) = make_uint4(0u, 0u, 0u, 0u);
-            run += c.x + c.y + c.z + c.w;
+    uint32_t carry = warp_pre[w];
+    constexpr int U = 8;                             // 32-count steps whose loads are issued together
+    for (int64_t base = c0; base < c1; base += 32 * U) {
+        uint32_t cv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + 32 * u + lane;
+            cv[u] = i < c1 ? counts[i] : 0u;
         }
-    } else {
-        for (int64_t i = i0; i < i1; ++i) {
-            const uint32_t c = counts[i];
-            offsets[i] = (int32_t)run;
-            cursor[i] = (int32_t)run;
-            counts[i] = 0u;
-            run += c;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + 32 * u + lane;
+            uint32_t inc = cv[u];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (i < c1) {
+                const int32_t e = (int32_t)(carry + inc - cv[u]);
+                offsets[i] = e;
+                cursor[i] = e;
+                counts[i] = 0u;
+            }
+            carry += __shfl_sync(0xffffffffu, inc, 31);
         }
     }
-    if (tid == CS_THREADS - 1) offsets[nblocks] = (int32_t)warp_tot[CS_THREADS / 32 - 1];
+    if (tid == 0) offsets[nblocks] = (int32_t)s_total;
 }
 
 // Counting-sort scatter of the particle state: particle j goes to the next
