@@ -204,27 +204,43 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
         for (int e = tid; e < 3 * SC; e += NT) halo[e] = (T)0;
         __syncthreads();
         const int64_t NN3 = (int64_t)N * N * N;
+        auto add_smem = [&](T* base) {
+            return [=](int k, int a1, int a2, int a3, T val) { atomicAdd(base + k * SC + a3 * S3 + a2 * S2 + a1, val); };
+        };
+        auto base_of = [&](int rp) {
+            return halo + ((rp >> 16) & 255) * S3 - LO * S3 + ((rp >> 8) & 255) * S2 - LO * S2 + (rp & 255) - LO;
+        };
         for (int q = warp; q < nbat; q += NW) {
+            const PRec<T> recs[2] = {p_rec[q], p_rec2[q]};
+            int rps[2];
 #pragma unroll
             for (int stage = 0; stage < 2; ++stage) {
-                const PRec<T> rec = stage == 0 ? p_rec[q] : p_rec2[q];
-                int rp;
-                if constexpr (sizeof(T) == 4) rp = __float_as_int(rec.relf);
-                else rp = (int)__double_as_longlong(rec.relf);
-                const T mu3[3] = {p_mu[q * 6 + 3 * stage + 0], p_mu[q * 6 + 3 * stage + 1],
-                                  p_mu[q * 6 + 3 * stage + 2]};
+                if constexpr (sizeof(T) == 4) rps[stage] = __float_as_int(recs[stage].relf);
+                else rps[stage] = (int)__double_as_longlong(recs[stage].relf);
+            }
+            const T mus[2][3] = {{p_mu[q * 6 + 0], p_mu[q * 6 + 1], p_mu[q * 6 + 2]},
+                                 {p_mu[q * 6 + 3], p_mu[q * 6 + 4], p_mu[q * 6 + 5]}};
+            if (rps[0] >= 0 && rps[0] == rps[1]) {
+                // X and X* in the same cell: one stencil, both weight sets, one add per node
+                const T sa[3] = {recs[0].t[0] - (T)0.5, recs[0].t[1] - (T)0.5, recs[0].t[2] - (T)0.5};
+                const T sb[3] = {recs[1].t[0] - (T)0.5, recs[1].t[1] - (T)0.5, recs[1].t[2] - (T)0.5};
+                W.eval_values2(sa, sb, wv, wd);
+                L.template scatter_n<true>(wv, mus[0], wd, mus[1], add_smem(base_of(rps[0])));
+                continue;
+            }
+#pragma unroll
+            for (int stage = 0; stage < 2; ++stage) {
+                const PRec<T>& rec = recs[stage];
+                const int rp = rps[stage];
                 W.eval(rec.t[0] - (T)0.5, rec.t[1] - (T)0.5, rec.t[2] - (T)0.5, wv, wd);
                 if (rp >= 0) {
-                    T* base = halo + ((rp >> 16) & 255) * S3 - LO * S3 + ((rp >> 8) & 255) * S2 - LO * S2 +
-                              (rp & 255) - LO;
-                    L.scatter(wv, mu3, [&](int k, int a1, int a2, int a3, T val) {
-                        atomicAdd(base + k * SC + a3 * S3 + a2 * S2 + a1, val);
-                    });
+                    L.template scatter_n<false>(wv, mus[stage], wv, mus[stage], add_smem(base_of(rp)));
                 } else {
                     const int pc = stage == 0 ? p_cell[q] : p_cell2[q];
                     const int c1 = pc & 1023, c2 = (pc >> 10) & 1023, c3 = (pc >> 20) & 1023;
                     double* gf = a.gfield;
-                    L.scatter(wv, mu3, [&](int k, int a1, int a2, int a3, T val) {
+                    L.template scatter_n<false>(wv, mus[stage], wv, mus[stage],
+                                                [&](int k, int a1, int a2, int a3, T val) {
                         const int x1 = (c1 + a1 - LO) & mask, x2 = (c2 + a2 - LO) & mask, x3 = (c3 + a3 - LO) & mask;
                         atomicAdd(gf + k * NN3 + ((int64_t)x3 * N + x2) * N + x1, (double)val);
                     });

@@ -221,6 +221,19 @@ struct WeightEval {
         if (D && act) wd[ax * 8 + i] = dw;
         __syncwarp();
     }
+    // value weights (no derivatives) of two points a and b into wva and wvb
+    __device__ __forceinline__ void eval_values2(const T (&sa)[3], const T (&sb)[3], T* wva, T* wvb) const
+    {
+        const T xa = ax == 0 ? sa[0] : (ax == 1 ? sa[1] : sa[2]);
+        const T xb = ax == 0 ? sb[0] : (ax == 1 ? sb[1] : sb[2]);
+        const T wa = horner(r, xa), wb = horner(r, xb);
+        __syncwarp();
+        if (act) {
+            wva[ax * 8 + i] = wa;
+            wvb[ax * 8 + i] = wb;
+        }
+        __syncwarp();
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -262,19 +275,24 @@ struct Lane<T, 8, D> {
                     for (int i3 = 0; i3 < 8; ++i3) f[k][h][i3] = ld(k, i1, j + 4 * h, i3);
         }
     }
-    // transpose of the gather: add w(node) mu_k into every node this lane gathers
-    template <class ADD>
-    __device__ __forceinline__ void scatter(const T* wv, const T (&mu)[3], const ADD& add) const
+    // transpose of the gather: add w(node) mu_k into every node this lane
+    // gathers; TWO adds wa(node) ma_k + wb(node) mb_k (two weight sets on the
+    // same stencil) with one add per node
+    template <bool TWO, class ADD>
+    __device__ __forceinline__ void scatter_n(const T* wa, const T (&ma)[3], const T* wb, const T (&mb)[3],
+                                              const ADD& add) const
     {
-        const T w1 = wv[i1];
+        const T w1a = wa[i1], w1b = TWO ? wb[i1] : (T)0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const T a12 = w1 * wv[8 + j + 4 * h];
+            const T a12a = w1a * wa[8 + j + 4 * h];
+            const T a12b = TWO ? w1b * wb[8 + j + 4 * h] : (T)0;
 #pragma unroll
             for (int i3 = 0; i3 < 8; ++i3) {
-                const T w = a12 * wv[16 + i3];
+                const T wA = a12a * wa[16 + i3];
+                const T wB = TWO ? a12b * wb[16 + i3] : (T)0;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) add(k, i1, j + 4 * h, i3, w * mu[k]);
+                for (int k = 0; k < 3; ++k) add(k, i1, j + 4 * h, i3, TWO ? fma(wA, ma[k], wB * mb[k]) : wA * ma[k]);
             }
         }
     }
@@ -358,26 +376,29 @@ struct Lane<T, 6, D> {
             }
         }
     }
-    template <class ADD>
-    __device__ __forceinline__ void scatter(const T* wv, const T (&mu)[3], const ADD& add) const
+    template <bool TWO, class ADD>
+    __device__ __forceinline__ void scatter_n(const T* wa, const T (&ma)[3], const T* wb, const T (&mb)[3],
+                                              const ADD& add) const
     {
-        const T w1 = wv[i1], w25 = wv[13];
+        auto val = [&](T wA, T wB, int k) { return TWO ? fma(wA, ma[k], wB * mb[k]) : wA * ma[k]; };
+        const T w1a = wa[i1], w25a = wa[13];
+        const T w1b = TWO ? wb[i1] : (T)0, w25b = TWO ? wb[13] : (T)0;
         if (act) {
-            const T a12 = w1 * wv[8 + j];
+            const T a12a = w1a * wa[8 + j], a12b = TWO ? w1b * wb[8 + j] : (T)0;
 #pragma unroll
             for (int i3 = 0; i3 < 6; ++i3) {
-                const T w = a12 * wv[16 + i3];
+                const T wA = a12a * wa[16 + i3], wB = TWO ? a12b * wb[16 + i3] : (T)0;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) add(k, i1, j, i3, w * mu[k]);
+                for (int k = 0; k < 3; ++k) add(k, i1, j, i3, val(wA, wB, k));
             }
-            const T wb = w1 * w25 * wv[16 + j];
+            const T wA = w1a * w25a * wa[16 + j], wB = TWO ? w1b * w25b * wb[16 + j] : (T)0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) add(k, i1, 5, j, wb * mu[k]);
+            for (int k = 0; k < 3; ++k) add(k, i1, 5, j, val(wA, wB, k));
         }
         if (actc) {
-            const T wc = w1 * w25 * wv[21];
+            const T wA = w1a * w25a * wa[21], wB = TWO ? w1b * w25b * wb[21] : (T)0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) add(k, i1, 5, 5, wc * mu[k]);
+            for (int k = 0; k < 3; ++k) add(k, i1, 5, 5, val(wA, wB, k));
         }
     }
     __device__ __forceinline__ void contract(const T* wv, const T* wd, T (&acc)[12]) const
@@ -451,15 +472,18 @@ struct Lane<T, 4, D> {
             }
         }
     }
-    template <class ADD>
-    __device__ __forceinline__ void scatter(const T* wv, const T (&mu)[3], const ADD& add) const
+    template <bool TWO, class ADD>
+    __device__ __forceinline__ void scatter_n(const T* wa, const T (&ma)[3], const T* wb, const T (&mb)[3],
+                                              const ADD& add) const
     {
-        const T a12 = wv[i1] * wv[8 + i2];
-        const T wa = a12 * wv[16 + p], wb = a12 * wv[18 + p];
+        auto val = [&](T wA, T wB, int k) { return TWO ? fma(wA, ma[k], wB * mb[k]) : wA * ma[k]; };
+        const T a12a = wa[i1] * wa[8 + i2], a12b = TWO ? wb[i1] * wb[8 + i2] : (T)0;
+        const T w0a = a12a * wa[16 + p], w1a = a12a * wa[18 + p];
+        const T w0b = TWO ? a12b * wb[16 + p] : (T)0, w1b = TWO ? a12b * wb[18 + p] : (T)0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            add(k, i1, i2, p, wa * mu[k]);
-            add(k, i1, i2, p + 2, wb * mu[k]);
+            add(k, i1, i2, p, val(w0a, w0b, k));
+            add(k, i1, i2, p + 2, val(w1a, w1b, k));
         }
     }
     __device__ __forceinline__ void contract(const T* wv, const T* wd, T (&acc)[12]) const
