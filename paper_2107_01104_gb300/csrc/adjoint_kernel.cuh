@@ -28,6 +28,20 @@ namespace trk {
 
 constexpr int PBA = 128;   // particles per adjoint batch (keeps the float64 I = 8 plan under 227 KB)
 
+// two-element vector of T for zeroing shared memory
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+    __device__ static float2 zero() { return make_float2(0.0f, 0.0f); }
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+};
+
 template <typename T, int SC>
 struct AdjPlan {
     static constexpr size_t rec = align32((size_t)3 * SC * sizeof(T));
@@ -201,7 +215,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             continue;
         }
         // ---------------- Q2: W^T scatter ----------------
-        for (int e = tid; e < 3 * SC; e += NT) halo[e] = (T)0;
+        static_assert(SC % 2 == 0, "the accumulator is zeroed two values at a time");
+        for (int e = tid; e < 3 * SC / 2; e += NT) reinterpret_cast<typename Vec2<T>::type*>(halo)[e] = Vec2<T>::zero();
         __syncthreads();
         const int64_t NN3 = (int64_t)N * N * N;
         auto add_smem = [&](T* base) {
@@ -250,11 +265,20 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
         __syncthreads();
         if (a.gscratch) {
             // the block's partial sums, [3][H][H][H]; later batches of a crowded block add in
+            // thread t owns column x, row y of every (component, plane): no index division per element
             T* sb = reinterpret_cast<T*>(a.gscratch) + (int64_t)b * 3 * H * H * H;
-            for (int e = tid; e < 3 * H * H * H; e += NT) {
-                const int x = e % H, yz = e / H, y = yz % H, zk = yz / H, z = zk % H, k = zk / H;
-                const T val = halo[k * SC + z * S3 + y * S2 + x];
-                sb[e] = batch == j0 ? val : sb[e] + val;
+            constexpr int RP = NT / H;                           // rows per pass
+            const int x = tid % H, yr = tid / H;
+            if (yr < RP) {
+                for (int kz = 0; kz < 3 * H; ++kz) {             // (component, plane) pairs
+                    const int k = kz / H, z = kz - (kz / H) * H;
+                    const T* src = halo + k * SC + z * S3 + x;
+                    T* dst = sb + (int64_t)kz * H * H + x;
+                    for (int y = yr; y < H; y += RP) {
+                        const T val = src[y * S2];
+                        dst[y * H] = batch == j0 ? val : dst[y * H] + val;
+                    }
+                }
             }
             continue;
         }
