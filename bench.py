@@ -355,7 +355,11 @@ def run_gb300(args):
     sha = kernel_source_sha(kind)
     gather_bytes = NP * 2 * I ** 3 * 3 * 4            # two stencil gathers per RK2 step, float32
     sm_mhz = clk.get("sm_mhz") or 1900.0
-    smem_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * sm_mhz * 1e6 / 1e9
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    smem_peak = nsm * 128 * sm_mhz * 1e6 / 1e9
+    # separable contraction: per stage and component I^3 + I^2 + I FMAs (x1 sums, then x2, then x3)
+    fma_per_ps = 2 * 3 * (I ** 3 + I ** 2 + I)
+    fp32_peak = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s, FP32 SIMT FMA
 
     # ---------------- end-to-end through the public API ----------------
     host = torch.from_numpy(pos).pin_memory()
@@ -412,6 +416,10 @@ def run_gb300(args):
                          "traffic": ncu_traffic(sha, kind), "kernel": STEP_KERNELS[kind][0],
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                          "launches_timed": step_n, "peak_kind": peak_kind, "source_sha": sha},
+            "fma_roofline": {"achieved": NP * fma_per_ps * 2 / avg_launch_s / 1e12, "peak": fp32_peak,
+                             "unit": "TFLOP/s", "frac": NP * fma_per_ps * 2 / avg_launch_s / 1e12 / fp32_peak,
+                             "fma_per_particle_step": fma_per_ps,
+                             "peak_def": "SMs x 128 FP32 FMA/clk x 2 FLOP x median SM clock under load"},
             "smem_roofline": {"achieved": gather_bytes / avg_launch_s / 1e9, "peak": smem_peak, "unit": "GB/s",
                               "frac": gather_bytes / avg_launch_s / 1e9 / smem_peak,
                               "gather_bytes_per_launch": gather_bytes,
