@@ -14,7 +14,7 @@ Functions and the passage of arXiv:2107.01104 each one follows:
                           construction, built procedurally)
 * :func:`bin_particles`-- Sec. 3.3.1, slice/block ordering with an ``offset`` array
 * :func:`interp`       -- Sec. 2.2 step 4, Eq. (triple_sum), direct quadruple loop
-* :func:`advance`      -- Eq. (tracers) with RK2 (Heun) or AB2 (Sec. 2.2, 3.3.1)
+* :func:`advance`      -- Eq. (tracers) with RK2 (Heun) or AB2/AB3/AB4 (Sec. 2.2, 3.3.1)
 * :func:`adjoint_rk2`  -- discrete adjoint of the RK2 map (no counterpart in the paper)
 """
 from __future__ import annotations
@@ -34,7 +34,7 @@ _lock = threading.Lock()
 _lib = None
 
 LAGRANGE, SPLINE = 0, 1
-RK2, AB2 = 0, 1
+RK2, AB2, AB3, AB4 = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -158,19 +158,27 @@ def interp_stencil(frac, stencil, family: int, I: int, m: int = 0):
 
 
 def advance(field, pos, dt: float, steps: int, family: int, I: int, m: int = 0, scheme: int = RK2,
-            rhs=None, history_valid: bool = False, L: float = 2 * np.pi):
-    """Integrate Eq. (tracers) for ``steps`` steps.  Returns new positions (and rhs history for AB2)."""
+            rhs=None, history_valid=0, L: float = 2 * np.pi):
+    """Integrate Eq. (tracers) for ``steps`` steps.
+
+    RK2 returns the new positions.  ABk (AB2, AB3, AB4: k = scheme + 1)
+    returns (positions, rhs): rhs holds the k-1 newest u, [k-1][3][np]
+    (AB2: [3][np]), u_{n-1} first; ``history_valid`` entries of the given rhs
+    are valid on entry (True counts as 1).
+    """
     field = _f64(field)
     pos = _f64(pos).copy()
     N = field.shape[-1]
     np_ = pos.shape[1]
-    if scheme == AB2:
-        rhs = np.zeros((3, np_)) if rhs is None else _f64(rhs).copy()
-    rc = _load().orc_advance(family, I, m, N, L, _ptr(field), np_, _ptr(pos),
-                             _ptr(rhs) if scheme == AB2 else None,
+    k = 0 if scheme == RK2 else scheme + 1
+    if k:
+        rhs = np.zeros((k - 1, 3, np_)) if rhs is None else _f64(rhs).reshape(k - 1, 3, np_).copy()
+    rc = _load().orc_advance(family, I, m, N, L, _ptr(field), np_, _ptr(pos), _ptr(rhs) if k else None,
                              float(dt), int(steps), int(scheme), int(history_valid))
     _check(rc, "advance")
-    return (pos, rhs) if scheme == AB2 else pos
+    if not k:
+        return pos
+    return pos, (rhs[0] if k == 2 else rhs)
 
 
 def adjoint_rk2(field, pos0, lambdaT, dt: float, steps: int, family: int, I: int, m: int = 0,

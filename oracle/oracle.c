@@ -355,11 +355,24 @@ int orc_interp_stencil(int family, int I, int m, int C, int64_t np, const double
 /*  scheme 0, RK2 (Heun, explicit trapezoid; the paper's particle stepper is */
 /*    Adams-Bashforth, RK2 is the second scheme this library offers):        */
 /*      k1 = u(X), X* = X + dt k1, k2 = u(X*), X' = X + dt/2 (k1 + k2)       */
-/*  scheme 1, AB2 (multi-step Adams-Bashforth, Sec. 2.2 / Sec. 3.3.1 "rhs"): */
-/*      X' = X + dt (3/2 u_n - 1/2 u_{n-1});  with no history yet the step   */
-/*      is forward Euler, X' = X + dt u_n.  rhs[3][np] holds u_{n-1} and is  */
-/*      overwritten with u_n.                                               */
+/*  schemes 1, 2, 3: ABk, k = 2, 3, 4 (multi-step Adams-Bashforth, Sec. 2.2 */
+/*    and the "rhs" history of Sec. 3.3.1):                                  */
+/*      X' = X + dt sum_{j<q} beta^q_j u_{n-j},  q = min(k, 1 + history),     */
+/*    the textbook Adams-Bashforth weights of order q (q = 1: forward Euler, */
+/*    2: 3/2, -1/2; 3: 23/12, -16/12, 5/12; 4: 55/24, -59/24, 37/24,        */
+/*    -9/24): a step takes the highest order its stored history allows, so  */
+/*    the first k-1 steps without history start at lower orders.  rhs holds  */
+/*    k-1 entries [k-1][3][np], u_{n-1} first; `history_valid` of them are   */
+/*    valid on entry; on return they hold the k-1 newest u.                  */
 /* ------------------------------------------------------------------------ */
+/* Adams-Bashforth weights by order q (row q - 1), newest rhs first */
+static const double AB_BETA[4][4] = {
+    { 1.0, 0.0, 0.0, 0.0 },
+    { 3.0 / 2.0, -1.0 / 2.0, 0.0, 0.0 },
+    { 23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0, 0.0 },
+    { 55.0 / 24.0, -59.0 / 24.0, 37.0 / 24.0, -9.0 / 24.0 },
+};
+
 static int eval_u(const struct orc_kernel* K, const double* f, int N, double inv_delta,
                   const double X[3], double u[3])
 {
@@ -383,15 +396,19 @@ int orc_advance(int family, int I, int m, int N, double L, const double* field,
 {
     struct orc_kernel K = { family, I, m };
     if (orc_check_kernel(family, I, m)) return -1;
-    if (scheme == 1 && !rhs) return -1;
+    if (scheme < 0 || scheme > 3) return -1;
+    const int k = scheme == 0 ? 0 : scheme + 1;          /* AB order */
+    if (k && !rhs) return -1;
+    if (k && (history_valid < 0 || history_valid > k - 1)) return -1;
     double inv_delta = orc_inv_delta(N, L);
     int bad = 0;
     #pragma omp parallel for schedule(dynamic, 256) reduction(|:bad)
     for (int64_t p = 0; p < np; ++p) {
         double X[3] = { pos[p], pos[np + p], pos[2 * np + p] };
-        double H[3] = { 0, 0, 0 };
+        double H[3][3] = { { 0 } };                     /* H[e][a] = u_{n-1-e}, axis a */
         int hv = history_valid;
-        if (scheme == 1) for (int a = 0; a < 3; ++a) H[a] = rhs[a * np + p];
+        for (int e = 0; e < k - 1; ++e)
+            for (int a = 0; a < 3; ++a) H[e][a] = rhs[((int64_t)e * 3 + a) * np + p];
         for (int s = 0; s < steps; ++s) {
             double k1[3];
             if (eval_u(&K, field, N, inv_delta, X, k1)) { bad = 1; break; }
@@ -401,16 +418,21 @@ int orc_advance(int family, int I, int m, int N, double L, const double* field,
                 if (eval_u(&K, field, N, inv_delta, Xs, k2)) { bad = 1; break; }
                 for (int a = 0; a < 3; ++a) X[a] = X[a] + 0.5 * dt * (k1[a] + k2[a]);
             } else {
+                const int q = hv + 1 < k ? hv + 1 : k;
                 for (int a = 0; a < 3; ++a) {
-                    double inc = hv ? (1.5 * k1[a] - 0.5 * H[a]) : k1[a];
+                    double inc = AB_BETA[q - 1][0] * k1[a];
+                    for (int j = 1; j < q; ++j) inc += AB_BETA[q - 1][j] * H[j - 1][a];
                     X[a] = X[a] + dt * inc;
-                    H[a] = k1[a];
                 }
-                hv = 1;
+                for (int e = k - 2; e > 0; --e)
+                    for (int a = 0; a < 3; ++a) H[e][a] = H[e - 1][a];
+                for (int a = 0; a < 3; ++a) H[0][a] = k1[a];
+                if (hv < k - 1) ++hv;
             }
         }
         for (int a = 0; a < 3; ++a) pos[a * np + p] = X[a];
-        if (scheme == 1) for (int a = 0; a < 3; ++a) rhs[a * np + p] = H[a];
+        for (int e = 0; e < k - 1; ++e)
+            for (int a = 0; a < 3; ++a) rhs[((int64_t)e * 3 + a) * np + p] = H[e][a];
     }
     return bad ? -4 : 0;
 }

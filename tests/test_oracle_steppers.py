@@ -93,3 +93,100 @@ def test_global_error_is_second_order(scheme):
         errs.append(np.abs(out - exact).max())
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(orders - 2.0) < 0.25), (errs, orders)
+
+
+# ---------------------------------------------------------------------------
+# Higher-order Adams-Bashforth (AB3, AB4)
+# ---------------------------------------------------------------------------
+def ab_weights_textbook(q):
+    """Adams-Bashforth weights of order q from their definition: the integral
+    over one step (s in [0, 1]) of the Lagrange basis polynomials on the past
+    nodes s = 0, -1, ..., -(q-1) (newest first)."""
+    nodes = -np.arange(q, dtype=float)
+    w = []
+    for j in range(q):
+        p = np.poly1d([1.0])
+        for i in range(q):
+            if i != j:
+                p = p * np.poly1d([1.0, -nodes[i]]) / (nodes[j] - nodes[i])
+        P = p.integ()
+        w.append(P(1.0) - P(0.0))
+    return np.array(w)
+
+
+@pytest.mark.parametrize("scheme,k", [(oracle.AB2, 2), (oracle.AB3, 3), (oracle.AB4, 4)])
+def test_ab_weights_match_their_definition(scheme, k):
+    """One step in a uniform field u with a chosen history isolates each weight:
+    X' - X = dt (beta_0 u + sum_j beta_j H_{j-1})."""
+    N, dt = 16, 0.1
+    u0 = np.array([0.25, 0.0, 0.0])
+    f = np.broadcast_to(u0[:, None, None, None], (3, N, N, N)).copy()
+    pos = np.array([[1.0], [2.0], [3.0]])
+    for hv in range(k):                      # history length -> order q = hv + 1
+        q = hv + 1
+        got = []
+        # beta_0 from a zero history, beta_j from a unit history entry j-1 on axis 1
+        out, _ = oracle.advance(f, pos, dt, 1, oracle.SPLINE, 4, 1, scheme=scheme,
+                                rhs=np.zeros((k - 1, 3, 1)), history_valid=hv)
+        got.append((out[0, 0] - pos[0, 0]) / (dt * u0[0]))
+        for j in range(1, q):
+            H = np.zeros((k - 1, 3, 1))
+            H[j - 1, 1, 0] = 1.0
+            out, _ = oracle.advance(f, pos, dt, 1, oracle.SPLINE, 4, 1, scheme=scheme, rhs=H, history_valid=hv)
+            got.append((out[1, 0] - pos[1, 0]) / dt)
+        np.testing.assert_allclose(got, ab_weights_textbook(q), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("scheme,k", [(oracle.AB3, 3), (oracle.AB4, 4)])
+def test_ab_global_error_order_with_exact_history(scheme, k):
+    """Rotation field, history taken from the exact solution: global error ~ dt^k."""
+    N = 32
+    f = linear_field(N, A_ROT, XC)
+    pos = XC[:, None] + np.random.default_rng(5).uniform(-0.5, 0.5, (3, 20))
+    T = 0.8
+    y0 = pos - XC[:, None]
+    exact = XC[:, None] + scipy.linalg.expm(T * A_ROT) @ y0
+    errs = []
+    for n in (16, 32, 64):
+        h = T / n
+        H = np.stack([A_ROT @ scipy.linalg.expm(-(e + 1) * h * A_ROT) @ y0 for e in range(k - 1)])
+        out, _ = oracle.advance(f, pos, h, n, oracle.SPLINE, 6, 2, scheme=scheme, rhs=H, history_valid=k - 1)
+        errs.append(np.abs(out - exact).max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - k) < 0.3), (errs, orders)
+
+
+@pytest.mark.parametrize("scheme,k", [(oracle.AB3, 3), (oracle.AB4, 4)])
+def test_ab_start_up_uses_lower_orders(scheme, k):
+    """Without history the first k-1 steps of ABk are those of AB(k-1)."""
+    N = 16
+    f = linear_field(N, A_ROT, XC)
+    pos = XC[:, None] + np.random.default_rng(6).uniform(-0.4, 0.4, (3, 25))
+    hi, _ = oracle.advance(f, pos, 0.03, k - 1, oracle.SPLINE, 4, 1, scheme=scheme)
+    lo, _ = oracle.advance(f, pos, 0.03, k - 1, oracle.SPLINE, 4, 1, scheme=scheme - 1)
+    np.testing.assert_array_equal(hi, lo)
+
+
+@pytest.mark.parametrize("scheme,k", [(oracle.AB3, 3), (oracle.AB4, 4)])
+def test_ab_history_continues(scheme, k):
+    N = 16
+    f = linear_field(N, A_ROT, XC)
+    pos = XC[:, None] + np.random.default_rng(7).uniform(-0.4, 0.4, (3, 30))
+    a, ra = oracle.advance(f, pos, 0.03, 11, oracle.LAGRANGE, 4, 0, scheme=scheme)
+    for first in (1, 2, 5):
+        b, rb = oracle.advance(f, pos, 0.03, first, oracle.LAGRANGE, 4, 0, scheme=scheme)
+        b, rb = oracle.advance(f, b, 0.03, 11 - first, oracle.LAGRANGE, 4, 0, scheme=scheme, rhs=rb,
+                               history_valid=min(first, k - 1))
+        np.testing.assert_allclose(a, b, atol=1e-14)
+        np.testing.assert_allclose(ra, rb, atol=1e-14)
+
+
+@pytest.mark.parametrize("scheme", [oracle.AB3, oracle.AB4])
+def test_ab_uniform_flow_is_exact(scheme):
+    N = 16
+    u0 = np.array([0.7, -1.1, 0.35])
+    f = np.broadcast_to(u0[:, None, None, None], (3, N, N, N)).copy()
+    pos = np.random.default_rng(8).uniform(0, L, (3, 100))
+    out, rhs = oracle.advance(f, pos, 0.01, 37, oracle.SPLINE, 6, 2, scheme=scheme)
+    np.testing.assert_allclose(out, pos + 37 * 0.01 * u0[:, None], atol=1e-12)
+    np.testing.assert_allclose(rhs, np.broadcast_to(u0[None, :, None], rhs.shape), atol=1e-14)
