@@ -398,6 +398,26 @@ def run_gb300(args):
             vms = v0.elapsed_time(v1)
             variants[name] = {"value": NP * inner * reps / (vms * 1e-3), "unit": UNIT, "rk2_steps": inner * reps}
             tv.close()
+        # Adams-Bashforth of orders 2 and 4 (one field evaluation per step), f32 field,
+        # history already full when the timed steps start
+        for name, scheme in (("ab2", trk.TRK_AB2), ("ab4", trk.TRK_AB4)):
+            k = scheme + 1
+            pv = torch.from_numpy(pos).to(dev)
+            hist = torch.zeros((k - 1, 3, NP), dtype=torch.float32, device=dev)
+            tr.advance(pv, DT, k - 1, scheme, rhs=hist, history_valid=0)
+            tr.advance(pv, DT, args.inner, scheme, rhs=hist, history_valid=k - 1)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 2
+            v0.record(stream)
+            for _ in range(reps):
+                tr.advance(pv, DT, args.inner, scheme, rhs=hist, history_valid=k - 1)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vms = v0.elapsed_time(v1)
+            variants[name] = {"value": NP * args.inner * reps / (vms * 1e-3), "unit": UNIT,
+                              "ab_steps": args.inner * reps, "field_storage": "f32"}
+            del pv, hist
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

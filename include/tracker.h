@@ -60,7 +60,7 @@ typedef enum { TRK_LAGRANGE = 0, TRK_SPLINE = 1 } trk_family;
  * significant bits). */
 typedef enum { TRK_F64 = 0, TRK_F32 = 1, TRK_BF16X2 = 2 } trk_storage;
 
-typedef enum { TRK_RK2 = 0, TRK_AB2 = 1 } trk_scheme;
+typedef enum { TRK_RK2 = 0, TRK_AB2 = 1, TRK_AB3 = 2, TRK_AB4 = 3 } trk_scheme;
 
 typedef enum { TRK_DTYPE_F64 = 0, TRK_DTYPE_F32 = 1 } trk_dtype;
 
@@ -154,16 +154,24 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
  * 3-component field (C must be 3).
  *   TRK_RK2 (Heun): k1 = u(X), X* = X + dt k1, k2 = u(X*),
  *                   X' = X + dt/2 (k1 + k2).
- *   TRK_AB2 (Adams-Bashforth, the paper's multi-step scheme, Sec. 2.2 and
- *            the rhs array of Sec. 3.3.1):
- *                   X' = X + dt (3/2 u_n - 1/2 u_{n-1}); when
- *                   history_valid = 0 the first step is forward Euler.
- *                   rhs[3][np] (float32, caller order) holds u_{n-1} on
- *                   entry when history_valid = 1 and u of the last step
- *                   on return.  rhs may be NULL for RK2.
+ *   TRK_AB2, TRK_AB3, TRK_AB4 (Adams-Bashforth of order k = 2, 3, 4, the
+ *            paper's multi-step scheme, Sec. 2.2 and the rhs array of
+ *            Sec. 3.3.1):
+ *                   X' = X + dt sum_{j<q} beta^q_j u_{n-j},
+ *                   q = min(k, 1 + number of valid history entries), with
+ *                   the textbook weights (q = 1 forward Euler; 2: 3/2,
+ *                   -1/2; 3: 23/12, -16/12, 5/12; 4: 55/24, -59/24, 37/24,
+ *                   -9/24), so a run without history starts at lower
+ *                   orders.  rhs[k-1][3][np] (float32, caller order) holds
+ *                   u_{n-1}, u_{n-2}, ... (newest first); history_valid
+ *                   (0 .. k-1) says how many of them are valid on entry; on
+ *                   return rhs holds the k-1 newest u (entries not yet
+ *                   filled are zero) and min(history_valid + steps, k-1)
+ *                   of them are valid.  rhs may be NULL for RK2.
  * pos[3][np] is read and overwritten in the caller's order.  Particles are
  * re-binned after every step (the update/re-sort of Sec. 3.3.1); the steps
- * are replayed from a captured CUDA graph.  A particle that moves more
+ * are replayed from a captured CUDA graph (Adams-Bashforth runs step by step
+ * until its history is full).  A particle that moves more
  * than one cell in one stage is still computed exactly (through a slower
  * path) and raises TRK_ECFL at the next tracker_sync.
  * Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
@@ -204,8 +212,9 @@ typedef struct {
     int deriv;           /* 0: outputs u; 1: outputs the gradient as well */
 } trk_set;
 
-/* Advance every set by `steps` AB2 steps (history_valid as in
- * tracker_advance, applied to all sets) in the tracker's 3-component
+/* Advance every set by `steps` AB2 steps (history_valid: 0 = no history,
+ * any other value = the one AB2 entry is valid; applied to all sets) in the
+ * tracker's 3-component
  * field.  Each step is one persistent kernel over a shared work list of
  * (set, block) items, so sets of very different sizes and kernels share
  * one launch; the step sequence is captured in a CUDA graph and replayed.

@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libtracker.so")
 TRK_OK, TRK_EINVAL, TRK_ENOMEM, TRK_ECUDA, TRK_ENONFINITE, TRK_ENOFIELD, TRK_ECFL = 0, -1, -2, -3, -4, -6, -7
 TRK_LAGRANGE, TRK_SPLINE = 0, 1
 TRK_F64, TRK_F32, TRK_BF16X2 = 0, 1, 2
-TRK_RK2, TRK_AB2 = 0, 1
+TRK_RK2, TRK_AB2, TRK_AB3, TRK_AB4 = 0, 1, 2, 3
 TRK_DTYPE_F64, TRK_DTYPE_F32 = 0, 1
 TRK_STEP_AUTO, TRK_STEP_BLOCK, TRK_STEP_COLUMN = 0, 1, 2
 
@@ -238,12 +238,18 @@ def tracker_interpolate(h, pos, C, out=None, out_dtype=torch.float32, deriv=Fals
     return out
 
 
-def tracker_advance(h, pos, dt, steps, scheme=TRK_RK2, rhs=None, history_valid=False):
+def tracker_advance(h, pos, dt, steps, scheme=TRK_RK2, rhs=None, history_valid=0):
+    """RK2 or ABk (k = scheme + 1).  rhs: AB history, [k-1][3][np] float32 on the
+    device (AB2 also [3][np]); history_valid: valid entries on entry (True = 1)."""
     pos = _dev(pos, torch.float64, "pos", 3)
     if rhs is not None:
-        _dev(rhs, torch.float32, "rhs", 3)
+        k = scheme + 1
+        if rhs.dtype != torch.float32 or not rhs.is_cuda or not rhs.is_contiguous():
+            raise ValueError("rhs must be a contiguous float32 CUDA tensor")
+        if rhs.numel() != (k - 1) * 3 * pos.shape[1]:
+            raise ValueError(f"rhs must hold {k - 1} x 3 x np values for AB{k}")
     _check(load_library().tracker_advance(h, pos.shape[1], _ptr(pos), _ptr(rhs), float(dt), int(steps),
-                                          int(scheme), int(bool(history_valid))))
+                                          int(scheme), int(history_valid)))
     return pos
 
 

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_count_scan(uint32_t* __restrict_
 // independent of the order, so the step results do not depend on it.
 __global__ void k_scatter_state(int64_t np, const uint32_t* __restrict__ keys, int32_t* __restrict__ cursor,
                                 const double* __restrict__ pos_in, const int32_t* __restrict__ id_in,
-                                const float* __restrict__ rhs_in, double* __restrict__ pos_out,
+                                const float* __restrict__ rhs_in, int rhs_rows, double* __restrict__ pos_out,
                                 int32_t* __restrict__ id_out, float* __restrict__ rhs_out, int* flags)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -145,10 +145,7 @@ __global__ void k_scatter_state(int64_t np, const uint32_t* __restrict__ keys, i
 #pragma unroll
     for (int a = 0; a < 3; ++a) pos_out[a * np + d] = pos_in[a * np + j];
     id_out[d] = id_in ? id_in[j] : (int32_t)j;
-    if (rhs_in) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) rhs_out[a * np + d] = rhs_in[a * np + j];
-    }
+    for (int r = 0; r < rhs_rows; ++r) rhs_out[r * np + d] = rhs_in[r * np + j];
 }
 
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
@@ -319,13 +316,12 @@ __global__ void k_unpermute_pos(int64_t np, const double* __restrict__ src, cons
 }
 
 __global__ void k_unpermute_rhs(int64_t np, const float* __restrict__ src, const int32_t* __restrict__ id,
-                                float* __restrict__ dst)
+                                float* __restrict__ dst, int rows)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= np) return;
     const int64_t p = id[j];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dst[a * np + p] = src[a * np + j];
+    for (int r = 0; r < rows; ++r) dst[r * np + p] = src[r * np + j];
 }
 
 // Fills the ghost-padded storage: padded node (x1, x2, x3) in [-PAD, N+PAD)^3
@@ -391,12 +387,12 @@ cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offset
 }
 
 cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,
-                                 const int32_t* id_in, const float* rhs_in, double* pos_out, int32_t* id_out,
-                                 float* rhs_out, int* flags, cudaStream_t st)
+                                 const int32_t* id_in, const float* rhs_in, int rhs_rows, double* pos_out,
+                                 int32_t* id_out, float* rhs_out, int* flags, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
-    k_scatter_state<<<grid_for(np, 256), 256, 0, st>>>(np, keys, cursor, pos_in, id_in, rhs_in, pos_out, id_out,
-                                                      rhs_out, flags);
+    k_scatter_state<<<grid_for(np, 256), 256, 0, st>>>(np, keys, cursor, pos_in, id_in, rhs_in, rhs_in ? rhs_rows : 0,
+                                                      pos_out, id_out, rhs_out, flags);
     return cudaGetLastError();
 }
 
@@ -462,10 +458,10 @@ cudaError_t launch_unpermute_pos(int64_t np, const double* src, const int32_t* i
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id, float* dst, cudaStream_t st)
+cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id, float* dst, int rows, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
-    k_unpermute_rhs<<<grid_for(np, 256), 256, 0, st>>>(np, src, id, dst);
+    k_unpermute_rhs<<<grid_for(np, 256), 256, 0, st>>>(np, src, id, dst, rows);
     return cudaGetLastError();
 }
 

@@ -733,7 +733,7 @@ constexpr size_t align32(size_t x) { return (x + 31) & ~size_t(31); }
 
 // STAGE: what P1 keeps for later phases besides the records: 0 = caller ids
 // (outputs in caller order), 1 = ids + float64 positions (RK2 update),
-// 2 = ids + positions + previous right-hand sides (AB2 update).
+// 2 = ids + positions + the AB history (up to AB_MAX_HIST entries of 3).
 template <typename T, int SC, int STAGE>
 struct SmemPlan {
     static constexpr size_t rec = align32((size_t)3 * SC * sizeof(T));
@@ -743,7 +743,7 @@ struct SmemPlan {
     static constexpr size_t id = align32(cell + PB * sizeof(int));
     static constexpr size_t x = align32(id + PB * sizeof(int));
     static constexpr size_t rhs = align32(x + (STAGE >= 1 ? (size_t)3 * PB * sizeof(double) : 0));
-    static constexpr size_t total = rhs + (STAGE >= 2 ? (size_t)3 * PB * sizeof(float) : 0);
+    static constexpr size_t total = rhs + (STAGE >= 2 ? (size_t)3 * AB_MAX_HIST * PB * sizeof(float) : 0);
 };
 
 template <int MODE>
@@ -782,7 +782,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     int* p_cell = reinterpret_cast<int*>(smem_raw + SM::cell);              // [PB]
     int* p_id = reinterpret_cast<int*>(smem_raw + SM::id);                  // [PB] caller ids
     double* p_x = reinterpret_cast<double*>(smem_raw + SM::x);              // [3][PB] positions (steps)
-    float* p_rhs = reinterpret_cast<float*>(smem_raw + SM::rhs);            // [3][PB] previous rhs (AB2)
+    float* p_rhs = reinterpret_cast<float*>(smem_raw + SM::rhs);            // [3 * (k-1)][PB] AB history
 
     if (j0 >= j1) return;
 
@@ -830,7 +830,10 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                 ok &= split_axis(x, inv_delta, mask, c[ax], t);
                 rec.t[ax] = (T)t;
                 if constexpr (IS_STEP) p_x[ax * PB + tid] = x;
-                if constexpr (IS_AB2) p_rhs[ax * PB + tid] = a.history_valid ? a.rhs_in[ax * np + src] : 0.0f;
+            }
+            if constexpr (IS_AB2) {   // the AB history rows; entries beyond the valid ones are zero
+                for (int r = 0; r < 3 * (a.ab_order - 1); ++r)
+                    p_rhs[r * PB + tid] = r < 3 * a.history_valid ? a.rhs_in[r * np + src] : 0.0f;
             }
             p_id[tid] = a.id_in ? a.id_in[src] : src;
             if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
@@ -966,11 +969,16 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                     if constexpr (MODE == MODE_RK2) {
                         const double k2 = (double)p_k[(3 + ax) * PB + tid];
                         xn = x0 + (0.5 * a.dt) * (k1 + k2);
-                    } else {   // AB2
-                        const double inc =
-                            a.history_valid ? (1.5 * k1 - 0.5 * (double)p_rhs[ax * PB + tid]) : k1;
+                    } else {   // ABk, order min(k, 1 + history)
+                        const int q = min(a.ab_order, a.history_valid + 1);
+                        const double inc = ab_increment(q, k1, [&](int e) {
+                            return (double)p_rhs[(3 * e + ax) * PB + tid];
+                        });
                         xn = x0 + a.dt * inc;
+                        // new history: u_n, then the older entries shifted by one
                         a.rhs_out[ax * np + j] = (float)k1;
+                        for (int e = 1; e < a.ab_order - 1; ++e)
+                            a.rhs_out[(3 * e + ax) * np + j] = p_rhs[(3 * (e - 1) + ax) * PB + tid];
                     }
                     double tt;
                     ok &= split_axis(xn, inv_delta, mask, cn[ax], tt);

@@ -69,7 +69,7 @@ struct ColPlan {
     static constexpr size_t w = align32(k + (size_t)2 * 6 * PBC * sizeof(float));         // [NQW][48]
     static constexpr size_t x = align32(w + (size_t)NQW * 48 * sizeof(float));            // [3][3][PBC]
     static constexpr size_t rhs = align32(x + (size_t)3 * 3 * PBC * sizeof(double));      // [3][3][PBC]
-    static constexpr size_t seg = align32(rhs + (AB2 ? (size_t)3 * 3 * PBC * sizeof(float) : 0));
+    static constexpr size_t seg = align32(rhs + (AB2 ? (size_t)3 * 3 * AB_MAX_HIST * PBC * sizeof(float) : 0));
     static constexpr size_t total = seg + (size_t)2 * MAXSEG * sizeof(int);
 };
 
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
     T* p_k = reinterpret_cast<T*>(smem_raw + CP::k);                    // [2][6][PBC]
     T* wbuf = reinterpret_cast<T*>(smem_raw + CP::w);                   // [NQW][48]
     double* p_x = reinterpret_cast<double*>(smem_raw + CP::x);          // [3 slots][3][PBC]
-    float* p_rhs = reinterpret_cast<float*>(smem_raw + CP::rhs);        // [3 slots][3][PBC] (AB2)
+    float* p_rhs = reinterpret_cast<float*>(smem_raw + CP::rhs);        // [3 slots][3 AB_MAX_HIST][PBC] (AB)
     int* s_beg = reinterpret_cast<int*>(smem_raw + CP::seg);            // [MAXSEG]
     int* s_end = s_beg + MAXSEG;                                        // [MAXSEG]
 
@@ -205,10 +205,12 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
                             const uint32_t d =
                                 (uint32_t)__cvta_generic_to_shared(p_x + (slot * 3 + ax) * PBC + i);
                             cp_async_elem<double>(d, a.pos_out + ax * np + t.j0 + i);
-                            if (IS_AB2 && a.history_valid) {
-                                const uint32_t dr =
-                                    (uint32_t)__cvta_generic_to_shared(p_rhs + (slot * 3 + ax) * PBC + i);
-                                cp_async_elem<float>(dr, a.rhs_out + ax * np + t.j0 + i);
+                        }
+                        if constexpr (IS_AB2) {   // the valid AB history rows
+                            for (int r = 0; r < 3 * a.history_valid; ++r) {
+                                const uint32_t dr = (uint32_t)__cvta_generic_to_shared(
+                                    p_rhs + (slot * 3 * AB_MAX_HIST + r) * PBC + i);
+                                cp_async_elem<float>(dr, a.rhs_out + r * np + t.j0 + i);
                             }
                         }
                     }
@@ -260,12 +262,16 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
                         if constexpr (MODE == MODE_RK2) {
                             const double k2 = (double)kk[(3 + ax) * PBC + i];
                             xn = x0 + (0.5 * a.dt) * (k1 + k2);
-                        } else {
-                            const double inc = a.history_valid
-                                                   ? (1.5 * k1 - 0.5 * (double)p_rhs[(slot * 3 + ax) * PBC + i])
-                                                   : k1;
+                        } else {   // ABk, order min(k, 1 + history)
+                            const float* hs = p_rhs + slot * 3 * AB_MAX_HIST * PBC + i;
+                            const int q = min(a.ab_order, a.history_valid + 1);
+                            const double inc =
+                                ab_increment(q, k1, [&](int e) { return (double)hs[(3 * e + ax) * PBC]; });
                             xn = x0 + a.dt * inc;
+                            // new history in place: u_n, then the valid older entries shifted by one
                             a.rhs_out[ax * np + j] = (float)k1;
+                            for (int e = 1; e < a.ab_order - 1; ++e)
+                                a.rhs_out[(3 * e + ax) * np + j] = e - 1 < a.history_valid ? hs[(3 * (e - 1) + ax) * PBC] : 0.0f;
                         }
                         double tt;
                         ok &= split_axis(xn, inv_delta, mask, cn[ax], tt);

@@ -76,17 +76,37 @@ struct BlockArgs {
     const int32_t* perm;      // sorted position j -> index into the *_in arrays
     const double* pos_in;     // [3][np]
     const int32_t* id_in;     // [np] or null (then id = perm[j])
-    const float* rhs_in;      // [3][np] AB2 history or null
+    const float* rhs_in;      // [ab_order-1][3][np] AB history (u_{n-1} first) or null
     double* pos_out;          // [3][np], written at j
     int32_t* id_out;          // [np], written at j
-    float* rhs_out;           // [3][np], written at j
+    float* rhs_out;           // [ab_order-1][3][np], written at j
     uint32_t* key_out;        // [np], written at j
     void* out;                // interpolation outputs [nout][np], written at id
     int out_f64;
-    int history_valid;
+    int history_valid;        // AB: valid history entries on entry, 0 .. ab_order-1
+    int ab_order;             // AB order k (2, 3, 4); the history holds k-1 entries
     double dt;
     int* flags;
 };
+
+constexpr int AB_MAX_HIST = 3;   // history entries of the highest supported order (AB4)
+
+// dt-free Adams-Bashforth increment of order q (1..4): sum_j beta^q_j u_{n-j}
+// with u_n = f0 and u_{n-j} = hist(j - 1), summed newest first; beta^q are the
+// textbook weights (integrals over one step of the Lagrange basis on the past
+// steps).
+template <class HIST>
+__device__ __forceinline__ double ab_increment(int q, double f0, const HIST& hist)
+{
+    switch (q) {
+        case 1: return f0;
+        case 2: return 1.5 * f0 + (-0.5) * hist(0);
+        case 3: return (23.0 / 12.0) * f0 + (-16.0 / 12.0) * hist(0) + (5.0 / 12.0) * hist(1);
+        default:
+            return (55.0 / 24.0) * f0 + (-59.0 / 24.0) * hist(0) + (37.0 / 24.0) * hist(1) +
+                   (-9.0 / 24.0) * hist(2);
+    }
+}
 
 // Arguments of the adjoint block kernel (one RK2 step, backwards).
 struct AdjArgs {
@@ -174,7 +194,7 @@ cudaError_t launch_offsets(const uint32_t* keys_sorted, int64_t n, int64_t nbloc
 
 // Scatter sorted state back to the caller's order: dst[a][id[j]] = src[a][j].
 cudaError_t launch_unpermute_pos(int64_t np, const double* src, const int32_t* id, double* dst, cudaStream_t st);
-cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id, float* dst, cudaStream_t st);
+cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id, float* dst, int rows, cudaStream_t st);
 
 // Fill the ghost-padded storage from a dense field src[C][N][N][N] (periodic ghosts).
 cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int C, int N, void* dst, cudaStream_t st);
@@ -213,8 +233,8 @@ cudaError_t launch_keys_count(const GridGeom& g, int64_t np, const double* pos, 
                               int* flags, cudaStream_t st);
 cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor, cudaStream_t st);
 cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,
-                                 const int32_t* id_in, const float* rhs_in, double* pos_out, int32_t* id_out,
-                                 float* rhs_out, int* flags, cudaStream_t st);
+                                 const int32_t* id_in, const float* rhs_in, int rhs_rows, double* pos_out,
+                                 int32_t* id_out, float* rhs_out, int* flags, cudaStream_t st);
 cudaError_t launch_block_i4(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_block_i6(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_block_i8(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);

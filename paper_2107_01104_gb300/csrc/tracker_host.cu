@@ -263,7 +263,7 @@ int ensure_state(tracker* t, int64_t np)
     t->state_cap = 0;
     for (int i = 0; i < 2; ++i) {
         if (dev_alloc(&t->pos_s[i], (size_t)np * 24) != cudaSuccess || dev_alloc(&t->id_s[i], (size_t)np * 4) != cudaSuccess ||
-            dev_alloc(&t->rhs_s[i], (size_t)np * 12) != cudaSuccess) {
+            dev_alloc(&t->rhs_s[i], (size_t)np * 12 * AB_MAX_HIST) != cudaSuccess) {
             cudaGetLastError();
             return fail(TRK_ENOMEM, "cannot allocate particle state for %lld particles", (long long)np);
         }
@@ -338,6 +338,7 @@ BlockArgs base_args(tracker* t)
         }
     a.offsets = t->offsets;
     a.flags = t->d_flags;
+    a.ab_order = 2;
     return a;
 }
 
@@ -399,21 +400,22 @@ bool use_column(const tracker* t) { return t->step_kernel != TRK_STEP_BLOCK && c
 // update or from the initial keys, scan, scatter of the state into its
 // blocks), then the column kernel, which counts the new keys.  Block path:
 // stable radix sort, then the block kernel reading through perm.
-// first: read the caller's arrays (identity ids, caller history flag).
-int advance_step(tracker* t, int64_t np, int mode, double dt, int cur, bool first, const double* pos,
-                 const float* rhs, int history_valid)
+// first: read the caller's arrays (identity ids).  AB steps: order k =
+// ab_order, `hist` valid history entries for this step.
+int advance_step(tracker* t, int64_t np, int mode, int ab_order, int hist, double dt, int cur, bool first,
+                 const double* pos, const float* rhs)
 {
     const bool col = use_column(t);
     const int nxt = cur ^ 1;
+    const bool ab = mode == MODE_AB2;
     {
         ProfScope ps(t, PROF_BIN);
         if (col) {
-            const bool hv = mode == MODE_AB2 && (first ? history_valid != 0 : true);
-            const float* rin = hv ? (first ? rhs : t->rhs_s[cur]) : nullptr;
+            const float* rin = ab && hist > 0 ? (first ? rhs : t->rhs_s[cur]) : nullptr;
             CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->stream));
             CUDA_TRY(launch_scatter_state(np, t->keys, t->d_cursor, first ? pos : t->pos_s[cur],
-                                          first ? nullptr : t->id_s[cur], rin, t->pos_s[nxt], t->id_s[nxt],
-                                          t->rhs_s[nxt], t->d_flags, t->stream));
+                                          first ? nullptr : t->id_s[cur], rin, 3 * (ab_order - 1),
+                                          t->pos_s[nxt], t->id_s[nxt], t->rhs_s[nxt], t->d_flags, t->stream));
             t->launches += 2;
         } else {
             CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
@@ -430,7 +432,8 @@ int advance_step(tracker* t, int64_t np, int mode, double dt, int cur, bool firs
         ca.a.pos_out = t->pos_s[nxt];
         ca.a.rhs_out = t->rhs_s[nxt];
         ca.a.key_out = t->keys;
-        ca.a.history_valid = mode == MODE_AB2 ? (first ? history_valid : 1) : 0;
+        ca.a.history_valid = ab ? hist : 0;
+        ca.a.ab_order = ab_order;
         ca.nseg = std::min(t->g.nb3, 8);
         ca.nitems = (int64_t)t->g.nb1 * t->g.nb2 * (t->g.nb3 / ca.nseg);
         ca.ctr = t->d_colctr;
@@ -450,13 +453,13 @@ int advance_step(tracker* t, int64_t np, int mode, double dt, int cur, bool firs
         a.pos_in = pos;
         a.id_in = nullptr;
         a.rhs_in = rhs;
-        a.history_valid = history_valid;
     } else {
         a.pos_in = t->pos_s[cur];
         a.id_in = t->id_s[cur];
         a.rhs_in = t->rhs_s[cur];
-        a.history_valid = (mode == MODE_AB2) ? 1 : 0;
     }
+    a.history_valid = ab ? hist : 0;
+    a.ab_order = ab_order;
     a.pos_out = t->pos_s[nxt];
     a.id_out = t->id_s[nxt];
     a.rhs_out = t->rhs_s[nxt];
@@ -735,8 +738,12 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     if (rc) return rc;
     if (!t->field) return fail(TRK_ENOFIELD, "no field set");
     if (t->C != 3) return fail(TRK_EINVAL, "advection needs a 3-component field (C=%d)", t->C);
-    if (scheme != TRK_RK2 && scheme != TRK_AB2) return fail(TRK_EINVAL, "unknown scheme %d", scheme);
-    if (scheme == TRK_AB2 && !rhs && np > 0) return fail(TRK_EINVAL, "AB2 needs the rhs history array");
+    if (scheme != TRK_RK2 && scheme != TRK_AB2 && scheme != TRK_AB3 && scheme != TRK_AB4)
+        return fail(TRK_EINVAL, "unknown scheme %d", scheme);
+    const int k = scheme == TRK_RK2 ? 0 : scheme + 1;   // Adams-Bashforth order
+    if (k && !rhs && np > 0) return fail(TRK_EINVAL, "AB%d needs the rhs history array", k);
+    if (k && (history_valid < 0 || history_valid > k - 1))
+        return fail(TRK_EINVAL, "history_valid=%d outside [0, %d] for AB%d", history_valid, k - 1, k);
     if (!std::isfinite(dt)) return fail(TRK_EINVAL, "dt must be finite");
     if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
     if (np > 0 && !pos) return fail(TRK_EINVAL, "pos must not be NULL");
@@ -744,7 +751,8 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     if (np == 0 || steps == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
     if ((rc = ensure_state(t, np))) return rc;
-    const int mode = scheme == TRK_RK2 ? MODE_RK2 : MODE_AB2;
+    const int mode = k ? MODE_AB2 : MODE_RK2;
+    const int ab_order = k ? k : 2;
     // initial keys from the caller's positions (with block counts on the column path)
     {
         ProfScope ps(t, PROF_BIN);
@@ -757,29 +765,39 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
         t->launches += 1;
     }
     // the first step reads the caller's arrays; the others ping-pong between
-    // the tracker's sorted state buffers, replayed as a two-step CUDA graph
-    if ((rc = advance_step(t, np, mode, dt, 0, true, pos, rhs, history_valid))) return rc;
+    // the tracker's state buffers.  AB steps run one by one until the history
+    // is full (k - 1 entries); from then on every step is the same and pairs
+    // of steps are replayed from a CUDA graph.
+    int hist = k ? history_valid : 0;
+    if ((rc = advance_step(t, np, mode, ab_order, hist, dt, 0, true, pos, rhs))) return rc;
     int cur = 1;
     int rest = steps - 1;
+    if (k) hist = std::min(hist + 1, k - 1);
+    for (; rest > 0 && k && hist < k - 1; --rest) {
+        if ((rc = advance_step(t, np, mode, ab_order, hist, dt, cur, false, nullptr, nullptr))) return rc;
+        cur ^= 1;
+        hist += 1;
+    }
     if (!t->prof && rest >= 2) {
         uint64_t key = mix(mix(mix(mix(0, (uint64_t)np), (uint64_t)mode), t->gen), dbits(dt));
-        key = mix(key, (uint64_t)(uintptr_t)t->field);
-        rc = replay_graph(t, t->adv_graph, key, rest / 2, [&]() {
-            int r = advance_step(t, np, mode, dt, 1, false, nullptr, nullptr, 1);
-            return r ? r : advance_step(t, np, mode, dt, 0, false, nullptr, nullptr, 1);
+        key = mix(mix(key, (uint64_t)(uintptr_t)t->field), (uint64_t)ab_order);
+        const int c0 = cur;
+        rc = replay_graph(t, t->adv_graph, mix(key, (uint64_t)c0), rest / 2, [&]() {
+            int r = advance_step(t, np, mode, ab_order, hist, dt, c0, false, nullptr, nullptr);
+            return r ? r : advance_step(t, np, mode, ab_order, hist, dt, c0 ^ 1, false, nullptr, nullptr);
         });
         if (rc) return rc;
         rest -= 2 * (rest / 2);
     }
     for (; rest > 0; --rest) {
-        if ((rc = advance_step(t, np, mode, dt, cur, false, nullptr, nullptr, 1))) return rc;
+        if ((rc = advance_step(t, np, mode, ab_order, hist, dt, cur, false, nullptr, nullptr))) return rc;
         cur ^= 1;
     }
     ProfScope ps(t, PROF_OTHER);
     CUDA_TRY(launch_unpermute_pos(np, t->pos_s[cur], t->id_s[cur], pos, t->stream));
     t->launches += 1;
-    if (scheme == TRK_AB2) {
-        CUDA_TRY(launch_unpermute_rhs(np, t->rhs_s[cur], t->id_s[cur], rhs, t->stream));
+    if (k) {
+        CUDA_TRY(launch_unpermute_rhs(np, t->rhs_s[cur], t->id_s[cur], rhs, 3 * (k - 1), t->stream));
         t->launches += 1;
     }
     return TRK_OK;
@@ -843,6 +861,7 @@ static int batched_launch(tracker* t, const BatchSet* d_desc, int nsets)
 
 int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double dt, int steps, int history_valid)
 {
+    history_valid = history_valid ? 1 : 0;   // AB2: one history entry, valid or not
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
     if (nsets < 0 || (nsets > 0 && !sets)) return fail(TRK_EINVAL, "bad set list");
     if (!t->field) return fail(TRK_ENOFIELD, "no field set");
@@ -1034,7 +1053,7 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
         if (sets[s].np == 0) continue;
         SetState& ss = t->sets[s];
         CUDA_TRY(launch_unpermute_pos(sets[s].np, ss.pos_s[cur], ss.id_s[cur], sets[s].pos, t->stream));
-        CUDA_TRY(launch_unpermute_rhs(sets[s].np, ss.rhs_s[cur], ss.id_s[cur], sets[s].rhs, t->stream));
+        CUDA_TRY(launch_unpermute_rhs(sets[s].np, ss.rhs_s[cur], ss.id_s[cur], sets[s].rhs, 3, t->stream));
         t->launches += 2;
     }
     return TRK_OK;

@@ -54,10 +54,11 @@ def positions(kind, N, n, seed):
 def run(N, I, m, field, pos, kind, scheme, steps, dt, cfl=False):
     t = tracker(N, I, m, field, kind)
     p = torch.from_numpy(pos).to(DEV)
-    rhs = torch.zeros((3, pos.shape[1]), dtype=torch.float32, device=DEV)
-    if scheme == trk.TRK_AB2:
-        t.advance(p, dt, 2, scheme, rhs=rhs, history_valid=False)
-        t.advance(p, dt, steps - 2, scheme, rhs=rhs, history_valid=True)
+    k = scheme + 1
+    rhs = torch.zeros((max(k - 1, 1), 3, pos.shape[1]), dtype=torch.float32, device=DEV)
+    if scheme != trk.TRK_RK2:
+        t.advance(p, dt, 2, scheme, rhs=rhs, history_valid=0)
+        t.advance(p, dt, steps - 2, scheme, rhs=rhs, history_valid=min(2, k - 1))
     else:
         t.advance(p, dt, steps, scheme)
     if cfl:
@@ -81,16 +82,16 @@ CASES = [
 
 
 @pytest.mark.parametrize("I,m", [(4, 1), (6, 2), (6, 3)])
-@pytest.mark.parametrize("scheme", [trk.TRK_RK2, trk.TRK_AB2])
+@pytest.mark.parametrize("scheme", [trk.TRK_RK2, trk.TRK_AB2, trk.TRK_AB3, trk.TRK_AB4])
 @pytest.mark.parametrize("N,n,layout", CASES)
 def test_column_bit_identical_to_block(I, m, scheme, N, n, layout):
     field = synth.velocity_field_np(N, min(10, N // 3), 300 + N).astype(np.float32)
     pos = positions(layout, N, n, 11)
-    steps, dt = 5, 4e-3
+    steps, dt = 6, 4e-3
     pb, rb = run(N, I, m, field, pos, trk.TRK_STEP_BLOCK, scheme, steps, dt)
     pc, rc = run(N, I, m, field, pos, trk.TRK_STEP_COLUMN, scheme, steps, dt)
     assert torch.equal(pb, pc)
-    if scheme == trk.TRK_AB2:
+    if scheme != trk.TRK_RK2:
         assert torch.equal(rb, rc)
 
 
