@@ -40,8 +40,7 @@ __global__ void k_keys(GridGeom g, int64_t np, const double* __restrict__ pos, u
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double t;
-        ok &= split_axis(pos[a * np + p], g.inv_delta, g.mask, c[a], t);
+        ok &= split_cell(pos[a * np + p], g.inv_delta, g.mask, c[a]);
     }
     if (!ok) atomicOr(flags + FLAG_NONFINITE, 1);
     const uint32_t key = block_key(g, c[0], c[1], c[2]);

@@ -980,8 +980,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                         for (int e = 1; e < a.ab_order - 1; ++e)
                             a.rhs_out[(3 * e + ax) * np + j] = p_rhs[(3 * (e - 1) + ax) * PB + tid];
                     }
-                    double tt;
-                    ok &= split_axis(xn, inv_delta, mask, cn[ax], tt);
+                    ok &= split_cell(xn, inv_delta, mask, cn[ax]);
                     a.pos_out[ax * np + j] = xn;
                 }
                 if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);

@@ -273,8 +273,7 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
                             for (int e = 1; e < a.ab_order - 1; ++e)
                                 a.rhs_out[(3 * e + ax) * np + j] = e - 1 < a.history_valid ? hs[(3 * (e - 1) + ax) * PBC] : 0.0f;
                         }
-                        double tt;
-                        ok &= split_axis(xn, inv_delta, mask, cn[ax], tt);
+                        ok &= split_cell(xn, inv_delta, mask, cn[ax]);
                         a.pos_out[ax * np + j] = xn;
                     }
                     if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);

@@ -156,10 +156,17 @@ struct ColumnArgs {
 // __dmul_rn/__dsub_rn forbid fused multiply-adds.  Positions beyond 2^51
 // cells are rejected (returned false) together with NaN/Inf.
 // ---------------------------------------------------------------------------
+// |g| < 2^51, false for NaN and Inf: the biased exponent of g is below
+// 1023 + 51 (an integer test, which keeps it off the float64 pipe)
+__device__ __forceinline__ bool cell_in_range(double g)
+{
+    return ((__double2hiint(g) >> 20) & 0x7ff) < 1074;
+}
+
 __device__ __forceinline__ bool split_axis(double X, double inv_delta, int mask, int& c, double& t)
 {
     const double g = __dmul_rn(X, inv_delta);
-    if (!(fabs(g) < 2251799813685248.0)) {   // 2^51; false for NaN too
+    if (!cell_in_range(g)) {
         c = 0;
         t = 0.0;
         return false;
@@ -167,6 +174,19 @@ __device__ __forceinline__ bool split_axis(double X, double inv_delta, int mask,
     const double c0 = floor(g);
     t = __dsub_rn(g, c0);
     c = (int)(__double2ll_rz(c0) & (long long)mask);
+    return true;
+}
+
+// The cell only (for block keys): floor(g) by one conversion rounding down,
+// which equals floor then truncation for |g| < 2^51.
+__device__ __forceinline__ bool split_cell(double X, double inv_delta, int mask, int& c)
+{
+    const double g = __dmul_rn(X, inv_delta);
+    if (!cell_in_range(g)) {
+        c = 0;
+        return false;
+    }
+    c = (int)(__double2ll_rd(g) & (long long)mask);
     return true;
 }
 
