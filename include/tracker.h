@@ -64,7 +64,7 @@ typedef enum { TRK_RK2 = 0, TRK_AB2 = 1, TRK_AB3 = 2, TRK_AB4 = 3 } trk_scheme;
 
 typedef enum { TRK_DTYPE_F64 = 0, TRK_DTYPE_F32 = 1 } trk_dtype;
 
-typedef enum { TRK_STEP_AUTO = 0, TRK_STEP_BLOCK = 1, TRK_STEP_COLUMN = 2 } trk_step_kernel;
+typedef enum { TRK_STEP_AUTO = 0, TRK_STEP_BLOCK = 1, TRK_STEP_COLUMN = 2, TRK_STEP_DIRECT = 3 } trk_step_kernel;
 
 /* ---------------------------------------------------------------------- */
 /* Lifetime                                                                */
@@ -178,7 +178,7 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
 int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, int steps, int scheme,
                     int history_valid);
 
-/* Step kernel used by tracker_advance (trk_step_kernel):
+/* Step kernel used by tracker_advance and tracker_interpolate (trk_step_kernel):
  *   TRK_STEP_COLUMN: a persistent kernel that walks column segments of cell
  *     blocks along x3 (the x3 slabs of Sec. 3.3.1): the field halo stays in a
  *     ring of x3 planes, so a slab brings in only the planes it does not
@@ -191,11 +191,24 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     8 x 8 x 8 block shape.
  *   TRK_STEP_BLOCK: one thread block per cell block, reading the state
  *     through the sort permutation (all storages and kernels).
- *   TRK_STEP_AUTO (default): COLUMN where available, else BLOCK.
- * Both kernels perform the same floating-point operations in the same
+ *   TRK_STEP_DIRECT: for sparse particle sets (the paper's production runs
+ *     carry ~1e-3 tracers per grid cell, Sec. 4): particles sorted by block
+ *     as for BLOCK, 256 of them per thread block, each stencil gathered
+ *     from the field in global memory, so no field sweep and no halo per
+ *     cell block (all storages and kernels, any block shape).  The stage-2
+ *     point of RK2 is gathered wherever it lies; TRK_ECFL is raised when it
+ *     is more than one cell away.
+ *   TRK_STEP_AUTO (default): DIRECT below 0.05 particles per grid cell
+ *     (np < 0.05 N^3, the measured crossover), else COLUMN where available,
+ *     else BLOCK.  tracker_interpolate uses DIRECT or BLOCK.
+ * All kernels perform the same floating-point operations in the same
  * order, so their results are bit-identical.  TRK_STEP_COLUMN on a tracker
  * without a column kernel is TRK_EINVAL.  Errors: TRK_EINVAL. */
 int tracker_set_step_kernel(tracker* t, int kind);
+
+/* The trk_step_kernel (COLUMN, BLOCK or DIRECT) that tracker_advance uses
+ * for np particles under the current setting; negative status on error. */
+int tracker_step_kernel_for(const tracker* t, int64_t np);
 
 /* ---------------------------------------------------------------------- */
 /* Batched advection: many particle sets, one persistent launch per step  */

@@ -31,7 +31,7 @@ TRK_LAGRANGE, TRK_SPLINE = 0, 1
 TRK_F64, TRK_F32, TRK_BF16X2 = 0, 1, 2
 TRK_RK2, TRK_AB2, TRK_AB3, TRK_AB4 = 0, 1, 2, 3
 TRK_DTYPE_F64, TRK_DTYPE_F32 = 0, 1
-TRK_STEP_AUTO, TRK_STEP_BLOCK, TRK_STEP_COLUMN = 0, 1, 2
+TRK_STEP_AUTO, TRK_STEP_BLOCK, TRK_STEP_COLUMN, TRK_STEP_DIRECT = 0, 1, 2, 3
 
 _STATUS = {TRK_EINVAL: "EINVAL", TRK_ENOMEM: "ENOMEM", TRK_ECUDA: "ECUDA", TRK_ENONFINITE: "ENONFINITE",
            TRK_ENOFIELD: "ENOFIELD", TRK_ECFL: "ECFL"}
@@ -42,6 +42,7 @@ ABI_FUNCTIONS = (
     "tracker_set_field", "tracker_set_block", "tracker_num_blocks", "tracker_bin", "tracker_interpolate",
     "tracker_advance", "tracker_advance_batched", "tracker_adjoint", "tracker_launch_count",
     "tracker_profile", "tracker_profile_read", "tracker_bin_static", "tracker_set_step_kernel",
+    "tracker_step_kernel_for",
 )
 
 
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH):
             "tracker_profile_read": (c_int, [vp, vp, vp]),
             "tracker_bin_static": (c_int, [c_i64, vp, c_int, c_d, c_int, c_int, c_int, vp, vp, vp, vp, vp]),
             "tracker_set_step_kernel": (c_int, [vp, c_int]),
+            "tracker_step_kernel_for": (c_int, [vp, c_i64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -175,6 +177,13 @@ def tracker_set_block(h, bx, by, bz):
 
 def tracker_set_step_kernel(h, kind):
     _check(load_library().tracker_set_step_kernel(h, int(kind)))
+
+
+def tracker_step_kernel_for(h, np_) -> int:
+    """The step kernel (TRK_STEP_COLUMN / BLOCK / DIRECT) tracker_advance uses for np_ particles."""
+    r = int(load_library().tracker_step_kernel_for(h, int(np_)))
+    _check(min(r, 0))
+    return r
 
 
 def tracker_num_blocks(h) -> int:
@@ -322,8 +331,11 @@ class Tracker:
         self.C = int(field.shape[0])
 
     def set_step_kernel(self, kind):
-        """TRK_STEP_AUTO, TRK_STEP_BLOCK or TRK_STEP_COLUMN (see tracker_set_step_kernel)."""
+        """TRK_STEP_AUTO, _BLOCK, _COLUMN or _DIRECT (see tracker_set_step_kernel)."""
         tracker_set_step_kernel(self.h, kind)
+
+    def step_kernel_for(self, np_):
+        return tracker_step_kernel_for(self.h, np_)
 
     def bin(self, pos):
         self._stream()

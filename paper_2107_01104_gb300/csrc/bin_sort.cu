@@ -114,6 +114,96 @@ __global__ void __launch_bounds__(CS_THREADS) k_count_scan(uint32_t* __restrict_
     if (tid == 0) offsets[nblocks] = (int32_t)s_total;
 }
 
+// The same for large grids, over all SMs: tiles of CT_TILE counts (nblocks a
+// multiple of CT_TILE).  k_tile_sums sums each tile; k_tile_scan adds the sums
+// of the preceding tiles and scans its own tile, CT_PER counts per thread
+// read and written as 16-byte vectors.
+constexpr int CT_THREADS = 256, CT_PER = 16, CT_TILE = CT_THREADS * CT_PER;
+
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();   // red may still be read by a previous call
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < CT_THREADS / 32; ++i) s += red[i];
+    return s;
+}
+
+__global__ void __launch_bounds__(CT_THREADS) k_tile_sums(const uint32_t* __restrict__ counts,
+                                                          uint32_t* __restrict__ tile_sums)
+{
+    __shared__ uint32_t red[CT_THREADS / 32];
+    const uint4* c = reinterpret_cast<const uint4*>(counts + (int64_t)blockIdx.x * CT_TILE) + threadIdx.x;
+    uint32_t s = 0;
+#pragma unroll
+    for (int u = 0; u < CT_PER / 4; ++u) {
+        const uint4 v = c[u * CT_THREADS];
+        s += v.x + v.y + v.z + v.w;
+    }
+    s = block_sum_u32(s, red);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(CT_THREADS) k_tile_scan(uint32_t* __restrict__ counts,
+                                                          const uint32_t* __restrict__ tile_sums, int64_t nblocks,
+                                                          int32_t* __restrict__ offsets, int32_t* __restrict__ cursor)
+{
+    __shared__ uint32_t red[CT_THREADS / 32];
+    __shared__ uint32_t wpre[CT_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tile = blockIdx.x;
+    // sum of the preceding tiles
+    uint32_t pre = 0;
+    for (int i = tid; i < tile; i += CT_THREADS) pre += tile_sums[i];
+    pre = block_sum_u32(pre, red);
+    // thread t owns counts [t CT_PER, (t + 1) CT_PER) of the tile
+    const int64_t base = (int64_t)tile * CT_TILE + (int64_t)tid * CT_PER;
+    uint4* c = reinterpret_cast<uint4*>(counts + base);
+    uint32_t v[CT_PER];
+#pragma unroll
+    for (int u = 0; u < CT_PER / 4; ++u) {
+        const uint4 q = c[u];
+        v[4 * u] = q.x, v[4 * u + 1] = q.y, v[4 * u + 2] = q.z, v[4 * u + 3] = q.w;
+    }
+    uint32_t own = 0;
+#pragma unroll
+    for (int u = 0; u < CT_PER; ++u) own += v[u];
+    uint32_t inc = own;   // inclusive scan of the per-thread sums over the warp, then the warps
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wpre[w] = inc;
+    __syncthreads();
+    uint32_t wp = 0;
+    for (int i = 0; i < w; ++i) wp += wpre[i];
+    uint32_t run = pre + wp + inc - own;   // exclusive prefix of this thread's first count
+    int4* o4 = reinterpret_cast<int4*>(offsets + base);
+    int4* k4 = reinterpret_cast<int4*>(cursor + base);
+#pragma unroll
+    for (int u = 0; u < CT_PER / 4; ++u) {
+        int4 e;
+        e.x = (int32_t)run;
+        run += v[4 * u];
+        e.y = (int32_t)run;
+        run += v[4 * u + 1];
+        e.z = (int32_t)run;
+        run += v[4 * u + 2];
+        e.w = (int32_t)run;
+        run += v[4 * u + 3];
+        o4[u] = e;
+        k4[u] = e;
+        c[u] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (base + CT_PER == nblocks) offsets[nblocks] = (int32_t)run;
+}
+
 // Counting-sort scatter of the particle state: particle j goes to the next
 // free slot of its block.  Lanes of a warp with the same key take one
 // cursor increment together (the state arrives grouped by the previous
@@ -379,9 +469,23 @@ cudaError_t launch_keys_count(const GridGeom& g, int64_t np, const double* pos, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor, cudaStream_t st)
+size_t count_scan_scratch_bytes(int64_t nblocks)
 {
-    k_count_scan<<<1, CS_THREADS, 0, st>>>(counts, nblocks, offsets, cursor);
+    return (size_t)((nblocks + CT_TILE - 1) / CT_TILE) * sizeof(uint32_t);
+}
+
+cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor,
+                              uint32_t* scratch, cudaStream_t st, int64_t* launches)
+{
+    if (nblocks <= COUNT_SCAN_ONE_CTA || nblocks % CT_TILE != 0) {
+        k_count_scan<<<1, CS_THREADS, 0, st>>>(counts, nblocks, offsets, cursor);
+        if (launches) *launches += 1;
+        return cudaGetLastError();
+    }
+    const unsigned tiles = (unsigned)(nblocks / CT_TILE);
+    k_tile_sums<<<tiles, CT_THREADS, 0, st>>>(counts, scratch);
+    k_tile_scan<<<tiles, CT_THREADS, 0, st>>>(counts, scratch, nblocks, offsets, cursor);
+    if (launches) *launches += 2;
     return cudaGetLastError();
 }
 

@@ -758,7 +758,8 @@ __host__ __device__ constexpr int stage_of()
 // Processes the sorted particles [j0, j1) of cell block b.  HALO = false skips
 // the halo staging and gathers every stencil from global memory (the direct
 // path for sparse particle sets, where a halo would serve one or two
-// particles).  Must be called by all threads of the CTA.
+// particles); its shared-memory plan has no halo region and b is unused.
+// Must be called by all threads of the CTA.
 template <typename T, int I, int DEG, int MODE, int STORE, bool HALO>
 __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0, int j1, unsigned char* smem_raw)
 {
@@ -774,8 +775,8 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     constexpr int S2 = Lay::S2, S3 = Lay::S3, SC = Lay::SC;
     using SL = SmemLd<T, S2, S3, SC>;
 
-    using SM = SmemPlan<T, SC, stage_of<MODE>()>;
-    T* halo = reinterpret_cast<T*>(smem_raw);                               // [3][SC]
+    using SM = SmemPlan<T, HALO ? SC : 0, stage_of<MODE>()>;
+    T* halo = reinterpret_cast<T*>(smem_raw);                               // [3][SC] (HALO only)
     PRec<T>* p_rec = reinterpret_cast<PRec<T>*>(smem_raw + SM::rec);        // [PB]
     T* p_k = reinterpret_cast<T*>(smem_raw + SM::k);                        // [6][PB]: k1 (3), k2 (3)
     T* wbuf = reinterpret_cast<T*>(smem_raw + SM::w);                       // [NW][2][24] weights
@@ -819,7 +820,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
         // ---------------- P1: split, stage what P3 and the writers need ----------------
         if (tid < nbat) {
             const int j = batch + tid;
-            const int src = a.perm[j];
+            const int src = a.perm ? a.perm[j] : j;
             bool ok = true;
             int c[3];
             PRec<T> rec;
@@ -888,14 +889,17 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                         dc[ax] = (int)fl;
                         ts[ax] -= fl;
                     }
-                    if ((dc[0] | dc[1] | dc[2]) != 0 || rp < 0) {
+                    // in the same cell the stage-1 stencil in L is re-used
+                    if ((dc[0] | dc[1] | dc[2]) != 0) {
                         const int s1 = r1 + dc[0], s2 = r2 + dc[1], s3 = r3 + dc[2];
-                        const bool in = rp >= 0 && s1 >= LO && s1 <= RMAX && s2 >= LO && s2 <= RMAX && s3 >= LO &&
-                                        s3 <= RMAX;
+                        const bool in =
+                            HALO && s1 >= LO && s1 <= RMAX && s2 >= LO && s2 <= RMAX && s3 >= LO && s3 <= RMAX;
                         if (in) {
                             L.load(SL{halo + (s3 - LO) * S3 + (s2 - LO) * S2 + (s1 - LO)});
                         } else {
-                            if (lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
+                            // left the staged halo, or (direct path) moved more than one cell
+                            const bool far = HALO || abs(dc[0]) > 1 || abs(dc[1]) > 1 || abs(dc[2]) > 1;
+                            if (far && lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
                             const int pc = p_cell[q];
                             L.load(GlobalLd<T, STORE, I>{a.f, ((pc & 1023) + dc[0]) & mask,
                                                          (((pc >> 10) & 1023) + dc[1]) & mask,
@@ -956,6 +960,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
         __syncthreads();
         if constexpr (IS_STEP) {
             // ---------------- P3: update, re-split, write ----------------
+            const unsigned valid = __ballot_sync(0xffffffffu, tid < nbat);
             if (tid < nbat) {
                 const int j = batch + tid;
                 const int id = p_id[tid];
@@ -985,7 +990,12 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                 }
                 if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
                 a.id_out[j] = id;
-                a.key_out[j] = block_key(a.g, cn[0], cn[1], cn[2]);
+                const uint32_t key = block_key(a.g, cn[0], cn[1], cn[2]);
+                a.key_out[j] = key;
+                if (a.counts) {   // block counts of the next binning, one add per group of equal keys
+                    const unsigned peers = __match_any_sync(valid, key);
+                    if (lane == __ffs(peers) - 1) atomicAdd(a.counts + key, (uint32_t)__popc(peers));
+                }
             }
             __syncthreads();
         }
@@ -1003,6 +1013,60 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int b = blockIdx.x;
     process_block<T, I, DEG, MODE, STORE, true>(a, b, a.offsets[b], a.offsets[b + 1], smem_raw);
+}
+
+// Direct path: CTA c takes the sorted particles [c PB, (c + 1) PB) and
+// gathers their stencils from global memory (no halo, no cell-block grid).
+template <typename T, int I, int DEG, int MODE, int STORE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN_BLOCKS) : 1)
+    k_direct(const __grid_constant__ BlockArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int64_t j0 = (int64_t)blockIdx.x * PB;
+    const int64_t j1 = j0 + PB < a.np ? j0 + PB : a.np;
+    process_block<T, I, DEG, MODE, STORE, false>(a, 0, (int)j0, (int)j1, smem_raw);
+}
+
+template <typename T, int I, int MODE>
+constexpr size_t direct_smem_bytes()
+{
+    return SmemPlan<T, 0, stage_of<MODE>()>::total;
+}
+
+template <typename T, int I, int DEG, int MODE, int STORE>
+cudaError_t launch_direct_t(const BlockArgs& a, cudaStream_t st)
+{
+    constexpr size_t smem = direct_smem_bytes<T, I, MODE>();
+    static_assert(smem <= 232448, "direct shared-memory plan exceeds the per-block limit");
+    auto kern = k_direct<T, I, DEG, MODE, STORE>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.np <= 0) return cudaSuccess;
+    kern<<<(unsigned)((a.np + PB - 1) / PB), NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int I, int DEG>
+cudaError_t dispatch_direct(int mode, const BlockArgs& a, cudaStream_t st)
+{
+    const int s = a.f.storage;
+#define TRK_CASE(M)                                                                    \
+    case M:                                                                            \
+        if (s == ST_F64) return launch_direct_t<double, I, DEG, M, ST_F64>(a, st);     \
+        if (s == ST_F32) return launch_direct_t<float, I, DEG, M, ST_F32>(a, st);      \
+        return launch_direct_t<float, I, DEG, M, ST_BF16X2>(a, st);
+    switch (mode) {
+        TRK_CASE(MODE_INTERP)
+        TRK_CASE(MODE_INTERP_DERIV)
+        TRK_CASE(MODE_RK2)
+        TRK_CASE(MODE_AB2)
+    }
+#undef TRK_CASE
+    return cudaErrorInvalidValue;
 }
 
 template <typename T, int I, int MODE>

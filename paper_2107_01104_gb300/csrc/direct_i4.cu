@@ -1,0 +1,13 @@
+// Direct-path kernels (stencils gathered from global memory) for kernel
+// width I = 4, all storages and modes.
+#include "block_kernel.cuh"
+
+namespace trk {
+
+cudaError_t launch_direct_i4(int mode, const BlockArgs& a, int deg_hi, cudaStream_t st)
+{
+    if (deg_hi) return dispatch_direct<4, 4 + 1>(mode, a, st);
+    return dispatch_direct<4, 4 - 1>(mode, a, st);
+}
+
+}  // namespace trk

@@ -73,7 +73,7 @@ struct BlockArgs {
     CoefTable<double> cd;     // weights for float64 arithmetic
     int64_t np;               // particle count (stride of the [3][np] arrays)
     const int32_t* offsets;   // [nblocks + 1]
-    const int32_t* perm;      // sorted position j -> index into the *_in arrays
+    const int32_t* perm;      // sorted position j -> index into the *_in arrays, or null (identity)
     const double* pos_in;     // [3][np]
     const int32_t* id_in;     // [np] or null (then id = perm[j])
     const float* rhs_in;      // [ab_order-1][3][np] AB history (u_{n-1} first) or null
@@ -81,6 +81,7 @@ struct BlockArgs {
     int32_t* id_out;          // [np], written at j
     float* rhs_out;           // [ab_order-1][3][np], written at j
     uint32_t* key_out;        // [np], written at j
+    uint32_t* counts;         // [nblocks] block counts of the new keys (added into) or null
     void* out;                // interpolation outputs [nout][np], written at id
     int out_f64;
     int history_valid;        // AB: valid history entries on entry, 0 .. ab_order-1
@@ -251,12 +252,21 @@ cudaError_t launch_column_i6(int mode, const ColumnArgs& ca, int deg_hi, int nsm
 // offsets + cursors (counts zeroed); scatter of the state into its blocks
 cudaError_t launch_keys_count(const GridGeom& g, int64_t np, const double* pos, uint32_t* keys, uint32_t* counts,
                               int* flags, cudaStream_t st);
-cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor, cudaStream_t st);
+// Up to COUNT_SCAN_ONE_CTA blocks one CTA scans (one launch); larger grids
+// take two launches over all SMs with count_scan_scratch_bytes of scratch.
+constexpr int64_t COUNT_SCAN_ONE_CTA = 65536;
+size_t count_scan_scratch_bytes(int64_t nblocks);
+cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor,
+                              uint32_t* scratch, cudaStream_t st, int64_t* launches);
 cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,
                                  const int32_t* id_in, const float* rhs_in, int rhs_rows, double* pos_out,
                                  int32_t* id_out, float* rhs_out, int* flags, cudaStream_t st);
 cudaError_t launch_block_i4(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_block_i6(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
 cudaError_t launch_block_i8(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
+// direct path (sparse particle sets): a.np sorted particles, PB per CTA, stencils from global memory
+cudaError_t launch_direct_i4(int mode, const BlockArgs& a, int deg_hi, cudaStream_t st);
+cudaError_t launch_direct_i6(int mode, const BlockArgs& a, int deg_hi, cudaStream_t st);
+cudaError_t launch_direct_i8(int mode, const BlockArgs& a, int deg_hi, cudaStream_t st);
 
 }  // namespace trk

@@ -156,6 +156,7 @@ struct tracker {
     int* d_colctr = nullptr;          // work counter of the column kernel
     uint32_t* d_counts = nullptr;     // [nblocks] block counts (counting-sort binning of the column path)
     int32_t* d_cursor = nullptr;      // [nblocks] scatter cursors
+    uint32_t* d_scan_tmp = nullptr;   // tile sums of the multi-CTA count scan
     // instrumentation: event pairs per kernel class
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -215,13 +216,16 @@ int set_geometry(tracker* t, int bx, int by, int bz)
     dev_free(t->offsets);
     dev_free(t->d_counts);
     dev_free(t->d_cursor);
+    dev_free(t->d_scan_tmp);
     t->offsets = nullptr;
     t->d_counts = nullptr;
     t->d_cursor = nullptr;
+    t->d_scan_tmp = nullptr;
     t->gen += 1;
     CUDA_TRY(dev_alloc(&t->offsets, (size_t)(t->nblocks + 1) * sizeof(int32_t)));
     CUDA_TRY(dev_alloc(&t->d_counts, (size_t)t->nblocks * sizeof(uint32_t)));
     CUDA_TRY(dev_alloc(&t->d_cursor, (size_t)t->nblocks * sizeof(int32_t)));
+    CUDA_TRY(dev_alloc(&t->d_scan_tmp, std::max<size_t>(count_scan_scratch_bytes(t->nblocks), 16)));
     CUDA_TRY(cudaMemset(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t)));
     return TRK_OK;
 }
@@ -299,15 +303,29 @@ cudaError_t launch_block(tracker* t, int mode, const BlockArgs& a)
     }
 }
 
-// keys (caller order) -> sorted keys, perm, offsets
+cudaError_t launch_direct(tracker* t, int mode, const BlockArgs& a)
+{
+    ProfScope ps(t, PROF_STEP);
+    t->launches += 1;
+    switch (t->I) {
+        case 4: return launch_direct_i4(mode, a, t->deg_hi, t->stream);
+        case 6: return launch_direct_i6(mode, a, t->deg_hi, t->stream);
+        default: return launch_direct_i8(mode, a, t->deg_hi, t->stream);
+    }
+}
+
+// keys (caller order) -> sorted keys, perm, offsets (offsets may be NULL: the
+// direct path needs only the permutation)
 int bin_into(tracker* t, int64_t np, const double* pos, uint32_t* keys, int32_t* perm, int32_t* offsets)
 {
     ProfScope ps(t, PROF_BIN);
     CUDA_TRY(launch_keys(t->g, np, pos, keys, t->d_flags, t->stream));
     t->launches += 1;
     CUDA_TRY(radix_sort(keys, np, t->key_bits, t->keys_sorted, perm, t->sort_scratch, t->stream, &t->launches));
-    CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, offsets, t->stream));
-    t->launches += 1;
+    if (offsets) {
+        CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, offsets, t->stream));
+        t->launches += 1;
+    }
     return TRK_OK;
 }
 
@@ -393,36 +411,70 @@ bool column_available(const tracker* t)
            t->g.lb3 == LBLK;
 }
 
-bool use_column(const tracker* t) { return t->step_kernel != TRK_STEP_BLOCK && column_available(t); }
+// Below this many particles per grid cell the automatic choice gathers every
+// stencil straight from global memory (direct path) instead of sweeping the
+// field.  Measured crossover on GB300 (float32 field, spline I = 6): RK2 steps
+// at 256^3 take 0.533 (column) vs 0.477 ms (direct) at 1/24 per cell and
+// 0.652 vs 0.693 ms at 1/16; AB2 steps favour the direct path down to 1/16.
+constexpr double kDirectDensity = 0.05;
 
-// One RK2/AB2 step of tracker_advance: re-bin, then the fused step kernel.
-// Column path: counting-sort binning (block counts from the previous step's
-// update or from the initial keys, scan, scatter of the state into its
-// blocks), then the column kernel, which counts the new keys.  Block path:
-// stable radix sort, then the block kernel reading through perm.
-// first: read the caller's arrays (identity ids).  AB steps: order k =
-// ab_order, `hist` valid history entries for this step.
-int advance_step(tracker* t, int64_t np, int mode, int ab_order, int hist, double dt, int cur, bool first,
+// The kernel tracker_advance (and, between BLOCK and DIRECT, tracker_interpolate)
+// uses for np particles.
+int step_path(const tracker* t, int64_t np)
+{
+    if (t->step_kernel != TRK_STEP_AUTO) return t->step_kernel;
+    if ((double)np < kDirectDensity * (double)t->N * t->N * t->N) return TRK_STEP_DIRECT;
+    return column_available(t) ? TRK_STEP_COLUMN : TRK_STEP_BLOCK;
+}
+
+// One RK2/ABk step of tracker_advance: re-bin, then the fused step kernel.
+// Column and direct paths: counting-sort binning (block counts from the
+// previous step's update or from the initial keys, scan, scatter of the
+// state into its blocks), then the column kernel, or the direct kernel (PB
+// grouped particles per CTA, stencils gathered from global memory), updating
+// the grouped state in place and counting the new keys.  Block path: stable
+// radix sort, then the block kernel reading through perm.  first: read the
+// caller's arrays (identity ids).  AB steps: order k = ab_order, `hist` valid
+// history entries for this step.
+int advance_step(tracker* t, int64_t np, int path, int mode, int ab_order, int hist, double dt, int cur, bool first,
                  const double* pos, const float* rhs)
 {
-    const bool col = use_column(t);
+    const bool col = path == TRK_STEP_COLUMN || path == TRK_STEP_DIRECT;   // counting-sort binning
     const int nxt = cur ^ 1;
     const bool ab = mode == MODE_AB2;
     {
         ProfScope ps(t, PROF_BIN);
         if (col) {
             const float* rin = ab && hist > 0 ? (first ? rhs : t->rhs_s[cur]) : nullptr;
-            CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->stream));
+            CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->d_scan_tmp, t->stream,
+                                       &t->launches));
             CUDA_TRY(launch_scatter_state(np, t->keys, t->d_cursor, first ? pos : t->pos_s[cur],
                                           first ? nullptr : t->id_s[cur], rin, 3 * (ab_order - 1),
                                           t->pos_s[nxt], t->id_s[nxt], t->rhs_s[nxt], t->d_flags, t->stream));
-            t->launches += 2;
+            t->launches += 1;
         } else {
             CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
                                 &t->launches));
-            CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
-            t->launches += 1;
+            if (path == TRK_STEP_BLOCK) {
+                CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
+                t->launches += 1;
+            }
         }
+    }
+    if (path == TRK_STEP_DIRECT) {
+        BlockArgs a = base_args(t);
+        a.np = np;
+        a.dt = dt;
+        a.perm = nullptr;   // the state is grouped: read and written at j
+        a.pos_in = a.pos_out = t->pos_s[nxt];
+        a.id_in = a.id_out = t->id_s[nxt];
+        a.rhs_in = a.rhs_out = t->rhs_s[nxt];
+        a.history_valid = ab ? hist : 0;
+        a.ab_order = ab_order;
+        a.key_out = t->keys;
+        a.counts = t->d_counts;
+        CUDA_TRY(launch_direct(t, mode, a));
+        return TRK_OK;
     }
     if (col) {
         ColumnArgs ca{};
@@ -571,6 +623,7 @@ int tracker_destroy(tracker* t)
     dev_free(t->d_colctr);
     dev_free(t->d_counts);
     dev_free(t->d_cursor);
+    dev_free(t->d_scan_tmp);
     if (t->gev[0]) cudaEventDestroy(t->gev[0]);
     if (t->gev[1]) cudaEventDestroy(t->gev[1]);
     if (t->gstream) cudaStreamDestroy(t->gstream);
@@ -685,13 +738,20 @@ int64_t tracker_num_blocks(const tracker* t) { return t ? t->nblocks : -1; }
 int tracker_set_step_kernel(tracker* t, int kind)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
-    if (kind != TRK_STEP_AUTO && kind != TRK_STEP_BLOCK && kind != TRK_STEP_COLUMN)
+    if (kind != TRK_STEP_AUTO && kind != TRK_STEP_BLOCK && kind != TRK_STEP_COLUMN && kind != TRK_STEP_DIRECT)
         return fail(TRK_EINVAL, "unknown step kernel %d", kind);
     if (kind == TRK_STEP_COLUMN && !column_available(t))
         return fail(TRK_EINVAL, "no column kernel for this tracker (needs F32 storage, I = 4 or 6, 8x8x8 blocks)");
     t->step_kernel = kind;
     t->gen += 1;                      // captured step graphs hold the other kernels
     return TRK_OK;
+}
+
+int tracker_step_kernel_for(const tracker* t, int64_t np)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (np < 0) return fail(TRK_EINVAL, "np=%lld < 0", (long long)np);
+    return step_path(t, np);
 }
 
 int64_t tracker_launch_count(const tracker* t) { return t ? t->launches : -1; }
@@ -716,17 +776,20 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     if (!t->field) return fail(TRK_ENOFIELD, "no field set");
     if (np > 0 && (!pos || !out)) return fail(TRK_EINVAL, "pos and out must not be NULL");
     if (out_dtype != TRK_DTYPE_F64 && out_dtype != TRK_DTYPE_F32) return fail(TRK_EINVAL, "unknown out_dtype %d", out_dtype);
-    if ((rc = check_block_kernel_shape(t))) return rc;
+    const bool direct = step_path(t, np) == TRK_STEP_DIRECT;
+    if (!direct && (rc = check_block_kernel_shape(t))) return rc;
     if (np == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
-    if ((rc = bin_into(t, np, pos, t->keys, t->perm, t->offsets))) return rc;
+    if ((rc = bin_into(t, np, pos, t->keys, t->perm, direct ? nullptr : t->offsets))) return rc;
     BlockArgs a = base_args(t);
     a.np = np;
     a.perm = t->perm;
     a.pos_in = pos;
     a.out = out;
     a.out_f64 = out_dtype == TRK_DTYPE_F64;
-    CUDA_TRY(launch_block(t, deriv ? MODE_INTERP_DERIV : MODE_INTERP, a));
+    const int mode = deriv ? MODE_INTERP_DERIV : MODE_INTERP;
+    if (direct) CUDA_TRY(launch_direct(t, mode, a));
+    else CUDA_TRY(launch_block(t, mode, a));
     return TRK_OK;
 }
 
@@ -747,7 +810,8 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     if (!std::isfinite(dt)) return fail(TRK_EINVAL, "dt must be finite");
     if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
     if (np > 0 && !pos) return fail(TRK_EINVAL, "pos must not be NULL");
-    if ((rc = check_block_kernel_shape(t))) return rc;
+    const int path = step_path(t, np);
+    if (path != TRK_STEP_DIRECT && (rc = check_block_kernel_shape(t))) return rc;
     if (np == 0 || steps == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
     if ((rc = ensure_state(t, np))) return rc;
@@ -756,7 +820,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     // initial keys from the caller's positions (with block counts on the column path)
     {
         ProfScope ps(t, PROF_BIN);
-        if (use_column(t)) {
+        if (path == TRK_STEP_COLUMN || path == TRK_STEP_DIRECT) {
             CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
             CUDA_TRY(launch_keys_count(t->g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
         } else {
@@ -769,28 +833,28 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     // is full (k - 1 entries); from then on every step is the same and pairs
     // of steps are replayed from a CUDA graph.
     int hist = k ? history_valid : 0;
-    if ((rc = advance_step(t, np, mode, ab_order, hist, dt, 0, true, pos, rhs))) return rc;
+    if ((rc = advance_step(t, np, path, mode, ab_order, hist, dt, 0, true, pos, rhs))) return rc;
     int cur = 1;
     int rest = steps - 1;
     if (k) hist = std::min(hist + 1, k - 1);
     for (; rest > 0 && k && hist < k - 1; --rest) {
-        if ((rc = advance_step(t, np, mode, ab_order, hist, dt, cur, false, nullptr, nullptr))) return rc;
+        if ((rc = advance_step(t, np, path, mode, ab_order, hist, dt, cur, false, nullptr, nullptr))) return rc;
         cur ^= 1;
         hist += 1;
     }
     if (!t->prof && rest >= 2) {
         uint64_t key = mix(mix(mix(mix(0, (uint64_t)np), (uint64_t)mode), t->gen), dbits(dt));
-        key = mix(mix(key, (uint64_t)(uintptr_t)t->field), (uint64_t)ab_order);
+        key = mix(mix(mix(key, (uint64_t)(uintptr_t)t->field), (uint64_t)ab_order), (uint64_t)path);
         const int c0 = cur;
         rc = replay_graph(t, t->adv_graph, mix(key, (uint64_t)c0), rest / 2, [&]() {
-            int r = advance_step(t, np, mode, ab_order, hist, dt, c0, false, nullptr, nullptr);
-            return r ? r : advance_step(t, np, mode, ab_order, hist, dt, c0 ^ 1, false, nullptr, nullptr);
+            int r = advance_step(t, np, path, mode, ab_order, hist, dt, c0, false, nullptr, nullptr);
+            return r ? r : advance_step(t, np, path, mode, ab_order, hist, dt, c0 ^ 1, false, nullptr, nullptr);
         });
         if (rc) return rc;
         rest -= 2 * (rest / 2);
     }
     for (; rest > 0; --rest) {
-        if ((rc = advance_step(t, np, mode, ab_order, hist, dt, cur, false, nullptr, nullptr))) return rc;
+        if ((rc = advance_step(t, np, path, mode, ab_order, hist, dt, cur, false, nullptr, nullptr))) return rc;
         cur ^= 1;
     }
     ProfScope ps(t, PROF_OTHER);

@@ -1,0 +1,185 @@
+"""GPU: the direct path (stencils gathered from global memory, no halo) for
+sparse particle sets.
+
+Per particle it performs the same floating-point operations in the same order
+as the block kernel, so positions, AB histories and interpolated values must
+agree bit for bit; at the paper's sparse density (about 1.5e-3 tracers per
+grid cell) it is also checked against the oracle.  The automatic choice picks
+it below 0.05 particles per cell.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2107_01104_gb300 as trk
+import synth
+
+pytestmark = pytest.mark.gpu
+L = 2 * math.pi
+DEV = "cuda"
+
+STORAGES = [trk.TRK_F64, trk.TRK_F32, trk.TRK_BF16X2]
+KERNELS = [(4, 1), (6, 2), (8, 3), (6, 3)]
+
+
+def stored(field, storage):
+    if storage == trk.TRK_F64:
+        return field
+    f32 = field.astype(np.float32)
+    if storage == trk.TRK_F32:
+        return f32.astype(np.float64)
+    hi, lo = synth.bf16_split(torch.from_numpy(f32))
+    return hi.double().numpy() + lo.double().numpy()
+
+
+def positions(layout, N, n, seed):
+    rng = np.random.default_rng(seed)
+    if layout == "uniform":
+        return rng.uniform(0.0, L, (3, n))
+    if layout == "cluster":                        # many particles in one cell block
+        return rng.uniform(1e-3, 8 * L / N - 1e-3, (3, n))
+    p = rng.uniform(-L, 2 * L, (3, n))             # edges: nodes and +-1 ulp of faces, unwrapped
+    q = n // 4
+    delta = L / N
+    p[:, :q] = rng.integers(-N, 2 * N, (3, q)) * delta
+    faces = rng.integers(0, N + 1, (3, q)) * delta
+    p[:, q:2 * q] = np.nextafter(faces, np.where(rng.random((3, q)) < 0.5, -np.inf, np.inf))
+    return p
+
+
+def advance(N, I, m, storage, field, pos, kind, scheme, steps, dt):
+    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=m, storage=storage)
+    t.set_step_kernel(kind)
+    t.set_field(torch.from_numpy(field).to(DEV))
+    p = torch.from_numpy(pos).to(DEV)
+    k = scheme + 1
+    rhs = torch.zeros((max(k - 1, 1), 3, pos.shape[1]), dtype=torch.float32, device=DEV)
+    if scheme != trk.TRK_RK2:
+        t.advance(p, dt, 2, scheme, rhs=rhs, history_valid=0)
+        t.advance(p, dt, steps - 2, scheme, rhs=rhs, history_valid=min(2, k - 1))
+    else:
+        t.advance(p, dt, steps, scheme)
+    t.sync()
+    return p.cpu(), rhs.cpu()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("I,m", KERNELS)
+@pytest.mark.parametrize("scheme", [trk.TRK_RK2, trk.TRK_AB2, trk.TRK_AB4])
+@pytest.mark.parametrize("N,n,layout", [(32, 300, "uniform"), (32, 3000, "cluster"), (64, 5000, "edges"),
+                                        (16, 1, "uniform"), (64, 257, "uniform")])
+def test_direct_bit_identical_to_block(storage, I, m, scheme, N, n, layout):
+    field = synth.velocity_field_np(N, min(10, N // 3), 400 + N)
+    pos = positions(layout, N, n, 21)
+    steps, dt = 5, 4e-3
+    pb, rb = advance(N, I, m, storage, field, pos, trk.TRK_STEP_BLOCK, scheme, steps, dt)
+    pd, rd = advance(N, I, m, storage, field, pos, trk.TRK_STEP_DIRECT, scheme, steps, dt)
+    assert torch.equal(pb, pd)
+    if scheme != trk.TRK_RK2:
+        assert torch.equal(rb, rd)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("I,m", KERNELS)
+@pytest.mark.parametrize("C,deriv", [(3, 0), (3, 1), (9, 0), (4, 1)])
+def test_direct_interpolation_bit_identical_to_block(storage, I, m, C, deriv):
+    N, n = 32, 2000
+    rng = np.random.default_rng(C)
+    field = rng.standard_normal((C, N, N, N))
+    pos = positions("edges", N, n, 22)
+    outs = []
+    for kind in (trk.TRK_STEP_BLOCK, trk.TRK_STEP_DIRECT):
+        t = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=m, storage=storage)
+        t.set_step_kernel(kind)
+        t.set_field(torch.from_numpy(field).to(DEV))
+        outs.append(t.interpolate(torch.from_numpy(pos).to(DEV), out_dtype=torch.float64, deriv=bool(deriv)).cpu())
+        t.sync()
+    assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_direct_at_paper_density_matches_oracle(storage):
+    """1.5e-3 tracers per cell (the paper's production runs): AUTO picks the direct path."""
+    N = 64
+    n = int(1.5e-3 * N ** 3)
+    field = synth.velocity_field_np(N, 20, 401)
+    pos = synth.uniform_particles_np(n, 23)
+    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=storage)
+    t.set_field(torch.from_numpy(field).to(DEV))
+    assert t.step_kernel_for(n) == trk.TRK_STEP_DIRECT
+    u = t.interpolate(torch.from_numpy(pos).to(DEV), out_dtype=torch.float64)
+    p = torch.from_numpy(pos).to(DEV)
+    dt, steps = 4e-3, 6
+    t.advance(p, dt, steps, trk.TRK_RK2)
+    t.sync()
+    f = stored(field, storage)
+    rms = np.sqrt(np.mean(field ** 2))
+    scale = np.abs(field).max() * 1e-12 if storage == trk.TRK_F64 else 2e-6 * rms
+    assert np.abs(u.cpu().numpy() - oracle.interp(f, pos, trk.TRK_SPLINE, 6, 2)).max() <= scale
+    ref = oracle.advance(f, pos, dt, steps, trk.TRK_SPLINE, 6, 2)
+    assert np.abs(p.cpu().numpy() - ref).max() <= 5 * scale * dt * steps
+
+
+@pytest.mark.parametrize("N,n,shapes", [
+    (32, 200, ((8, 8, 8), (32, 32, 1))),                 # x3 slices
+    (128, 5000, ((8, 8, 8), (2, 2, 2), (1, 1, 1))),      # 2^18 and 2^21 blocks: the multi-CTA count scan
+])
+def test_direct_any_block_shape(N, n, shapes):
+    """The direct path needs no 8^3 cell blocks: with other groupings the results are the same."""
+    field = synth.velocity_field_np(N, 10, 402).astype(np.float32)
+    pos = synth.uniform_particles_np(n, 24)
+    res = []
+    for shape in shapes:
+        t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+        trk.tracker_set_block(t.h, *shape)
+        t.set_step_kernel(trk.TRK_STEP_DIRECT)
+        t.set_field(torch.from_numpy(field).to(DEV))
+        p = torch.from_numpy(pos).to(DEV)
+        t.advance(p, 4e-3, 4, trk.TRK_RK2)
+        t.sync()
+        res.append(p.cpu())
+    for r in res[1:]:
+        assert torch.equal(res[0], r)
+
+
+def test_direct_cfl_flag():
+    """Stage-2 points more than one cell away raise TRK_ECFL; the result is still exact."""
+    N, n, dt = 32, 600, 5e-3
+    field = (synth.velocity_field_np(N, 10, 81) * 30.0).astype(np.float32)
+    pos = synth.uniform_particles_np(n, 7)
+    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    t.set_step_kernel(trk.TRK_STEP_DIRECT)
+    t.set_field(torch.from_numpy(field).to(DEV))
+    p = torch.from_numpy(pos).to(DEV)
+    t.advance(p, dt, 2, trk.TRK_RK2)
+    with pytest.raises(trk.TrackerError) as e:
+        t.sync()
+    assert e.value.status == trk.TRK_ECFL
+    ref = oracle.advance(field.astype(np.float64), pos, dt, 2, trk.TRK_SPLINE, 6, 2)
+    assert np.abs(p.cpu().numpy() - ref).max() <= 5 * 2e-6 * 30.0 * dt * 2
+    # one cell per stage at most: no flag
+    p = torch.from_numpy(pos).to(DEV)
+    t.advance(p, 1e-4, 2, trk.TRK_RK2)
+    t.sync()
+
+
+def test_automatic_choice():
+    N = 64
+    f = synth.velocity_field_np(N, 5, 1)
+    t32 = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    thr = int(0.05 * N ** 3)
+    assert t32.step_kernel_for(0) == trk.TRK_STEP_DIRECT
+    assert t32.step_kernel_for(thr - 1) == trk.TRK_STEP_DIRECT
+    assert t32.step_kernel_for(thr + 1) == trk.TRK_STEP_COLUMN
+    t64 = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F64)
+    assert t64.step_kernel_for(thr + 1) == trk.TRK_STEP_BLOCK
+    t64.set_step_kernel(trk.TRK_STEP_DIRECT)
+    assert t64.step_kernel_for(10 ** 9) == trk.TRK_STEP_DIRECT
+    t32.set_step_kernel(trk.TRK_STEP_BLOCK)
+    assert t32.step_kernel_for(1) == trk.TRK_STEP_BLOCK
+    with pytest.raises(trk.TrackerError):
+        t32.step_kernel_for(-1)
+    del f
