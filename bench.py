@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the float64 and split-bf16 forms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "block", "column"],
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "block", "column", "direct"],
                     help="step kernel of the headline workload (default: the column kernel)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="2: the headline workload (default); 1 small, 3 precision, 4 batching, 5 adjoint")
@@ -154,7 +154,9 @@ def field_and_particles():
 STEP_KERNELS = {"column": ("k_column<6,5,RK2> (float32 field)", "k_column_rk2_f32_i6",
                             ("column_kernel.cuh", "column_i6.cu", "block_kernel.cuh", "internal.cuh", "coeffs.inc")),
                 "block": ("k_block<float,6,5,RK2,F32>", "k_block_rk2_f32_i6",
-                          ("block_kernel.cuh", "block_i6.cu", "internal.cuh", "coeffs.inc"))}
+                          ("block_kernel.cuh", "block_i6.cu", "internal.cuh", "coeffs.inc")),
+                "direct": ("k_direct<float,6,5,RK2,F32>", "k_direct_rk2_f32_i6",
+                           ("block_kernel.cuh", "direct_i6.cu", "internal.cuh", "coeffs.inc"))}
 
 
 def kernel_source_sha(kind="column"):
@@ -296,7 +298,7 @@ def run_gb300(args):
     field, pos = field_and_particles()
     tr = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
     tr.set_step_kernel({"auto": trk.TRK_STEP_AUTO, "block": trk.TRK_STEP_BLOCK,
-                        "column": trk.TRK_STEP_COLUMN}[args.step_kernel])
+                        "column": trk.TRK_STEP_COLUMN, "direct": trk.TRK_STEP_DIRECT}[args.step_kernel])
     tr.set_field(torch.from_numpy(field).to(dev))
     p = torch.from_numpy(pos).to(dev)
     stream = torch.cuda.current_stream()
@@ -351,7 +353,8 @@ def run_gb300(args):
     alg_bytes = field_bytes + 52 * NP                 # field once + fp64 positions read and written + key
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    kind = "block" if args.step_kernel == "block" else "column"
+    kind = {trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_COLUMN: "column",
+            trk.TRK_STEP_DIRECT: "direct"}[tr.step_kernel_for(NP)]
     sha = kernel_source_sha(kind)
     gather_bytes = NP * 2 * I ** 3 * 3 * 4            # two stencil gathers per RK2 step, float32
     sm_mhz = clk.get("sm_mhz") or 1900.0
@@ -418,6 +421,7 @@ def run_gb300(args):
             variants[name] = {"value": NP * args.inner * reps / (vms * 1e-3), "unit": UNIT,
                               "ab_steps": args.inner * reps, "field_storage": "f32"}
             del pv, hist
+        variants["sparse_1024"] = sparse_variant(trk, dev, stream, measured_peaks())
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -460,6 +464,44 @@ def run_gb300(args):
 # --------------------------------------------------------------------------
 # other configurations (single GPU; one JSON line each, same keys)
 # --------------------------------------------------------------------------
+def sparse_variant(trk, dev, stream, peaks):
+    """The paper's production density, 1.5e-3 tracers per grid cell, on a 1024^3
+    float32 field (spline I = 6, RK2): the automatic choice is the direct path.
+    Its roofline counts, per particle and stage, one stencil of I^3 nodes x 3
+    components x 4 B (no overlap between stencils at this density) plus 52 B of
+    particle state per step."""
+    import torch
+
+    import synth
+
+    Ns, ns = 1024, int(1.5e-3 * 1024 ** 3)
+    field = synth.velocity_field_torch(Ns, Ns // 3, 1006, device=dev, out_dtype=torch.float32)
+    tv = trk.Tracker(Ns, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
+    tv.set_field(field)
+    del field
+    kernel = tv.step_kernel_for(ns)
+    pv = torch.from_numpy(synth.uniform_particles_np(ns, 7)).to(dev)
+    steps = 20
+    tv.advance(pv, DT, steps, trk.TRK_RK2)
+    torch.cuda.synchronize()
+    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0.record(stream)
+    tv.advance(pv, DT, steps, trk.TRK_RK2)
+    v1.record(stream)
+    torch.cuda.synchronize()
+    ms = v0.elapsed_time(v1) / steps
+    alg = ns * (2 * I ** 3 * 3 * 4 + 52)
+    tv.close()
+    del pv
+    torch.cuda.empty_cache()
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"value": ns / (ms * 1e-3), "unit": UNIT, "N": Ns, "np": ns, "per_cell": 1.5e-3, "scheme": "RK2",
+            "kernel": {trk.TRK_STEP_DIRECT: "direct", trk.TRK_STEP_COLUMN: "column",
+                       trk.TRK_STEP_BLOCK: "block"}[kernel],
+            "ms_per_step": ms, "alg_bytes_per_step": alg, "achieved_gbs": gbs, "hbm_frac": gbs / peaks[0],
+            "note": "whole step incl. binning; alg bytes = 2 stencils x I^3 x 3 x 4 B + 52 B state per particle"}
+
+
 def _events():
     import torch
 

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             const int pc = p_cell[q];
             const int c1 = pc & 1023, c2 = (pc >> 10) & 1023, c3 = (pc >> 20) & 1023;
             if (rp >= 0) L.load(SL{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)});
-            else L.load(GlobalLd<T, STORE, I>{a.f, c1, c2, c3, 0, 2, mask});
+            else L.load(global_ld<T, STORE, I>(a.f, c1, c2, c3, 0, 2));
             W.eval(rec.t[0] - (T)0.5, rec.t[1] - (T)0.5, rec.t[2] - (T)0.5, wv, wd);
             T acc[12];
             L.contract(wv, wd, acc);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
                     L.load(SL{halo + (s3 - LO) * S3 + (s2 - LO) * S2 + (s1 - LO)});
                 } else {
                     if (lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
-                    L.load(GlobalLd<T, STORE, I>{a.f, cs1, cs2, cs3, 0, 2, mask});
+                    L.load(global_ld<T, STORE, I>(a.f, cs1, cs2, cs3, 0, 2));
                 }
             }
             W.eval(ts[0] - (T)0.5, ts[1] - (T)0.5, ts[2] - (T)0.5, wv, wd);

@@ -175,20 +175,31 @@ __device__ __forceinline__ T fetch(const FieldView& f, int k, int64_t idx)
     else return (T)(__bfloat162float(f.hi[o]) + __bfloat162float(f.lo[o]));
 }
 
-// Global-memory loader with periodic wrap (stencils outside the staged halo).
+// Global-memory loader (stencils outside a staged halo, and the direct path).
+// The cell c lies in [0, N) and a stencil node is at most I/2 <= PAD cells
+// from it, so every node is inside the ghost-padded array: no periodic wrap,
+// and each node is a fixed offset from the stencil's first node.
 template <typename T, int STORE, int I>
 struct GlobalLd {
     static constexpr bool kShared = false;
     FieldView f;
-    int c1, c2, c3, k0, kmax, mask;
+    int64_t base;        // padded index of node (c1, c2, c3) - (I/2 - 1)
+    int k0, kmax;        // component k reads min(k0 + k, kmax)
     __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
     {
-        const int x1 = (c1 + a1 - (I / 2 - 1)) & mask;
-        const int x2 = (c2 + a2 - (I / 2 - 1)) & mask;
-        const int x3 = (c3 + a3 - (I / 2 - 1)) & mask;
-        return fetch<T, STORE>(f, min(k0 + k, kmax), padded_index(f.NP, x1, x2, x3));
+        const int64_t NP = f.NP;
+        return fetch<T, STORE>(f, min(k0 + k, kmax), base + ((int64_t)a3 * NP + a2) * NP + a1);
     }
 };
+
+// c1, c2, c3 in [0, N)
+template <typename T, int STORE, int I>
+__device__ __forceinline__ GlobalLd<T, STORE, I> global_ld(const FieldView& f, int c1, int c2, int c3, int k0,
+                                                           int kmax)
+{
+    constexpr int LO = I / 2 - 1;
+    return GlobalLd<T, STORE, I>{f, padded_index(f.NP, c1 - LO, c2 - LO, c3 - LO), k0, kmax};
+}
 
 // ---------------------------------------------------------------------------
 // 1-D weights, once per particle and axis: lane l < 3I evaluates
@@ -869,8 +880,8 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                     L.load(SL{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)});
                 } else {
                     const int pc = p_cell[q];
-                    L.load(GlobalLd<T, STORE, I>{a.f, pc & 1023, (pc >> 10) & 1023, (pc >> 20) & 1023, 3 * ch,
-                                                 a.f.C - 1, mask});
+                    L.load(global_ld<T, STORE, I>(a.f, pc & 1023, (pc >> 10) & 1023, (pc >> 20) & 1023, 3 * ch,
+                                                  a.f.C - 1));
                 }
                 W.eval(t1 - (T)0.5, t2 - (T)0.5, t3 - (T)0.5, wv, wd);
                 T acc[12];
@@ -901,9 +912,8 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                             const bool far = HALO || abs(dc[0]) > 1 || abs(dc[1]) > 1 || abs(dc[2]) > 1;
                             if (far && lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
                             const int pc = p_cell[q];
-                            L.load(GlobalLd<T, STORE, I>{a.f, ((pc & 1023) + dc[0]) & mask,
-                                                         (((pc >> 10) & 1023) + dc[1]) & mask,
-                                                         (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2, mask});
+                            L.load(global_ld<T, STORE, I>(a.f, ((pc & 1023) + dc[0]) & mask, (((pc >> 10) & 1023) + dc[1]) & mask,
+                                                          (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2));
                         }
                     }
                     W.eval(ts[0] - (T)0.5, ts[1] - (T)0.5, ts[2] - (T)0.5, wv, wd);

@@ -400,9 +400,8 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
                             } else {
                                 if (lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
                                 const int pc = cells[q];
-                                L.load(GlobalLd<T, ST_F32, I>{a.f, ((pc & 1023) + dc[0]) & mask,
-                                                              (((pc >> 10) & 1023) + dc[1]) & mask,
-                                                              (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2, mask});
+                                L.load(global_ld<T, ST_F32, I>(a.f, ((pc & 1023) + dc[0]) & mask, (((pc >> 10) & 1023) + dc[1]) & mask,
+                                                          (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2));
                             }
                         }
                         W.eval(ts[0] - (T)0.5, ts[1] - (T)0.5, ts[2] - (T)0.5, wv, wd);
