@@ -49,7 +49,8 @@ typedef enum {
     TRK_ECUDA = -3,       /* CUDA runtime error (message has the CUDA string) */
     TRK_ENONFINITE = -4,  /* a position was NaN/Inf or beyond 2^51 cells (device flag) */
     TRK_ENOFIELD = -6,    /* no field set yet */
-    TRK_ECFL = -7         /* a particle moved more than one cell in one stage (device flag; result still exact) */
+    TRK_ECFL = -7,        /* a particle moved more than one cell in one stage (device flag; result still exact) */
+    TRK_EIO = -8          /* a state file could not be written or read, or failed its checks */
 } trk_status;
 
 typedef enum { TRK_LAGRANGE = 0, TRK_SPLINE = 1 } trk_family;
@@ -234,6 +235,50 @@ typedef struct {
  * Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
 int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double dt, int steps,
                             int history_valid);
+
+/* ---------------------------------------------------------------------- */
+/* Tracer-set checkpoints (in-order particle output and restart, Sec. 3.4) */
+/* ---------------------------------------------------------------------- */
+
+/* What a state file holds besides the arrays.  N, L, family, I, m record the
+ * writer's grid and kernel (a reader compares them with its own tracker);
+ * scheme and history_valid describe the AB history (as in tracker_advance);
+ * step, time and dt are the run's counters (an AB history is only valid for
+ * the dt it was made with). */
+typedef struct {
+    int32_t N;
+    double L;
+    int32_t family, I, m;
+    int64_t np;
+    int32_t scheme;
+    int32_t history_valid;
+    int64_t step;
+    double time;
+    double dt;
+} trk_state_info;
+
+/* Write a tracer set to a binary file: a 96-byte header (magic, version, the
+ * info fields, checksums of header and payload), then pos[3][np] float64 and,
+ * for ABk, rhs[3(k-1)][np] float32, all in the caller's particle order (the
+ * order tracker_advance returns).  Little-endian, no padding.  pos and rhs
+ * are HOST pointers (copy device arrays first); rhs is ignored for RK2.  The
+ * file is written under a temporary name and renamed into place, so a failed
+ * write leaves an existing file intact.  Errors: TRK_EINVAL (bad fields or
+ * NULL arrays), TRK_EIO (open/write/rename failed). */
+int tracker_state_write(const char* path, const trk_state_info* info, const double* pos, const float* rhs);
+
+/* Read only the header of a state file into *info (to size the buffers).
+ * Errors: TRK_EINVAL, TRK_EIO (missing file, wrong magic or version,
+ * header checksum mismatch, invalid fields). */
+int tracker_state_read_info(const char* path, trk_state_info* info);
+
+/* Read a state file into HOST buffers pos[3][np] and, for ABk,
+ * rhs[3(k-1)][np]; np must equal the file's particle count.  *info receives
+ * the header.  The payload checksum is verified after reading (the buffers
+ * then hold the file's bytes even when TRK_EIO reports a mismatch).
+ * Errors: TRK_EINVAL (np differs, NULL arrays), TRK_EIO (as above, a
+ * truncated payload, trailing bytes, payload checksum mismatch). */
+int tracker_state_read(const char* path, int64_t np, double* pos, float* rhs, trk_state_info* info);
 
 /* ---------------------------------------------------------------------- */
 /* Adjoint (no counterpart in the paper: gradient of a loss through RK2)   */

@@ -26,7 +26,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libtracker.so")
 
-TRK_OK, TRK_EINVAL, TRK_ENOMEM, TRK_ECUDA, TRK_ENONFINITE, TRK_ENOFIELD, TRK_ECFL = 0, -1, -2, -3, -4, -6, -7
+TRK_OK, TRK_EINVAL, TRK_ENOMEM, TRK_ECUDA, TRK_ENONFINITE, TRK_ENOFIELD, TRK_ECFL, TRK_EIO = 0, -1, -2, -3, -4, -6, -7, -8
 TRK_LAGRANGE, TRK_SPLINE = 0, 1
 TRK_F64, TRK_F32, TRK_BF16X2 = 0, 1, 2
 TRK_RK2, TRK_AB2, TRK_AB3, TRK_AB4 = 0, 1, 2, 3
@@ -34,7 +34,7 @@ TRK_DTYPE_F64, TRK_DTYPE_F32 = 0, 1
 TRK_STEP_AUTO, TRK_STEP_BLOCK, TRK_STEP_COLUMN, TRK_STEP_DIRECT = 0, 1, 2, 3
 
 _STATUS = {TRK_EINVAL: "EINVAL", TRK_ENOMEM: "ENOMEM", TRK_ECUDA: "ECUDA", TRK_ENONFINITE: "ENONFINITE",
-           TRK_ENOFIELD: "ENOFIELD", TRK_ECFL: "ECFL"}
+           TRK_ENOFIELD: "ENOFIELD", TRK_ECFL: "ECFL", TRK_EIO: "EIO"}
 
 # Every exported symbol of the ABI (checked against include/tracker.h by the tests).
 ABI_FUNCTIONS = (
@@ -42,7 +42,7 @@ ABI_FUNCTIONS = (
     "tracker_set_field", "tracker_set_block", "tracker_num_blocks", "tracker_bin", "tracker_interpolate",
     "tracker_advance", "tracker_advance_batched", "tracker_adjoint", "tracker_launch_count",
     "tracker_profile", "tracker_profile_read", "tracker_bin_static", "tracker_set_step_kernel",
-    "tracker_step_kernel_for",
+    "tracker_step_kernel_for", "tracker_state_write", "tracker_state_read_info", "tracker_state_read",
 )
 
 
@@ -50,6 +50,15 @@ class TrackerError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{_STATUS.get(status, status)}: {message}")
         self.status = status
+
+
+class trk_state_info(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32), ("L", ctypes.c_double), ("family", ctypes.c_int32), ("I", ctypes.c_int32),
+        ("m", ctypes.c_int32), ("np", ctypes.c_int64), ("scheme", ctypes.c_int32),
+        ("history_valid", ctypes.c_int32), ("step", ctypes.c_int64), ("time", ctypes.c_double),
+        ("dt", ctypes.c_double),
+    ]
 
 
 class trk_set(ctypes.Structure):
@@ -93,6 +102,9 @@ def load_library(path: str = LIB_PATH):
             "tracker_bin_static": (c_int, [c_i64, vp, c_int, c_d, c_int, c_int, c_int, vp, vp, vp, vp, vp]),
             "tracker_set_step_kernel": (c_int, [vp, c_int]),
             "tracker_step_kernel_for": (c_int, [vp, c_i64]),
+            "tracker_state_write": (c_int, [ctypes.c_char_p, vp, vp, vp]),
+            "tracker_state_read_info": (c_int, [ctypes.c_char_p, vp]),
+            "tracker_state_read": (c_int, [ctypes.c_char_p, c_i64, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -184,6 +196,50 @@ def tracker_step_kernel_for(h, np_) -> int:
     r = int(load_library().tracker_step_kernel_for(h, int(np_)))
     _check(min(r, 0))
     return r
+
+
+def _host_copy(x, dtype, rows, np_, name):
+    """A contiguous host copy of a [rows][np] (or [k][3][np]) array."""
+    if x is None:
+        raise ValueError(f"{name} is required")
+    t = torch.as_tensor(x)
+    if t.dtype != dtype or t.numel() != rows * np_:
+        raise ValueError(f"{name} must be {dtype} with {rows} x {np_} values")
+    return t.detach().to("cpu").contiguous()
+
+
+def tracker_state_write(path, pos, rhs=None, scheme=TRK_RK2, history_valid=0, step=0, time=0.0, dt=0.0,
+                        N=0, L=0.0, family=0, I=0, m=0):
+    """Write a tracer set (pos [3][np] float64, rhs [k-1][3][np] float32 for ABk) to a state file."""
+    np_ = int(torch.as_tensor(pos).shape[-1])
+    rows = 3 * int(scheme) if scheme in (TRK_AB2, TRK_AB3, TRK_AB4) else 0   # other values: the library rejects them
+    hp = _host_copy(pos, torch.float64, 3, np_, "pos")
+    hr = _host_copy(rhs, torch.float32, rows, np_, "rhs") if rows else None
+    info = trk_state_info(N=int(N), L=float(L), family=int(family), I=int(I), m=int(m), np=np_,
+                          scheme=int(scheme), history_valid=int(history_valid), step=int(step), time=float(time),
+                          dt=float(dt))
+    _check(load_library().tracker_state_write(os.fsencode(path), ctypes.byref(info), _ptr(hp), _ptr(hr)))
+
+
+def tracker_state_read_info(path) -> dict:
+    info = trk_state_info()
+    _check(load_library().tracker_state_read_info(os.fsencode(path), ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in trk_state_info._fields_}
+
+
+def tracker_state_read(path, device=None):
+    """(pos [3][np] float64, rhs [k-1][3][np] float32 or None, info dict) from a state file."""
+    meta = tracker_state_read_info(path)
+    np_, scheme = meta["np"], meta["scheme"]
+    pos = torch.empty((3, np_), dtype=torch.float64)
+    rhs = torch.empty((scheme, 3, np_), dtype=torch.float32) if scheme != TRK_RK2 else None
+    info = trk_state_info()
+    _check(load_library().tracker_state_read(os.fsencode(path), np_, _ptr(pos), _ptr(rhs), ctypes.byref(info)))
+    meta = {f: getattr(info, f) for f, _ in trk_state_info._fields_}
+    if device is not None:
+        pos = pos.to(device)
+        rhs = rhs.to(device) if rhs is not None else None
+    return pos, rhs, meta
 
 
 def tracker_num_blocks(h) -> int:
@@ -336,6 +392,20 @@ class Tracker:
 
     def step_kernel_for(self, np_):
         return tracker_step_kernel_for(self.h, np_)
+
+    def save_state(self, path, pos, rhs=None, scheme=TRK_RK2, history_valid=0, step=0, time=0.0, dt=0.0):
+        """Checkpoint a tracer set with this tracker's grid and kernel in the header."""
+        tracker_state_write(path, pos, rhs, scheme, history_valid, step, time, dt, self.N, self.L, self.family,
+                            self.I, self.m)
+
+    def load_state(self, path, device="cuda"):
+        """Read a checkpoint written for the same grid and kernel: (pos, rhs, info)."""
+        pos, rhs, info = tracker_state_read(path, device)
+        mine = (self.N, self.family, self.I, self.m)
+        theirs = (info["N"], info["family"], info["I"], info["m"])
+        if mine != theirs or abs(info["L"] - self.L) > 0:
+            raise ValueError(f"state file was written for (N, family, I, m, L) = {theirs + (info['L'],)}")
+        return pos, rhs, info
 
     def bin(self, pos):
         self._stream()

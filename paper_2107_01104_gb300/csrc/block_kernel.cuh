@@ -183,12 +183,13 @@ template <typename T, int STORE, int I>
 struct GlobalLd {
     static constexpr bool kShared = false;
     FieldView f;
-    int64_t base;        // padded index of node (c1, c2, c3) - (I/2 - 1)
+    int base;            // padded index of node (c1, c2, c3) - (I/2 - 1) within a component
     int k0, kmax;        // component k reads min(k0 + k, kmax)
     __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
     {
-        const int64_t NP = f.NP;
-        return fetch<T, STORE>(f, min(k0 + k, kmax), base + ((int64_t)a3 * NP + a2) * NP + a1);
+        // a padded component holds (N + 2 PAD)^3 < 2^31 nodes for N <= 1024: 32-bit offsets
+        const int NP = f.NP;
+        return fetch<T, STORE>(f, min(k0 + k, kmax), (int64_t)(base + (a3 * NP + a2) * NP + a1));
     }
 };
 
@@ -198,7 +199,7 @@ __device__ __forceinline__ GlobalLd<T, STORE, I> global_ld(const FieldView& f, i
                                                            int kmax)
 {
     constexpr int LO = I / 2 - 1;
-    return GlobalLd<T, STORE, I>{f, padded_index(f.NP, c1 - LO, c2 - LO, c3 - LO), k0, kmax};
+    return GlobalLd<T, STORE, I>{f, (int)padded_index(f.NP, c1 - LO, c2 - LO, c3 - LO), k0, kmax};
 }
 
 // ---------------------------------------------------------------------------

@@ -1,5 +1,5 @@
 // Column step kernel: persistent, warp-specialised, software-pipelined RK2 /
-// AB2 steps for float32 fields and kernel widths I = 4, 6.
+// Adams-Bashforth steps for float32 fields and kernel widths I = 4, 6.
 //
 // The paper distributes the particles in slabs along x3 and interpolates each
 // slab against its own field slab plus ghost layers (Sec. 3.3.1).  Here a CTA
@@ -22,20 +22,24 @@
 // slab (a slab with more particles has several tasks, an empty slab one empty
 // task).  Two kinds of warps run the tasks as a pipeline:
 //
-//   particle warp (1 warp): for task tau, prefetches the positions (and AB2
-//     history) of task tau + 2 by cp.async, splits the positions of task
-//     tau + 1 in float64 into the records the interpolation warps read (P1),
-//     then, once task tau is interpolated, does the float64 update, re-split
-//     and write-back of task tau (P3).  All float64 work is lane-dense here.
+//   particle warps (NPW: 1 for RK2, 2 for Adams-Bashforth, whose single
+//     stencil per step leaves one warp's float64 work on the critical path):
+//     warp w owns the tasks tau = w mod NPW.  For its task tau it prefetches
+//     the positions (and AB history) of its task tau + 2 NPW by cp.async,
+//     splits the positions of its task tau + NPW in float64 into the records
+//     the interpolation warps read (P1), then, once task tau is interpolated,
+//     does the float64 update, re-split and write-back of task tau (P3).  All
+//     float64 work is lane-dense here.
 //   interpolation warps (NQW warps): for task tau, wait for its records, on
 //     the first task of a slab copy that slab's successor's new planes into
 //     the ring (cp.async), then gather and contract the stencils, one warp
 //     per particle (stage 1 and, for RK2, stage 2), and hand k1 (k2) to the
-//     particle warp.
+//     particle warp that owns the task.
 //
-// Hand-offs use two named barriers per direction (double-buffered records and
-// k values): REC[tau % 2] (particle warp arrives, interpolation warps wait)
-// and KV[tau % 2] (interpolation warps arrive, particle warp waits).
+// Hand-offs use NB = 2 NPW named barriers per direction (records and k values
+// in NB buffers): REC[tau % NB] (the owning particle warp arrives,
+// interpolation warps wait) and KV[tau % NB] (interpolation warps arrive, the
+// owner waits).  Input slots rotate over NS = 3 NPW.
 //
 // Particle state is read from and written back to the same arrays, grouped
 // by block beforehand (counting-sort scatter), so each task's inputs are
@@ -50,9 +54,21 @@
 namespace trk {
 
 constexpr int PBC = 64;              // particles per task
-constexpr int NQW = 10;              // interpolation warps
-constexpr int NQT = NQW * 32;        // interpolation threads
-constexpr int NTC = NQT + 32;        // threads per CTA: interpolation warps + the particle warp
+constexpr int NQW_MAX = 10;          // interpolation warps at most (weight buffers)
+
+// warp roles and buffer counts of a step mode
+template <int MODE>
+struct ColCfg {
+    static constexpr int NPW = MODE == MODE_RK2 ? 1 : 2;   // particle warps
+    static constexpr int NQW = 10;                           // interpolation warps
+    static constexpr int NTC = (NQW + NPW) * 32;             // threads per CTA
+    static constexpr int NQT = NQW * 32;
+    static constexpr int NB = 2 * NPW;                       // record / k buffers, barriers per direction (power of 2)
+    static constexpr int NS = 3 * NPW;                       // input slots
+    static constexpr int BCNT = NQT + 32;                    // threads at a hand-off barrier
+    static_assert(NQW <= NQW_MAX, "weight buffers");
+    static_assert(NPW == 1 || NPW == 2, "one or two particle warps");
+};
 
 template <int I, int H>
 struct RingGeom {
@@ -61,15 +77,15 @@ struct RingGeom {
     static constexpr int P = R + M;      // allocated planes per component
 };
 
-template <size_t RING_BYTES, bool AB2>
+template <size_t RING_BYTES, bool AB2, int NB, int NS>
 struct ColPlan {
-    static constexpr size_t rec = align32(RING_BYTES);                                   // [2][PBC] records
-    static constexpr size_t cell = align32(rec + 2 * PBC * sizeof(PRec<float>));          // [2][PBC]
-    static constexpr size_t k = align32(cell + 2 * PBC * sizeof(int));                    // [2][6][PBC]
-    static constexpr size_t w = align32(k + (size_t)2 * 6 * PBC * sizeof(float));         // [NQW][48]
-    static constexpr size_t x = align32(w + (size_t)NQW * 48 * sizeof(float));            // [3][3][PBC]
-    static constexpr size_t rhs = align32(x + (size_t)3 * 3 * PBC * sizeof(double));      // [3][3][PBC]
-    static constexpr size_t seg = align32(rhs + (AB2 ? (size_t)3 * 3 * AB_MAX_HIST * PBC * sizeof(float) : 0));
+    static constexpr size_t rec = align32(RING_BYTES);                                    // [NB][PBC] records
+    static constexpr size_t cell = align32(rec + (size_t)NB * PBC * sizeof(PRec<float>));  // [NB][PBC]
+    static constexpr size_t k = align32(cell + (size_t)NB * PBC * sizeof(int));           // [NB][6][PBC]
+    static constexpr size_t w = align32(k + (size_t)NB * 6 * PBC * sizeof(float));         // [NQW_MAX][48]
+    static constexpr size_t x = align32(w + (size_t)NQW_MAX * 48 * sizeof(float));         // [NS][3][PBC]
+    static constexpr size_t rhs = align32(x + (size_t)NS * 3 * PBC * sizeof(double));      // [NS][3 AB_MAX_HIST][PBC]
+    static constexpr size_t seg = align32(rhs + (AB2 ? (size_t)NS * 3 * AB_MAX_HIST * PBC * sizeof(float) : 0));
     static constexpr size_t total = seg + (size_t)2 * MAXSEG * sizeof(int);
 };
 
@@ -79,11 +95,12 @@ constexpr size_t column_smem_bytes()
     constexpr int MARGIN = (MODE == MODE_RK2) ? 1 : 0;
     constexpr int H = BLK + I - 1 + 2 * MARGIN;
     using RG = RingGeom<I, H>;
-    return ColPlan<(size_t)3 * RG::P * Layout<I, H>::S3 * sizeof(float), MODE == MODE_AB2>::total;
+    using CC = ColCfg<MODE>;
+    return ColPlan<(size_t)3 * RG::P * Layout<I, H>::S3 * sizeof(float), MODE == MODE_AB2, CC::NB, CC::NS>::total;
 }
 
-// named barriers (0 is __syncthreads)
-enum { BAR_REC = 1, BAR_KV = 3 };   // BAR_REC + 0/1, BAR_KV + 0/1
+// named barriers (0 is __syncthreads): REC + 0 .. NB-1, then KV + 0 .. NB-1
+constexpr int BAR_REC = 1;
 
 // compile-time barrier ids (a runtime id makes ptxas reserve all sixteen)
 template <int ID>
@@ -96,18 +113,34 @@ __device__ __forceinline__ void bar_arrive(int count)
 {
     asm volatile("bar.arrive %0, %1;\n" ::"n"(ID), "r"(count) : "memory");
 }
-// barrier BASE + (parity & 1)
-template <int BASE>
-__device__ __forceinline__ void bar_sync_par(int parity, int count)
+// barrier BASE + i, 0 <= i < NB (NB = 2 or 4)
+template <int BASE, int NB>
+__device__ __forceinline__ void bar_sync_idx(int i, int count)
 {
-    if (parity & 1) bar_sync<BASE + 1>(count);
-    else bar_sync<BASE>(count);
+    static_assert(NB == 2 || NB == 4, "two or four buffers");
+    if constexpr (NB == 2) {
+        if (i == 0) bar_sync<BASE>(count);
+        else bar_sync<BASE + 1>(count);
+    } else {
+        if (i == 0) bar_sync<BASE>(count);
+        else if (i == 1) bar_sync<BASE + 1>(count);
+        else if (i == 2) bar_sync<BASE + 2>(count);
+        else bar_sync<BASE + 3>(count);
+    }
 }
-template <int BASE>
-__device__ __forceinline__ void bar_arrive_par(int parity, int count)
+template <int BASE, int NB>
+__device__ __forceinline__ void bar_arrive_idx(int i, int count)
 {
-    if (parity & 1) bar_arrive<BASE + 1>(count);
-    else bar_arrive<BASE>(count);
+    static_assert(NB == 2 || NB == 4, "two or four buffers");
+    if constexpr (NB == 2) {
+        if (i == 0) bar_arrive<BASE>(count);
+        else bar_arrive<BASE + 1>(count);
+    } else {
+        if (i == 0) bar_arrive<BASE>(count);
+        else if (i == 1) bar_arrive<BASE + 1>(count);
+        else if (i == 2) bar_arrive<BASE + 2>(count);
+        else bar_arrive<BASE + 3>(count);
+    }
 }
 
 // A task: particles [j0, j0 + n) of slab s; first = first task of the slab.
@@ -132,7 +165,7 @@ __device__ __forceinline__ Task next_task(const Task& t, const int* s_beg, const
 }
 
 template <int I, int DEG, int MODE>
-__global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ ColumnArgs ca)
+__global__ void __launch_bounds__(ColCfg<MODE>::NTC, 2) k_column(const __grid_constant__ ColumnArgs ca)
 {
     using T = float;
     static_assert(MODE == MODE_RK2 || MODE == MODE_AB2, "column kernel: time steps only");
@@ -147,25 +180,29 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
     using RG = RingGeom<I, H>;
     constexpr int R = RG::R, M = RG::M;
     constexpr int SC = RG::P * S3;                 // ring component stride
-    using CP = ColPlan<(size_t)3 * SC * sizeof(T), IS_AB2>;
+    using CC = ColCfg<MODE>;
+    constexpr int NPW = CC::NPW, NQW = CC::NQW, NB = CC::NB, NS = CC::NS, BCNT = CC::BCNT;
+    constexpr int BAR_KV = BAR_REC + NB;
+    using CP = ColPlan<(size_t)3 * SC * sizeof(T), IS_AB2, NB, NS>;
     using SL = SmemLd<T, S2, S3, SC>;
-    static_assert(H - I < R && H * H <= NQT, "ring geometry");
+    static_assert(H - I < R && H * H <= CC::NQT, "ring geometry");
+    static_assert(BAR_KV + NB <= 16, "named barriers");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_item;
     T* ring = reinterpret_cast<T*>(smem_raw);
-    PRec<T>* p_rec = reinterpret_cast<PRec<T>*>(smem_raw + CP::rec);   // [2][PBC]
-    int* p_cell = reinterpret_cast<int*>(smem_raw + CP::cell);          // [2][PBC]
-    T* p_k = reinterpret_cast<T*>(smem_raw + CP::k);                    // [2][6][PBC]
+    PRec<T>* p_rec = reinterpret_cast<PRec<T>*>(smem_raw + CP::rec);   // [NB][PBC]
+    int* p_cell = reinterpret_cast<int*>(smem_raw + CP::cell);          // [NB][PBC]
+    T* p_k = reinterpret_cast<T*>(smem_raw + CP::k);                    // [NB][6][PBC]
     T* wbuf = reinterpret_cast<T*>(smem_raw + CP::w);                   // [NQW][48]
-    double* p_x = reinterpret_cast<double*>(smem_raw + CP::x);          // [3 slots][3][PBC]
-    float* p_rhs = reinterpret_cast<float*>(smem_raw + CP::rhs);        // [3 slots][3 AB_MAX_HIST][PBC] (AB)
+    double* p_x = reinterpret_cast<double*>(smem_raw + CP::x);          // [NS][3][PBC]
+    float* p_rhs = reinterpret_cast<float*>(smem_raw + CP::rhs);        // [NS][3 AB_MAX_HIST][PBC] (AB)
     int* s_beg = reinterpret_cast<int*>(smem_raw + CP::seg);            // [MAXSEG]
     int* s_end = s_beg + MAXSEG;                                        // [MAXSEG]
 
     const BlockArgs& a = ca.a;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool pwarp = warp == NQW;                                     // the particle warp
+    const bool pwarp = warp >= NQW;                                     // a particle warp
     const int mask = a.g.mask, nb1 = a.g.nb1, nb2 = a.g.nb2;
     const int64_t np = a.np;
     const double inv_delta = a.g.inv_delta;
@@ -286,32 +323,44 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
                 }
             };
 
+            // this warp's tasks: tau = pw, pw + NPW, pw + 2 NPW, ...
+            const unsigned pw = NPW == 1 ? 0u : (unsigned)(warp - NQW);
+            auto adv = [&](Task t) {
+#pragma unroll
+                for (int i = 0; i < NPW; ++i) t = next_task(t, s_beg, s_end, nseg);
+                return t;
+            };
             Task t0 = first_task(s_beg, s_end);
-            Task t1 = next_task(t0, s_beg, s_end, nseg);
-            Task t2 = next_task(t1, s_beg, s_end, nseg);
-            issue_inputs(t0, 0);
-            issue_inputs(t1, 1);                       // empty group when t1 is the end marker
+            if (NPW > 1 && pw > 0) t0 = next_task(t0, s_beg, s_end, nseg);
+            Task t1 = adv(t0);
+            Task t2 = adv(t1);
+            unsigned tau = pw;
+            issue_inputs(t0, tau % NS);                // empty groups for end markers
+            issue_inputs(t1, (tau + NPW) % NS);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
             __syncwarp();
-            p1(t0, 0, 0);
-            __syncwarp();
-            bar_arrive<BAR_REC>(NTC);
-            for (int tau = 0; t0.s < nseg; ++tau) {
-                // inputs of tau + 2 (slot (tau + 2) % 3, last read by P3 of tau - 1)
-                if (t2.s < nseg) issue_inputs(t2, (tau + 2) % 3);
+            if (t0.s < nseg) {
+                p1(t0, tau % NS, tau & (NB - 1));
+                __syncwarp();
+                bar_arrive_idx<BAR_REC, NB>(tau & (NB - 1), BCNT);
+            }
+            for (; t0.s < nseg; tau += NPW) {
+                // inputs of tau + 2 NPW (their slot was last read by P3 of tau - NPW)
+                if (t2.s < nseg) issue_inputs(t2, (tau + 2 * NPW) % NS);
                 else asm volatile("cp.async.commit_group;\n" ::: "memory");
                 if (t1.s < nseg) {
-                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // inputs of tau + 1
+                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // inputs of tau + NPW
                     __syncwarp();
-                    p1(t1, (tau + 1) % 3, (tau + 1) & 1);
+                    // record buffer (tau + NPW) % NB was last read for task tau - NPW (its KV is passed)
+                    p1(t1, (tau + NPW) % NS, (tau + NPW) & (NB - 1));
                     __syncwarp();
-                    bar_arrive_par<BAR_REC>(tau + 1, NTC);
+                    bar_arrive_idx<BAR_REC, NB>((tau + NPW) & (NB - 1), BCNT);
                 }
-                bar_sync_par<BAR_KV>(tau, NTC);                                // task tau interpolated
-                p3(t0, tau % 3, tau & 1);
+                bar_sync_idx<BAR_KV, NB>(tau & (NB - 1), BCNT);                // task tau interpolated
+                p3(t0, tau % NS, tau & (NB - 1));
                 t0 = t1;
                 t1 = t2;
-                t2 = next_task(t2, s_beg, s_end, nseg);
+                t2 = adv(t2);
             }
             asm volatile("cp.async.wait_all;\n" ::: "memory");
         } else {
@@ -356,10 +405,10 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
             issue_planes(za0, H);                                   // window of slab 0
             asm volatile("cp.async.wait_all;\n" ::: "memory");
             Task t = first_task(s_beg, s_end);
-            for (int tau = 0; t.s < nseg; ++tau) {
-                bar_sync_par<BAR_REC>(tau, NTC);     // records of tau ready; every warp is done with tau - 1
+            for (unsigned tau = 0; t.s < nseg; ++tau) {
+                bar_sync_idx<BAR_REC, NB>(tau & (NB - 1), BCNT);   // records of tau ready; every warp is done with tau - 1
                 if (t.first && t.s + 1 < nseg) issue_planes(za0 + (t.s + 1) * BLK + H - BLK, BLK);
-                const int rb = tau & 1;
+                const int rb = tau & (NB - 1);
                 const PRec<T>* recs = p_rec + rb * PBC;
                 const int* cells = p_cell + rb * PBC;
                 T* kk = p_k + rb * 6 * PBC;
@@ -400,8 +449,9 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
                             } else {
                                 if (lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
                                 const int pc = cells[q];
-                                L.load(global_ld<T, ST_F32, I>(a.f, ((pc & 1023) + dc[0]) & mask, (((pc >> 10) & 1023) + dc[1]) & mask,
-                                                          (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2));
+                                L.load(global_ld<T, ST_F32, I>(a.f, ((pc & 1023) + dc[0]) & mask,
+                                                               (((pc >> 10) & 1023) + dc[1]) & mask,
+                                                               (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2));
                             }
                         }
                         W.eval(ts[0] - (T)0.5, ts[1] - (T)0.5, ts[2] - (T)0.5, wv, wd);
@@ -415,7 +465,7 @@ __global__ void __launch_bounds__(NTC, 2) k_column(const __grid_constant__ Colum
                         if (writer) kk[rcomp * PBC + q] = m;
                     }
                 }
-                bar_arrive_par<BAR_KV>(tau, NTC);                    // k of tau ready
+                bar_arrive_idx<BAR_KV, NB>(tau & (NB - 1), BCNT);    // k of tau ready
                 const Task tn = next_task(t, s_beg, s_end, nseg);
                 // the next slab's planes (copied at the start of this slab) must have landed
                 // before its first task; the barrier that opens that task publishes them
@@ -437,13 +487,13 @@ cudaError_t launch_column_t(const ColumnArgs& ca, int nsm, cudaStream_t st)
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTC, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, ColCfg<MODE>::NTC, smem);
         if (e != cudaSuccess) return e;
         grid_per_sm = occ > 0 ? occ : 1;
     }
     if (ca.nitems <= 0) return cudaSuccess;
     const int64_t grid = std::min<int64_t>(ca.nitems, (int64_t)grid_per_sm * nsm);
-    kern<<<(unsigned)grid, NTC, smem, st>>>(ca);
+    kern<<<(unsigned)grid, ColCfg<MODE>::NTC, smem, st>>>(ca);
     return cudaGetLastError();
 }
 
