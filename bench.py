@@ -52,8 +52,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "block", "column", "direct"],
                     help="step kernel of the headline workload (default: the column kernel)")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
-                    help="2: the headline workload (default); 1 small, 3 precision, 4 batching, 5 adjoint")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6],
+                    help="2: the headline workload (default); 1 small, 3 precision, 4 batching, 5 adjoint, "
+                         "6 the paper's sparse tracer density")
+    ap.add_argument("--sparse-n", type=int, default=1024, help="grid of config 6 (1.5e-3 tracers per cell)")
     return ap.parse_args()
 
 
@@ -354,7 +356,7 @@ def run_gb300(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
     kind = {trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_COLUMN: "column",
-            trk.TRK_STEP_DIRECT: "direct"}[tr.step_kernel_for(NP)]
+            trk.TRK_STEP_DIRECT: "direct"}[tr.last_step_kernel()]
     sha = kernel_source_sha(kind)
     gather_bytes = NP * 2 * I ** 3 * 3 * 4            # two stencil gathers per RK2 step, float32
     sm_mhz = clk.get("sm_mhz") or 1900.0
@@ -447,7 +449,8 @@ def run_gb300(args):
             "smem_roofline": {"achieved": gather_bytes / avg_launch_s / 1e9, "peak": smem_peak, "unit": "GB/s",
                               "frac": gather_bytes / avg_launch_s / 1e9 / smem_peak,
                               "gather_bytes_per_launch": gather_bytes,
-                              "peak_def": "SMs x 128 B/clk x median SM clock under load"},
+                              "path": "shared memory" if kind != "direct" else "L1 (global gathers)",
+                              "peak_def": "SMs x 128 B/clk (the L1 / shared-memory data path) x median SM clock under load"},
             "phase_ms_per_step": {"step_kernel": step_ms / psteps, "binning": prof["bin"][0] / psteps,
                                   "other": prof["other"][0] / psteps, "profiled_steps": psteps,
                                   "note": "event-bracketed launches without graph replay"},
@@ -475,6 +478,7 @@ def sparse_variant(trk, dev, stream, peaks):
     import synth
 
     Ns, ns = 1024, int(1.5e-3 * 1024 ** 3)
+    dt = DT * 256 / Ns                      # the same CFL number as the 256^3 workload
     field = synth.velocity_field_torch(Ns, Ns // 3, 1006, device=dev, out_dtype=torch.float32)
     tv = trk.Tracker(Ns, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
     tv.set_field(field)
@@ -482,11 +486,11 @@ def sparse_variant(trk, dev, stream, peaks):
     kernel = tv.step_kernel_for(ns)
     pv = torch.from_numpy(synth.uniform_particles_np(ns, 7)).to(dev)
     steps = 20
-    tv.advance(pv, DT, steps, trk.TRK_RK2)
+    tv.advance(pv, dt, steps, trk.TRK_RK2)
     torch.cuda.synchronize()
     v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     v0.record(stream)
-    tv.advance(pv, DT, steps, trk.TRK_RK2)
+    tv.advance(pv, dt, steps, trk.TRK_RK2)
     v1.record(stream)
     torch.cuda.synchronize()
     ms = v0.elapsed_time(v1) / steps
@@ -498,7 +502,7 @@ def sparse_variant(trk, dev, stream, peaks):
     return {"value": ns / (ms * 1e-3), "unit": UNIT, "N": Ns, "np": ns, "per_cell": 1.5e-3, "scheme": "RK2",
             "kernel": {trk.TRK_STEP_DIRECT: "direct", trk.TRK_STEP_COLUMN: "column",
                        trk.TRK_STEP_BLOCK: "block"}[kernel],
-            "ms_per_step": ms, "alg_bytes_per_step": alg, "achieved_gbs": gbs, "hbm_frac": gbs / peaks[0],
+            "ms_per_step": ms, "dt": dt, "alg_bytes_per_step": alg, "achieved_gbs": gbs, "hbm_frac": gbs / peaks[0],
             "note": "whole step incl. binning; alg bytes = 2 stencils x I^3 x 3 x 4 B + 52 B state per particle"}
 
 
@@ -661,6 +665,81 @@ def run_config4(args):
           {"gpu_launches": t.launch_count - l0, "per_set_path": "direct or halo, chosen by timing"})
 
 
+def run_config6(args):
+    """The paper's production density, 1.5e-3 tracers per grid cell, on an N^3
+    float32 field (default 1024^3), spline I = 6, 20 RK2 steps per call; the
+    automatic choice is the direct path.  Roofline of the step kernel in
+    algorithmic bytes: per particle and stage one stencil of I^3 x 3 x 4 B
+    (stencils do not overlap at this density) plus 52 B of particle state."""
+    import torch
+
+    import paper_2107_01104_gb300 as trk
+    import synth
+
+    Ns = args.sparse_n
+    ns, inner = int(1.5e-3 * Ns ** 3), 20
+    dt = DT * 256 / Ns                      # the same CFL number as the 256^3 workload
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    field = synth.velocity_field_torch(Ns, Ns // 3, 1006, device=dev, out_dtype=torch.float32)
+    t = trk.Tracker(Ns, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
+    t.set_field(field)
+    del field
+    kind = {trk.TRK_STEP_DIRECT: "direct", trk.TRK_STEP_COLUMN: "column",
+            trk.TRK_STEP_BLOCK: "block"}[t.step_kernel_for(ns)]
+    p = synth.uniform_particles_torch(ns, 7, device=dev)
+    notes = {"cfl_slow_path_used": False}
+    for _ in range(args.warmup):
+        t.advance(p, dt, inner, trk.TRK_RK2)
+    sync_flags(t, trk, notes)
+    l0 = t.launch_count
+    e0, e1 = _events()
+    e0.record(stream)
+    for _ in range(args.steps):
+        t.advance(p, dt, inner, trk.TRK_RK2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = t.launch_count - l0
+    ms = e0.elapsed_time(e1) / (args.steps * inner)
+    trk.tracker_profile(t.h, True)
+    t.advance(p, dt, inner, trk.TRK_RK2)
+    torch.cuda.synchronize()
+    prof = trk.tracker_profile_read(t.h)
+    trk.tracker_profile(t.h, False)
+    sync_flags(t, trk, notes)
+    step_ms, step_n = prof["step"]
+    launch_s = step_ms * 1e-3 / max(step_n, 1)
+    alg = ns * (2 * I ** 3 * 3 * 4 + 52)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / launch_s / 1e9
+    per_particle = sparse_traffic_per_particle(kind)
+    _line("particle-steps/s", ns / (ms * 1e-3), "particle-steps/s", args, ms * inner,
+          f"{Ns}^3 fp32 velocity |k|<={Ns // 3}, {ns} uniform tracers (1.5e-3 per cell, the paper's density), "
+          f"spline I={I} m={M}, {inner} RK2 steps dt={dt} per call, re-binned every step",
+          {"roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": per_particle * ns if per_particle else None, "kernel": kind,
+                        "alg_bytes_per_launch": alg, "avg_launch_ms": launch_s * 1e3, "peak_kind": peak_kind,
+                        "alg_def": "2 stencils x I^3 x 3 x 4 B + 52 B state per particle-step"},
+           "phase_ms_per_step": {"step_kernel": step_ms / inner, "binning": prof["bin"][0] / inner},
+           "gpu_launches": launches, "notes": notes})
+
+
+def sparse_traffic_per_particle(kind):
+    """DRAM bytes per particle of the sparse direct step kernel from the committed
+    ncu summary (captured on a smaller grid at the same density; the traffic of
+    this kernel grows with the particle count), if it matches the source."""
+    if kind != "direct":
+        return None
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        e = json.load(fh).get("k_direct_rk2_f32_i6_sparse")
+    if not e or e.get("source_sha") != kernel_source_sha("direct"):
+        return None
+    return e.get("dram_bytes_per_particle")
+
+
 def run_config5(args):
     """256^3 float32 u, 2^22 tracers, spline I=6, 20 RK2 steps, adjoint with checkpoints every 5."""
     import numpy as np
@@ -717,7 +796,7 @@ def main():
 
         torch.cuda.set_device(0)
         lib_build.build()
-        {1: run_config1, 3: run_config3, 4: run_config4, 5: run_config5}[args.config](args)
+        {1: run_config1, 3: run_config3, 4: run_config4, 5: run_config5, 6: run_config6}[args.config](args)
 
 
 if __name__ == "__main__":

@@ -200,16 +200,27 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     point of RK2 is gathered wherever it lies; TRK_ECFL is raised when it
  *     is more than one cell away.
  *   TRK_STEP_AUTO (default): DIRECT below 0.05 particles per grid cell
- *     (np < 0.05 N^3, the measured crossover), else COLUMN where available,
- *     else BLOCK.  tracker_interpolate uses DIRECT or BLOCK.
+ *     (np < 0.05 N^3), else COLUMN where available, else BLOCK.  Where the
+ *     column kernel exists and the density lies in [0.01, 0.25], the first
+ *     tracker_advance call of at least 6 steps for a given (np, scheme) runs
+ *     two of its steps on each kernel, timed with CUDA events (the host waits
+ *     for them once; skipped while the stream is being captured), and that
+ *     and later calls use the faster (the crossover moves with N and the
+ *     scheme).  tracker_interpolate uses DIRECT or BLOCK.
  * All kernels perform the same floating-point operations in the same
  * order, so their results are bit-identical.  TRK_STEP_COLUMN on a tracker
  * without a column kernel is TRK_EINVAL.  Errors: TRK_EINVAL. */
 int tracker_set_step_kernel(tracker* t, int kind);
 
-/* The trk_step_kernel (COLUMN, BLOCK or DIRECT) that tracker_advance uses
- * for np particles under the current setting; negative status on error. */
+/* The trk_step_kernel (COLUMN, BLOCK or DIRECT) that tracker_advance starts
+ * with for np particles under the current setting, before any timing;
+ * negative status on error. */
 int tracker_step_kernel_for(const tracker* t, int64_t np);
+
+/* The trk_step_kernel the latest tracker_advance ran its remaining steps
+ * with (after any timing), TRK_STEP_AUTO before the first call; negative
+ * status on error. */
+int tracker_last_step_kernel(const tracker* t);
 
 /* ---------------------------------------------------------------------- */
 /* Batched advection: many particle sets, one persistent launch per step  */

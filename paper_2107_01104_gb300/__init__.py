@@ -43,6 +43,7 @@ ABI_FUNCTIONS = (
     "tracker_advance", "tracker_advance_batched", "tracker_adjoint", "tracker_launch_count",
     "tracker_profile", "tracker_profile_read", "tracker_bin_static", "tracker_set_step_kernel",
     "tracker_step_kernel_for", "tracker_state_write", "tracker_state_read_info", "tracker_state_read",
+    "tracker_last_step_kernel",
 )
 
 
@@ -102,6 +103,7 @@ def load_library(path: str = LIB_PATH):
             "tracker_bin_static": (c_int, [c_i64, vp, c_int, c_d, c_int, c_int, c_int, vp, vp, vp, vp, vp]),
             "tracker_set_step_kernel": (c_int, [vp, c_int]),
             "tracker_step_kernel_for": (c_int, [vp, c_i64]),
+            "tracker_last_step_kernel": (c_int, [vp]),
             "tracker_state_write": (c_int, [ctypes.c_char_p, vp, vp, vp]),
             "tracker_state_read_info": (c_int, [ctypes.c_char_p, vp]),
             "tracker_state_read": (c_int, [ctypes.c_char_p, c_i64, vp, vp, vp]),
@@ -392,6 +394,12 @@ class Tracker:
 
     def step_kernel_for(self, np_):
         return tracker_step_kernel_for(self.h, np_)
+
+    def last_step_kernel(self):
+        """The step kernel the latest advance used (after AUTO's timing)."""
+        r = int(load_library().tracker_last_step_kernel(self.h))
+        _check(min(r, 0))
+        return r
 
     def save_state(self, path, pos, rhs=None, scheme=TRK_RK2, history_valid=0, step=0, time=0.0, dt=0.0):
         """Checkpoint a tracer set with this tracker's grid and kernel in the header."""

@@ -193,6 +193,23 @@ struct GlobalLd {
     }
 };
 
+// Global-memory loader from the node-major float32 copy (the direct path): the
+// C components of a node are adjacent, so a stencil row of I nodes is I*C*4
+// contiguous bytes instead of C separate runs of I*4 bytes, which roughly
+// halves the DRAM sectors a sparse particle's stencil costs.
+template <typename T, int I>
+struct NodeLd {
+    static constexpr bool kShared = false;
+    const float* nm;
+    int base;            // padded index of node (c1, c2, c3) - (I/2 - 1)
+    int NP, C, k0, kmax;
+    __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
+    {
+        const int node = base + (a3 * NP + a2) * NP + a1;
+        return (T)__ldg(nm + (int64_t)node * C + min(k0 + k, kmax));
+    }
+};
+
 // c1, c2, c3 in [0, N)
 template <typename T, int STORE, int I>
 __device__ __forceinline__ GlobalLd<T, STORE, I> global_ld(const FieldView& f, int c1, int c2, int c3, int k0,
@@ -771,8 +788,9 @@ __host__ __device__ constexpr int stage_of()
 // the halo staging and gathers every stencil from global memory (the direct
 // path for sparse particle sets, where a halo would serve one or two
 // particles); its shared-memory plan has no halo region and b is unused.
-// Must be called by all threads of the CTA.
-template <typename T, int I, int DEG, int MODE, int STORE, bool HALO>
+// NM (with HALO = false, float32 storage): the gathers read the node-major
+// copy a.f.nm.  Must be called by all threads of the CTA.
+template <typename T, int I, int DEG, int MODE, int STORE, bool HALO, bool NM = false>
 __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0, int j1, unsigned char* smem_raw)
 {
     constexpr bool IS_AB2 = (MODE == MODE_AB2 || MODE == MODE_AB2_D);
@@ -818,6 +836,15 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     const T dtid = (T)(a.dt * inv_delta);
     const int rcomp = ((lane & 16) ? 2 : 0) + ((lane & 8) ? 1 : 0);   // component held after reduce4
     const bool writer = (lane & 7) == 0 && rcomp < 3;                 // lanes 0, 8, 16
+
+    // a stencil from global memory at cell (c1, c2, c3) in [0, N)^3, components k0 + k (clamped to kmax)
+    static_assert(!NM || (!HALO && STORE == ST_F32), "node-major gathers: direct path, float32 storage");
+    auto gload = [&](int c1, int c2, int c3, int k0, int kmax) {
+        if constexpr (NM)
+            L.load(NodeLd<T, I>{a.f.nm, (int)padded_index(a.f.NP, c1 - LO, c2 - LO, c3 - LO), a.f.NP, a.f.C, k0, kmax});
+        else
+            L.load(global_ld<T, STORE, I>(a.f, c1, c2, c3, k0, kmax));
+    };
 
     // the halo of component chunk ch (all three velocity components for the steps)
     constexpr bool ASYNC = STORE != ST_BF16X2;
@@ -881,8 +908,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                     L.load(SL{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)});
                 } else {
                     const int pc = p_cell[q];
-                    L.load(global_ld<T, STORE, I>(a.f, pc & 1023, (pc >> 10) & 1023, (pc >> 20) & 1023, 3 * ch,
-                                                  a.f.C - 1));
+                    gload(pc & 1023, (pc >> 10) & 1023, (pc >> 20) & 1023, 3 * ch, a.f.C - 1);
                 }
                 W.eval(t1 - (T)0.5, t2 - (T)0.5, t3 - (T)0.5, wv, wd);
                 T acc[12];
@@ -913,8 +939,8 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                             const bool far = HALO || abs(dc[0]) > 1 || abs(dc[1]) > 1 || abs(dc[2]) > 1;
                             if (far && lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
                             const int pc = p_cell[q];
-                            L.load(global_ld<T, STORE, I>(a.f, ((pc & 1023) + dc[0]) & mask, (((pc >> 10) & 1023) + dc[1]) & mask,
-                                                          (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2));
+                            gload(((pc & 1023) + dc[0]) & mask, (((pc >> 10) & 1023) + dc[1]) & mask,
+                                  (((pc >> 20) & 1023) + dc[2]) & mask, 0, 2);
                         }
                     }
                     W.eval(ts[0] - (T)0.5, ts[1] - (T)0.5, ts[2] - (T)0.5, wv, wd);
@@ -1027,7 +1053,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN
 }
 
 // Direct path: CTA c takes the sorted particles [c PB, (c + 1) PB) and
-// gathers their stencils from global memory (no halo, no cell-block grid).
+// gathers their stencils from global memory (no halo, no cell-block grid);
+// float32 fields are read from the node-major copy a.f.nm.
 template <typename T, int I, int DEG, int MODE, int STORE>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN_BLOCKS) : 1)
     k_direct(const __grid_constant__ BlockArgs a)
@@ -1035,7 +1062,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int64_t j0 = (int64_t)blockIdx.x * PB;
     const int64_t j1 = j0 + PB < a.np ? j0 + PB : a.np;
-    process_block<T, I, DEG, MODE, STORE, false>(a, 0, (int)j0, (int)j1, smem_raw);
+    process_block<T, I, DEG, MODE, STORE, false, STORE == ST_F32>(a, 0, (int)j0, (int)j1, smem_raw);
 }
 
 template <typename T, int I, int MODE>
@@ -1057,6 +1084,7 @@ cudaError_t launch_direct_t(const BlockArgs& a, cudaStream_t st)
         attr_set = true;
     }
     if (a.np <= 0) return cudaSuccess;
+    if (STORE == ST_F32 && !a.f.nm) return cudaErrorInvalidValue;   // the node-major copy is required
     kern<<<(unsigned)((a.np + PB - 1) / PB), NT, smem, st>>>(a);
     return cudaGetLastError();
 }

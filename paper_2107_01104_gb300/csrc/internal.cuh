@@ -43,6 +43,7 @@ struct FieldView {
     const float* f32;         // [C][NP^3]                (ST_F32)
     const __nv_bfloat16* hi;  // [C][NP^3] high parts     (ST_BF16X2)
     const __nv_bfloat16* lo;  // [C][NP^3] low parts      (ST_BF16X2)
+    const float* nm;          // [NP^3][C] node-major copy of f32 for the direct path, or null
 };
 
 __host__ __device__ __forceinline__ int64_t padded_index(int NP, int x1, int x2, int x3)
@@ -219,6 +220,8 @@ cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id
 
 // Fill the ghost-padded storage from a dense field src[C][N][N][N] (periodic ghosts).
 cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int C, int N, void* dst, cudaStream_t st);
+// node-major copy nm[node][C] of the padded float32 field f[C][node] (plane nodes)
+cudaError_t launch_node_major(const float* f, int C, int64_t plane, float* nm, cudaStream_t st);
 
 // dLoss/dfield from the per-block partial sums: every node adds, in a fixed
 // order, the partials of the non-empty blocks whose halo holds it

@@ -119,6 +119,9 @@ struct tracker {
     // field
     int C = 0;
     void* field = nullptr;
+    float* field_nm = nullptr;        // node-major copy of a float32 field (direct path), built on first use
+    size_t nm_bytes = 0;
+    bool nm_valid = false;
     // sort scratch
     int64_t sort_cap = 0;
     void* sort_scratch = nullptr;
@@ -153,6 +156,8 @@ struct tracker {
     std::vector<std::pair<uint64_t, int>> tune_cache;   // set signature -> direct path?
     int nsm = 0;
     int step_kernel = TRK_STEP_AUTO;  // trk_step_kernel
+    std::vector<std::pair<uint64_t, int>> path_cache;   // (np, mode, order) -> step kernel chosen by timing
+    int last_kernel = TRK_STEP_AUTO;  // step kernel of the latest tracker_advance
     int* d_colctr = nullptr;          // work counter of the column kernel
     uint32_t* d_counts = nullptr;     // [nblocks] block counts (counting-sort binning of the column path)
     int32_t* d_cursor = nullptr;      // [nblocks] scatter cursors
@@ -289,6 +294,7 @@ FieldView field_view(const tracker* t)
         f.hi = reinterpret_cast<const __nv_bfloat16*>(t->field);
         f.lo = f.hi + f.plane * t->C;
     }
+    f.nm = t->nm_valid ? t->field_nm : nullptr;
     return f;
 }
 
@@ -411,6 +417,35 @@ bool column_available(const tracker* t)
            t->g.lb3 == LBLK;
 }
 
+// The node-major copy of a float32 field that the direct kernel reads, made
+// (or refreshed after tracker_set_field) before the first direct launch that
+// needs it; never inside a graph capture (the first step of a call is eager).
+int ensure_node_major(tracker* t)
+{
+    if (t->storage != ST_F32 || t->nm_valid) return TRK_OK;
+    const int64_t NP = t->N + 2 * PAD;
+    const int64_t plane = NP * NP * NP;
+    const size_t bytes = (size_t)plane * t->C * sizeof(float);
+    if (t->nm_bytes != bytes) {
+        dev_free(t->field_nm);
+        t->field_nm = nullptr;
+        t->nm_bytes = 0;
+        t->gen += 1;                  // captured graphs hold the old pointer
+        if (dev_alloc(&t->field_nm, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TRK_ENOMEM, "cannot allocate the node-major field copy (%zu bytes)", bytes);
+        }
+        t->nm_bytes = bytes;
+    }
+    {
+        ProfScope ps(t, PROF_OTHER);
+        CUDA_TRY(launch_node_major(reinterpret_cast<const float*>(t->field), t->C, plane, t->field_nm, t->stream));
+    }
+    t->launches += 1;
+    t->nm_valid = true;
+    return TRK_OK;
+}
+
 // Below this many particles per grid cell the automatic choice gathers every
 // stencil straight from global memory (direct path) instead of sweeping the
 // field.  Measured crossover on GB300 (float32 field, spline I = 6): RK2 steps
@@ -418,8 +453,15 @@ bool column_available(const tracker* t)
 // 0.652 vs 0.693 ms at 1/16; AB2 steps favour the direct path down to 1/16.
 constexpr double kDirectDensity = 0.05;
 
+// Densities (particles per cell) between which AUTO times the column and the
+// direct kernel on the first tracker_advance call of a (np, scheme) and keeps
+// the faster: the crossover moves with the grid (L2 holds a 256^3 float32
+// field but not a 512^3 one) and with the scheme.
+constexpr double kProbeMin = 0.01, kProbeMax = 0.25;
+constexpr int kProbeSteps = 4;   // two timed steps per kernel (the first launch of a kernel may load its module)
+
 // The kernel tracker_advance (and, between BLOCK and DIRECT, tracker_interpolate)
-// uses for np particles.
+// uses for np particles before any timing.
 int step_path(const tracker* t, int64_t np)
 {
     if (t->step_kernel != TRK_STEP_AUTO) return t->step_kernel;
@@ -624,6 +666,7 @@ int tracker_destroy(tracker* t)
     dev_free(t->d_counts);
     dev_free(t->d_cursor);
     dev_free(t->d_scan_tmp);
+    dev_free(t->field_nm);
     if (t->gev[0]) cudaEventDestroy(t->gev[0]);
     if (t->gev[1]) cudaEventDestroy(t->gev[1]);
     if (t->gstream) cudaStreamDestroy(t->gstream);
@@ -719,6 +762,7 @@ int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src
         ProfScope ps(t, PROF_OTHER);
         CUDA_TRY(launch_convert_field(t->storage, src_dtype == TRK_DTYPE_F64, dsrc, C, t->N, t->field, t->stream));
     }
+    t->nm_valid = false;              // the node-major copy is refreshed before its next use
     t->launches += 1;
     if (staging) {
         CUDA_TRY(cudaStreamSynchronize(t->stream));
@@ -754,6 +798,12 @@ int tracker_step_kernel_for(const tracker* t, int64_t np)
     return step_path(t, np);
 }
 
+int tracker_last_step_kernel(const tracker* t)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    return t->last_kernel;
+}
+
 int64_t tracker_launch_count(const tracker* t) { return t ? t->launches : -1; }
 
 int tracker_bin(tracker* t, int64_t np, const double* pos, int32_t* keys, int32_t* perm, int32_t* offsets)
@@ -780,6 +830,7 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     if (!direct && (rc = check_block_kernel_shape(t))) return rc;
     if (np == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
+    if (direct && (rc = ensure_node_major(t))) return rc;
     if ((rc = bin_into(t, np, pos, t->keys, t->perm, direct ? nullptr : t->offsets))) return rc;
     BlockArgs a = base_args(t);
     a.np = np;
@@ -810,13 +861,32 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     if (!std::isfinite(dt)) return fail(TRK_EINVAL, "dt must be finite");
     if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
     if (np > 0 && !pos) return fail(TRK_EINVAL, "pos must not be NULL");
-    const int path = step_path(t, np);
+    const int mode = k ? MODE_AB2 : MODE_RK2;
+    const int ab_order = k ? k : 2;
+    int path = step_path(t, np);
+    // AUTO between the column and the direct kernel: a cached timing decision,
+    // or time both now (both give bit-identical steps and share the binning)
+    bool probe = false;
+    const uint64_t sig = mix(mix(mix(0, (uint64_t)np), (uint64_t)mode), (uint64_t)ab_order);
+    if (t->step_kernel == TRK_STEP_AUTO && column_available(t) && np > 0) {
+        int cached = -1;
+        for (const auto& e : t->path_cache)
+            if (e.first == sig) cached = e.second;
+        if (cached >= 0) {
+            path = cached;
+        } else {
+            const double dens = (double)np / ((double)t->N * t->N * t->N);
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            CUDA_TRY(cudaStreamIsCapturing(t->stream, &cs));
+            probe = dens >= kProbeMin && dens <= kProbeMax && steps >= kProbeSteps + 2 &&
+                    cs == cudaStreamCaptureStatusNone;
+        }
+    }
     if (path != TRK_STEP_DIRECT && (rc = check_block_kernel_shape(t))) return rc;
     if (np == 0 || steps == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
     if ((rc = ensure_state(t, np))) return rc;
-    const int mode = k ? MODE_AB2 : MODE_RK2;
-    const int ab_order = k ? k : 2;
+    if ((path == TRK_STEP_DIRECT || probe) && (rc = ensure_node_major(t))) return rc;
     // initial keys from the caller's positions (with block counts on the column path)
     {
         ProfScope ps(t, PROF_BIN);
@@ -833,15 +903,48 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     // is full (k - 1 entries); from then on every step is the same and pairs
     // of steps are replayed from a CUDA graph.
     int hist = k ? history_valid : 0;
-    if ((rc = advance_step(t, np, path, mode, ab_order, hist, dt, 0, true, pos, rhs))) return rc;
-    int cur = 1;
-    int rest = steps - 1;
-    if (k) hist = std::min(hist + 1, k - 1);
-    for (; rest > 0 && k && hist < k - 1; --rest) {
-        if ((rc = advance_step(t, np, path, mode, ab_order, hist, dt, cur, false, nullptr, nullptr))) return rc;
-        cur ^= 1;
-        hist += 1;
+    int cur = 0, rest = steps;
+    bool first = true;
+    auto eager = [&](int p) {
+        const int r = advance_step(t, np, p, mode, ab_order, hist, dt, cur, first, first ? pos : nullptr,
+                                   first ? rhs : nullptr);
+        if (r == TRK_OK) {
+            first = false;
+            cur ^= 1;
+            --rest;
+            if (k) hist = std::min(hist + 1, k - 1);
+        }
+        return r;
+    };
+    if ((rc = eager(path))) return rc;
+    if (probe) {
+        // kProbeSteps eager steps, the first half on the column kernel, then on the direct one
+        cudaEvent_t ev[kProbeSteps + 1] = {};
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) rc = fail(TRK_ECUDA, "cudaEventCreate failed");
+        for (int i = 0; rc == TRK_OK && i < kProbeSteps; ++i) {
+            if (cudaEventRecord(ev[i], t->stream) != cudaSuccess) rc = fail(TRK_ECUDA, "cudaEventRecord failed");
+            if (rc == TRK_OK) rc = eager(2 * i < kProbeSteps ? TRK_STEP_COLUMN : TRK_STEP_DIRECT);
+        }
+        float ms[kProbeSteps] = {};
+        if (rc == TRK_OK && (cudaEventRecord(ev[kProbeSteps], t->stream) != cudaSuccess ||
+                             cudaEventSynchronize(ev[kProbeSteps]) != cudaSuccess))
+            rc = fail(TRK_ECUDA, "timing the step kernels failed");
+        for (int i = 0; rc == TRK_OK && i < kProbeSteps; ++i)
+            if (cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) != cudaSuccess) rc = fail(TRK_ECUDA, "cudaEventElapsedTime failed");
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (rc) return rc;
+        float col = ms[0], dir = ms[kProbeSteps / 2];
+        for (int i = 1; i < kProbeSteps / 2; ++i) {
+            col = std::min(col, ms[i]);
+            dir = std::min(dir, ms[kProbeSteps / 2 + i]);
+        }
+        path = dir < col ? TRK_STEP_DIRECT : TRK_STEP_COLUMN;
+        t->path_cache.emplace_back(sig, path);
     }
+    for (; rest > 0 && k && hist < k - 1;)
+        if ((rc = eager(path))) return rc;
     if (!t->prof && rest >= 2) {
         uint64_t key = mix(mix(mix(mix(0, (uint64_t)np), (uint64_t)mode), t->gen), dbits(dt));
         key = mix(mix(mix(key, (uint64_t)(uintptr_t)t->field), (uint64_t)ab_order), (uint64_t)path);
@@ -857,6 +960,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
         if ((rc = advance_step(t, np, path, mode, ab_order, hist, dt, cur, false, nullptr, nullptr))) return rc;
         cur ^= 1;
     }
+    t->last_kernel = path;
     ProfScope ps(t, PROF_OTHER);
     CUDA_TRY(launch_unpermute_pos(np, t->pos_s[cur], t->id_s[cur], pos, t->stream));
     t->launches += 1;

@@ -183,3 +183,75 @@ def test_automatic_choice():
     with pytest.raises(trk.TrackerError):
         t32.step_kernel_for(-1)
     del f
+
+
+def test_direct_sees_a_replaced_field():
+    """The direct path of a float32 tracker reads a node-major copy of the field:
+    after set_field it must gather the new values (interpolation and steps)."""
+    N, n = 32, 500
+    fa = synth.velocity_field_np(N, 10, 410).astype(np.float32)
+    fb = synth.velocity_field_np(N, 10, 411).astype(np.float32)
+    pos = synth.uniform_particles_np(n, 25)
+    td = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    td.set_step_kernel(trk.TRK_STEP_DIRECT)
+    tb = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    tb.set_step_kernel(trk.TRK_STEP_BLOCK)
+    x = torch.from_numpy(pos).to(DEV)
+    for f in (fa, fb, fa):
+        for t in (td, tb):
+            t.set_field(torch.from_numpy(f).to(DEV))
+        ud = td.interpolate(x, out_dtype=torch.float64)
+        ub = tb.interpolate(x, out_dtype=torch.float64)
+        pd, pb = x.clone(), x.clone()
+        td.advance(pd, 4e-3, 3, trk.TRK_RK2)
+        tb.advance(pb, 4e-3, 3, trk.TRK_RK2)
+        td.sync()
+        tb.sync()
+        assert torch.equal(ud, ub)
+        assert torch.equal(pd, pb)
+
+
+@pytest.mark.parametrize("scheme", [trk.TRK_RK2, trk.TRK_AB4])
+def test_automatic_choice_by_timing(scheme):
+    """At 1/16 per cell (inside the timed range) the first call of >= 6 steps
+    times both kernels and keeps one; the results equal the block kernel's and
+    the decision is reused."""
+    N = 64
+    n = N ** 3 // 16
+    field = synth.velocity_field_np(N, 20, 412).astype(np.float32)
+    pos = synth.uniform_particles_np(n, 26)
+    res = []
+    for kind in (trk.TRK_STEP_AUTO, trk.TRK_STEP_BLOCK):
+        t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+        t.set_step_kernel(kind)
+        t.set_field(torch.from_numpy(field).to(DEV))
+        assert t.last_step_kernel() == trk.TRK_STEP_AUTO
+        p = torch.from_numpy(pos).to(DEV)
+        k = scheme + 1
+        h = torch.zeros((max(k - 1, 1), 3, n), dtype=torch.float32, device=DEV)
+        kw = dict(rhs=h, history_valid=0) if scheme else {}
+        t.advance(p, 4e-3, 8, scheme, **kw)
+        chosen = t.last_step_kernel()
+        if scheme:
+            kw["history_valid"] = k - 1
+        t.advance(p, 4e-3, 7, scheme, **kw)
+        t.sync()
+        if kind == trk.TRK_STEP_AUTO:
+            assert chosen in (trk.TRK_STEP_COLUMN, trk.TRK_STEP_DIRECT)
+            assert t.last_step_kernel() == chosen                      # cached
+        else:
+            assert chosen == trk.TRK_STEP_BLOCK
+        res.append((p.cpu(), h.cpu()))
+    assert torch.equal(res[0][0], res[1][0])
+    assert torch.equal(res[0][1], res[1][1])
+
+
+def test_no_timing_for_short_calls():
+    N = 64
+    n = N ** 3 // 16
+    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    t.set_field(torch.from_numpy(synth.velocity_field_np(N, 5, 413).astype(np.float32)).to(DEV))
+    p = torch.from_numpy(synth.uniform_particles_np(n, 27)).to(DEV)
+    t.advance(p, 4e-3, 5, trk.TRK_RK2)
+    t.sync()
+    assert t.last_step_kernel() == t.step_kernel_for(n)
