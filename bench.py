@@ -612,9 +612,13 @@ def run_config3(args):
             if storage == trk.TRK_F32 and C == 3:
                 alg = 3 * N ** 3 * 4 + NPART * 36
                 ach = alg / (prof["step"][0] / reps * 1e-3) / 1e9
+                kname = {trk.TRK_STEP_DIRECT: "k_direct<float,8,7,INTERP,F32>",
+                         trk.TRK_STEP_BLOCK: "k_block<float,8,7,INTERP,F32>"}.get(t.last_step_kernel(), "?")
                 roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                        "traffic": None, "kernel": "k_block<float,8,7,INTERP,F32>", "alg_bytes_per_launch": alg,
+                        "traffic": None, "kernel": kname, "alg_bytes_per_launch": alg,
                         "peak_kind": peak_kind}
+            results[key]["kernel"] = {trk.TRK_STEP_DIRECT: "direct", trk.TRK_STEP_BLOCK: "block"}.get(
+                t.last_step_kernel(), "?")
             t.close()
             del out
             torch.cuda.empty_cache()

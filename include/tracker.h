@@ -206,7 +206,11 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     two of its steps on each kernel, timed with CUDA events (the host waits
  *     for them once; skipped while the stream is being captured), and that
  *     and later calls use the faster (the crossover moves with N and the
- *     scheme).  tracker_interpolate uses DIRECT or BLOCK.
+ *     scheme).  tracker_interpolate uses DIRECT or BLOCK, and in the same
+ *     density range its first call per (np, C, deriv, out_dtype) runs both
+ *     kernels (they write the same values) and keeps the faster: which one
+ *     wins depends on C (the direct kernel gathers every component of a node
+ *     at once for C = 3).
  * All kernels perform the same floating-point operations in the same
  * order, so their results are bit-identical.  TRK_STEP_COLUMN on a tracker
  * without a column kernel is TRK_EINVAL.  Errors: TRK_EINVAL. */
@@ -218,8 +222,8 @@ int tracker_set_step_kernel(tracker* t, int kind);
 int tracker_step_kernel_for(const tracker* t, int64_t np);
 
 /* The trk_step_kernel the latest tracker_advance ran its remaining steps
- * with (after any timing), TRK_STEP_AUTO before the first call; negative
- * status on error. */
+ * with, or the latest tracker_interpolate used (after any timing);
+ * TRK_STEP_AUTO before the first call; negative status on error. */
 int tracker_last_step_kernel(const tracker* t);
 
 /* ---------------------------------------------------------------------- */

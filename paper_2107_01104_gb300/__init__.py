@@ -396,7 +396,7 @@ class Tracker:
         return tracker_step_kernel_for(self.h, np_)
 
     def last_step_kernel(self):
-        """The step kernel the latest advance used (after AUTO's timing)."""
+        """The kernel the latest advance or interpolate used (after AUTO's timing)."""
         r = int(load_library().tracker_last_step_kernel(self.h))
         _check(min(r, 0))
         return r

@@ -443,12 +443,12 @@ __global__ void k_convert_padded(int storage, const S* __restrict__ src, int C, 
     }
 }
 
-// nm[i][k] = f[k][i]: each thread one node, reads coalesced per component,
-// writes its C values contiguously
-__global__ void k_node_major(const float* __restrict__ f, int C, int64_t plane, float* __restrict__ nm)
+// nm[i][k] = f[k][i] (k < C), 0 for C <= k < nmc: each thread one node, reads
+// coalesced per component, writes its nmc values contiguously
+__global__ void k_node_major(const float* __restrict__ f, int C, int nmc, int64_t plane, float* __restrict__ nm)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x)
-        for (int k = 0; k < C; ++k) nm[i * C + k] = f[k * plane + i];
+        for (int k = 0; k < nmc; ++k) nm[i * nmc + k] = k < C ? f[k * plane + i] : 0.0f;
 }
 
 unsigned grid_for(int64_t n, int threads) { return (unsigned)ceil_div(n > 0 ? n : 1, threads); }
@@ -576,9 +576,9 @@ cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id
     return cudaGetLastError();
 }
 
-cudaError_t launch_node_major(const float* f, int C, int64_t plane, float* nm, cudaStream_t st)
+cudaError_t launch_node_major(const float* f, int C, int nmc, int64_t plane, float* nm, cudaStream_t st)
 {
-    k_node_major<<<(unsigned)std::min<int64_t>(ceil_div(plane, 256), 1 << 20), 256, 0, st>>>(f, C, plane, nm);
+    k_node_major<<<(unsigned)std::min<int64_t>(ceil_div(plane, 256), 1 << 20), 256, 0, st>>>(f, C, nmc, plane, nm);
     return cudaGetLastError();
 }
 

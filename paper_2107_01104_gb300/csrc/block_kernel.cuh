@@ -158,7 +158,7 @@ __device__ __forceinline__ T horner_c(const T (&row)[TRK_TAB_MAX_DEG], T s)
 template <typename T, int S2_, int S3_, int SC_>
 struct SmemLd {
     static constexpr int S2 = S2_, S3 = S3_, SC = SC_;
-    static constexpr bool kShared = true;
+    static constexpr bool kShared = true, kNode4 = false;
     const T* base;
     __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
     {
@@ -181,7 +181,7 @@ __device__ __forceinline__ T fetch(const FieldView& f, int k, int64_t idx)
 // and each node is a fixed offset from the stencil's first node.
 template <typename T, int STORE, int I>
 struct GlobalLd {
-    static constexpr bool kShared = false;
+    static constexpr bool kShared = false, kNode4 = false;
     FieldView f;
     int base;            // padded index of node (c1, c2, c3) - (I/2 - 1) within a component
     int k0, kmax;        // component k reads min(k0 + k, kmax)
@@ -199,14 +199,27 @@ struct GlobalLd {
 // halves the DRAM sectors a sparse particle's stencil costs.
 template <typename T, int I>
 struct NodeLd {
-    static constexpr bool kShared = false;
+    static constexpr bool kShared = false, kNode4 = false;
     const float* nm;
     int base;            // padded index of node (c1, c2, c3) - (I/2 - 1)
-    int NP, C, k0, kmax;
+    int NP, nmc, k0, kmax;
     __device__ __forceinline__ T operator()(int k, int a1, int a2, int a3) const
     {
         const int node = base + (a3 * NP + a2) * NP + a1;
-        return (T)__ldg(nm + (int64_t)node * C + min(k0 + k, kmax));
+        return (T)__ldg(nm + (int64_t)node * nmc + min(k0 + k, kmax));
+    }
+};
+
+// The three velocity components of a node as one aligned 16-byte load from the
+// padded node-major copy (nmc = 4).
+template <int I>
+struct NodeLd4 {
+    static constexpr bool kShared = false, kNode4 = true;
+    const float4* nm;
+    int base, NP;
+    __device__ __forceinline__ float4 node(int a1, int a2, int a3) const
+    {
+        return __ldg(nm + (base + (a3 * NP + a2) * NP + a1));
     }
 };
 
@@ -295,6 +308,16 @@ struct Lane<T, 8, D> {
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
                     for (int i3 = 0; i3 < 8; ++i3) f[k][h][i3] = pa[k * LD::SC + 4 * h * LD::S2 + i3 * LD::S3];
+        } else if constexpr (LD::kNode4) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i3 = 0; i3 < 8; ++i3) {
+                    const float4 v = ld.node(i1, j + 4 * h, i3);
+                    f[0][h][i3] = v.x;
+                    f[1][h][i3] = v.y;
+                    f[2][h][i3] = v.z;
+                }
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k)
@@ -395,6 +418,15 @@ struct Lane<T, 6, D> {
                 f[k][6] = pb[k * LD::SC];
                 f[k][7] = pc[k * LD::SC];
             }
+        } else if constexpr (LD::kNode4) {
+#pragma unroll
+            for (int i3 = 0; i3 < 8; ++i3) {
+                // pass A: row (i1, j) at i3 < 6; pass B: node (i1, 5, j); pass C: node (i1, 5, 5)
+                const float4 v = i3 < 6 ? ld.node(i1, j, i3) : (i3 == 6 ? ld.node(i1, 5, j) : ld.node(i1, 5, 5));
+                f[0][i3] = v.x;
+                f[1][i3] = v.y;
+                f[2][i3] = v.z;
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -493,6 +525,14 @@ struct Lane<T, 4, D> {
                 f[k][0] = pa[k * LD::SC];
                 f[k][1] = pa[k * LD::SC + 2 * LD::S3];
             }
+        } else if constexpr (LD::kNode4) {
+            const float4 a = ld.node(i1, i2, p), b = ld.node(i1, i2, p + 2);
+            f[0][0] = a.x;
+            f[1][0] = a.y;
+            f[2][0] = a.z;
+            f[0][1] = b.x;
+            f[1][1] = b.y;
+            f[2][1] = b.z;
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -789,8 +829,10 @@ __host__ __device__ constexpr int stage_of()
 // path for sparse particle sets, where a halo would serve one or two
 // particles); its shared-memory plan has no halo region and b is unused.
 // NM (with HALO = false, float32 storage): the gathers read the node-major
-// copy a.f.nm.  Must be called by all threads of the CTA.
-template <typename T, int I, int DEG, int MODE, int STORE, bool HALO, bool NM = false>
+// copy a.f.nm, as one 16-byte load per node when NM == NM_VEC4 (three
+// components padded to four floats), else per component (NM_SCALAR).  Must be
+// called by all threads of the CTA.
+template <typename T, int I, int DEG, int MODE, int STORE, bool HALO, int NM = NM_NONE>
 __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0, int j1, unsigned char* smem_raw)
 {
     constexpr bool IS_AB2 = (MODE == MODE_AB2 || MODE == MODE_AB2_D);
@@ -838,10 +880,13 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     const bool writer = (lane & 7) == 0 && rcomp < 3;                 // lanes 0, 8, 16
 
     // a stencil from global memory at cell (c1, c2, c3) in [0, N)^3, components k0 + k (clamped to kmax)
-    static_assert(!NM || (!HALO && STORE == ST_F32), "node-major gathers: direct path, float32 storage");
+    static_assert(NM == NM_NONE || (!HALO && STORE == ST_F32), "node-major gathers: direct path, float32 storage");
     auto gload = [&](int c1, int c2, int c3, int k0, int kmax) {
-        if constexpr (NM)
-            L.load(NodeLd<T, I>{a.f.nm, (int)padded_index(a.f.NP, c1 - LO, c2 - LO, c3 - LO), a.f.NP, a.f.C, k0, kmax});
+        const int base = (int)padded_index(a.f.NP, c1 - LO, c2 - LO, c3 - LO);
+        if constexpr (NM == NM_VEC4)   // three components, padded to four floats per node
+            L.load(NodeLd4<I>{reinterpret_cast<const float4*>(a.f.nm), base, a.f.NP});
+        else if constexpr (NM == NM_SCALAR)
+            L.load(NodeLd<T, I>{a.f.nm, base, a.f.NP, a.f.nmc, k0, kmax});
         else
             L.load(global_ld<T, STORE, I>(a.f, c1, c2, c3, k0, kmax));
     };
@@ -1055,14 +1100,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN
 // Direct path: CTA c takes the sorted particles [c PB, (c + 1) PB) and
 // gathers their stencils from global memory (no halo, no cell-block grid);
 // float32 fields are read from the node-major copy a.f.nm.
-template <typename T, int I, int DEG, int MODE, int STORE>
+template <typename T, int I, int DEG, int MODE, int STORE, int NM>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN_BLOCKS) : 1)
     k_direct(const __grid_constant__ BlockArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int64_t j0 = (int64_t)blockIdx.x * PB;
     const int64_t j1 = j0 + PB < a.np ? j0 + PB : a.np;
-    process_block<T, I, DEG, MODE, STORE, false, STORE == ST_F32>(a, 0, (int)j0, (int)j1, smem_raw);
+    process_block<T, I, DEG, MODE, STORE, false, NM>(a, 0, (int)j0, (int)j1, smem_raw);
 }
 
 template <typename T, int I, int MODE>
@@ -1071,22 +1116,37 @@ constexpr size_t direct_smem_bytes()
     return SmemPlan<T, 0, stage_of<MODE>()>::total;
 }
 
-template <typename T, int I, int DEG, int MODE, int STORE>
-cudaError_t launch_direct_t(const BlockArgs& a, cudaStream_t st)
+template <typename T, int I, int DEG, int MODE, int STORE, int NM>
+cudaError_t launch_direct_nm(const BlockArgs& a, cudaStream_t st)
 {
     constexpr size_t smem = direct_smem_bytes<T, I, MODE>();
     static_assert(smem <= 232448, "direct shared-memory plan exceeds the per-block limit");
-    auto kern = k_direct<T, I, DEG, MODE, STORE>;
+    auto kern = k_direct<T, I, DEG, MODE, STORE, NM>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (a.np <= 0) return cudaSuccess;
-    if (STORE == ST_F32 && !a.f.nm) return cudaErrorInvalidValue;   // the node-major copy is required
     kern<<<(unsigned)((a.np + PB - 1) / PB), NT, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// float32 fields read the node-major copy (16-byte node loads for three
+// components, which the time steps always have), other storages the field
+template <typename T, int I, int DEG, int MODE, int STORE>
+cudaError_t launch_direct_t(const BlockArgs& a, cudaStream_t st)
+{
+    if (a.np <= 0) return cudaSuccess;
+    if constexpr (STORE == ST_F32) {
+        if (!a.f.nm) return cudaErrorInvalidValue;   // the node-major copy is required
+        constexpr bool STEP = MODE == MODE_RK2 || MODE == MODE_AB2;
+        if (STEP || (a.f.C == 3 && a.f.nmc == 4)) return launch_direct_nm<T, I, DEG, MODE, STORE, NM_VEC4>(a, st);
+        if constexpr (!STEP) return launch_direct_nm<T, I, DEG, MODE, STORE, NM_SCALAR>(a, st);
+        return cudaErrorInvalidValue;
+    } else {
+        return launch_direct_nm<T, I, DEG, MODE, STORE, NM_NONE>(a, st);
+    }
 }
 
 template <int I, int DEG>

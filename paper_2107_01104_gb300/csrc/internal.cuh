@@ -43,7 +43,8 @@ struct FieldView {
     const float* f32;         // [C][NP^3]                (ST_F32)
     const __nv_bfloat16* hi;  // [C][NP^3] high parts     (ST_BF16X2)
     const __nv_bfloat16* lo;  // [C][NP^3] low parts      (ST_BF16X2)
-    const float* nm;          // [NP^3][C] node-major copy of f32 for the direct path, or null
+    const float* nm;          // [NP^3][nmc] node-major copy of f32 for the direct path, or null
+    int nmc;                  // floats per node in nm: 4 for C = 3 (padded: one 16-byte load per node), else C
 };
 
 __host__ __device__ __forceinline__ int64_t padded_index(int NP, int x1, int x2, int x3)
@@ -92,6 +93,11 @@ struct BlockArgs {
 };
 
 constexpr int AB_MAX_HIST = 3;   // history entries of the highest supported order (AB4)
+
+// where the direct path gathers a float32 stencil from: the component-major
+// field, the node-major copy per component, or the node-major copy as one
+// 16-byte load per node (three components padded to four floats)
+enum { NM_NONE = 0, NM_SCALAR = 1, NM_VEC4 = 2 };
 
 // dt-free Adams-Bashforth increment of order q (1..4): sum_j beta^q_j u_{n-j}
 // with u_n = f0 and u_{n-j} = hist(j - 1), summed newest first; beta^q are the
@@ -220,8 +226,9 @@ cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id
 
 // Fill the ghost-padded storage from a dense field src[C][N][N][N] (periodic ghosts).
 cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int C, int N, void* dst, cudaStream_t st);
-// node-major copy nm[node][C] of the padded float32 field f[C][node] (plane nodes)
-cudaError_t launch_node_major(const float* f, int C, int64_t plane, float* nm, cudaStream_t st);
+// node-major copy nm[node][nmc] of the padded float32 field f[C][node] (plane nodes);
+// floats C .. nmc-1 of a node are zero
+cudaError_t launch_node_major(const float* f, int C, int nmc, int64_t plane, float* nm, cudaStream_t st);
 
 // dLoss/dfield from the per-block partial sums: every node adds, in a fixed
 // order, the partials of the non-empty blocks whose halo holds it

@@ -157,7 +157,8 @@ struct tracker {
     int nsm = 0;
     int step_kernel = TRK_STEP_AUTO;  // trk_step_kernel
     std::vector<std::pair<uint64_t, int>> path_cache;   // (np, mode, order) -> step kernel chosen by timing
-    int last_kernel = TRK_STEP_AUTO;  // step kernel of the latest tracker_advance
+    std::vector<std::pair<uint64_t, int>> interp_cache; // (np, C, deriv, out dtype) -> interpolation kernel
+    int last_kernel = TRK_STEP_AUTO;  // kernel of the latest tracker_advance or tracker_interpolate
     int* d_colctr = nullptr;          // work counter of the column kernel
     uint32_t* d_counts = nullptr;     // [nblocks] block counts (counting-sort binning of the column path)
     int32_t* d_cursor = nullptr;      // [nblocks] scatter cursors
@@ -295,6 +296,7 @@ FieldView field_view(const tracker* t)
         f.lo = f.hi + f.plane * t->C;
     }
     f.nm = t->nm_valid ? t->field_nm : nullptr;
+    f.nmc = t->C == 3 ? 4 : t->C;
     return f;
 }
 
@@ -425,7 +427,8 @@ int ensure_node_major(tracker* t)
     if (t->storage != ST_F32 || t->nm_valid) return TRK_OK;
     const int64_t NP = t->N + 2 * PAD;
     const int64_t plane = NP * NP * NP;
-    const size_t bytes = (size_t)plane * t->C * sizeof(float);
+    const int nmc = t->C == 3 ? 4 : t->C;
+    const size_t bytes = (size_t)plane * nmc * sizeof(float);
     if (t->nm_bytes != bytes) {
         dev_free(t->field_nm);
         t->field_nm = nullptr;
@@ -439,7 +442,7 @@ int ensure_node_major(tracker* t)
     }
     {
         ProfScope ps(t, PROF_OTHER);
-        CUDA_TRY(launch_node_major(reinterpret_cast<const float*>(t->field), t->C, plane, t->field_nm, t->stream));
+        CUDA_TRY(launch_node_major(reinterpret_cast<const float*>(t->field), t->C, nmc, plane, t->field_nm, t->stream));
     }
     t->launches += 1;
     t->nm_valid = true;
@@ -826,12 +829,31 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     if (!t->field) return fail(TRK_ENOFIELD, "no field set");
     if (np > 0 && (!pos || !out)) return fail(TRK_EINVAL, "pos and out must not be NULL");
     if (out_dtype != TRK_DTYPE_F64 && out_dtype != TRK_DTYPE_F32) return fail(TRK_EINVAL, "unknown out_dtype %d", out_dtype);
-    const bool direct = step_path(t, np) == TRK_STEP_DIRECT;
+    bool direct = step_path(t, np) == TRK_STEP_DIRECT;
+    // AUTO: a cached timing decision, or time the block and the direct kernel
+    // now (they write the same values; the better one depends on density, C
+    // and the grid)
+    bool probe = false;
+    const uint64_t sig = mix(mix(mix(mix(0x1f, (uint64_t)np), (uint64_t)t->C), (uint64_t)deriv), (uint64_t)out_dtype);
+    const bool block_shape = t->g.lb1 == LBLK && t->g.lb2 == LBLK && t->g.lb3 == LBLK;
+    if (t->step_kernel == TRK_STEP_AUTO && np > 0 && block_shape) {
+        int cached = -1;
+        for (const auto& e : t->interp_cache)
+            if (e.first == sig) cached = e.second;
+        if (cached >= 0) {
+            direct = cached == TRK_STEP_DIRECT;
+        } else {
+            const double dens = (double)np / ((double)t->N * t->N * t->N);
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            CUDA_TRY(cudaStreamIsCapturing(t->stream, &cs));
+            probe = dens >= kProbeMin && dens <= kProbeMax && cs == cudaStreamCaptureStatusNone;
+        }
+    }
     if (!direct && (rc = check_block_kernel_shape(t))) return rc;
     if (np == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
-    if (direct && (rc = ensure_node_major(t))) return rc;
-    if ((rc = bin_into(t, np, pos, t->keys, t->perm, direct ? nullptr : t->offsets))) return rc;
+    if ((direct || probe) && (rc = ensure_node_major(t))) return rc;
+    if ((rc = bin_into(t, np, pos, t->keys, t->perm, direct && !probe ? nullptr : t->offsets))) return rc;
     BlockArgs a = base_args(t);
     a.np = np;
     a.perm = t->perm;
@@ -839,8 +861,32 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     a.out = out;
     a.out_f64 = out_dtype == TRK_DTYPE_F64;
     const int mode = deriv ? MODE_INTERP_DERIV : MODE_INTERP;
+    if (probe) {
+        cudaEvent_t ev[3] = {};
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) rc = fail(TRK_ECUDA, "cudaEventCreate failed");
+        float tb = 0, td = 0;
+        if (rc == TRK_OK) {
+            cudaError_t e = cudaEventRecord(ev[0], t->stream);
+            if (e == cudaSuccess) e = launch_block(t, mode, a);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], t->stream);
+            if (e == cudaSuccess) e = launch_direct(t, mode, a);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2], t->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&tb, ev[0], ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&td, ev[1], ev[2]);
+            if (e != cudaSuccess) rc = fail(TRK_ECUDA, "timing the interpolation kernels: %s", cudaGetErrorString(e));
+        }
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (rc) return rc;
+        t->interp_cache.emplace_back(sig, td < tb ? TRK_STEP_DIRECT : TRK_STEP_BLOCK);
+        t->last_kernel = td < tb ? TRK_STEP_DIRECT : TRK_STEP_BLOCK;
+        return TRK_OK;
+    }
     if (direct) CUDA_TRY(launch_direct(t, mode, a));
     else CUDA_TRY(launch_block(t, mode, a));
+    t->last_kernel = direct ? TRK_STEP_DIRECT : TRK_STEP_BLOCK;
     return TRK_OK;
 }
 
@@ -1040,6 +1086,8 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
     if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
     int rc = check_block_kernel_shape(t);
     if (rc) return rc;
+    // the direct items of float32 sets read the node-major copy of the field
+    if (t->storage == TRK_F32 && nsets > 0 && steps > 0 && (rc = ensure_node_major(t))) return rc;
     std::vector<int> tabs(nsets);
     int64_t npmax = 0;
     for (int s = 0; s < nsets; ++s) {

@@ -255,3 +255,22 @@ def test_no_timing_for_short_calls():
     t.advance(p, 4e-3, 5, trk.TRK_RK2)
     t.sync()
     assert t.last_step_kernel() == t.step_kernel_for(n)
+
+
+@pytest.mark.parametrize("C,deriv", [(3, 0), (3, 1), (12, 0)])
+def test_interpolation_choice_by_timing(C, deriv):
+    """Inside the timed density range the first AUTO call runs both kernels and
+    keeps one; every call gives the block kernel's values."""
+    N, n = 32, 4099
+    rng = np.random.default_rng(40 + C)
+    field = rng.standard_normal((C, N, N, N)).astype(np.float32)
+    x = torch.from_numpy(synth.uniform_particles_np(n, 28)).to(DEV)
+    ta = trk.Tracker(N, family=trk.TRK_SPLINE, I=8, m=3, storage=trk.TRK_F32)
+    ta.set_field(torch.from_numpy(field).to(DEV))
+    tb = trk.Tracker(N, family=trk.TRK_SPLINE, I=8, m=3, storage=trk.TRK_F32)
+    tb.set_step_kernel(trk.TRK_STEP_BLOCK)
+    tb.set_field(torch.from_numpy(field).to(DEV))
+    ref = tb.interpolate(x, deriv=bool(deriv))
+    for _ in range(2):   # timed, then cached
+        assert torch.equal(ta.interpolate(x, deriv=bool(deriv)), ref)
+    ta.sync()
