@@ -196,11 +196,14 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     carry ~1e-3 tracers per grid cell, Sec. 4): particles sorted by block
  *     as for BLOCK, 256 of them per thread block, each stencil gathered
  *     from the field in global memory, so no field sweep and no halo per
- *     cell block (all storages and kernels, any block shape).  The stage-2
+ *     cell block (all storages and kernels, any block shape; float32 and
+ *     three-component split-bf16 fields are read from a node-major copy the
+ *     tracker keeps, 16 bytes per node, made on first use).  The stage-2
  *     point of RK2 is gathered wherever it lies; TRK_ECFL is raised when it
  *     is more than one cell away.
  *   TRK_STEP_AUTO (default): DIRECT below 0.05 particles per grid cell
- *     (np < 0.05 N^3), else COLUMN where available, else BLOCK.  Where the
+ *     (np < 0.05 N^3), else COLUMN where available; without a column kernel
+ *     DIRECT below 0.25 per cell, else BLOCK (measured crossovers).  Where the
  *     column kernel exists and the density lies in [0.01, 0.25], the first
  *     tracker_advance call of at least 6 steps for a given (np, scheme) runs
  *     two of its steps on each kernel, timed with CUDA events (the host waits

@@ -3,8 +3,8 @@
 // persistent launch per step.  CTAs take work items from a per-set atomic
 // counter, set after set: an item is a non-empty cell block (halo-staged
 // path) or, for sparse sets, a chunk of 256 sorted particles gathered straight
-// from global memory (direct path; float32 fields through the node-major
-// copy, one 16-byte load per stencil node).  The choice per set is made on the
+// from global memory (direct path, through the node-major copy of the field:
+// one 16-byte load per stencil node).  The choice per set is made on the
 // host (tracker_host.cu) by timing both paths once.
 #include <algorithm>
 
@@ -17,7 +17,7 @@ namespace {
 template <int I, int DEG, int STORE>
 __device__ __noinline__ void run_item(const BatchSet& S, int b, int j0, int j1, unsigned char* smem)
 {
-    constexpr int NM = STORE == ST_F32 ? NM_VEC4 : NM_NONE;   // three components (batched fields)
+    constexpr int NM = NM_VEC4;   // batched fields have three components: 16-byte node loads
     if (S.direct) {
         if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, false, NM>(S.a, b, j0, j1, smem);
         else process_block<float, I, DEG, MODE_AB2, STORE, false, NM>(S.a, b, j0, j1, smem);

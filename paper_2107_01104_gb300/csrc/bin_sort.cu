@@ -451,6 +451,20 @@ __global__ void k_node_major(const float* __restrict__ f, int C, int nmc, int64_
         for (int k = 0; k < nmc; ++k) nm[i * nmc + k] = k < C ? f[k * plane + i] : 0.0f;
 }
 
+// node i: the hi and lo halves of its three components, interleaved, then two zeros
+__global__ void k_node_major_bf16(const __nv_bfloat16* __restrict__ hi, const __nv_bfloat16* __restrict__ lo,
+                                  int64_t plane, uint4* __restrict__ nm)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t w[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            w[k] = (uint32_t)__bfloat16_as_ushort(hi[k * plane + i]) |
+                   ((uint32_t)__bfloat16_as_ushort(lo[k * plane + i]) << 16);
+        nm[i] = make_uint4(w[0], w[1], w[2], 0u);
+    }
+}
+
 unsigned grid_for(int64_t n, int threads) { return (unsigned)ceil_div(n > 0 ? n : 1, threads); }
 
 }  // namespace
@@ -579,6 +593,14 @@ cudaError_t launch_unpermute_rhs(int64_t np, const float* src, const int32_t* id
 cudaError_t launch_node_major(const float* f, int C, int nmc, int64_t plane, float* nm, cudaStream_t st)
 {
     k_node_major<<<(unsigned)std::min<int64_t>(ceil_div(plane, 256), 1 << 20), 256, 0, st>>>(f, C, nmc, plane, nm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_major_bf16(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t plane, void* nm,
+                                   cudaStream_t st)
+{
+    k_node_major_bf16<<<(unsigned)std::min<int64_t>(ceil_div(plane, 256), 1 << 20), 256, 0, st>>>(
+        hi, lo, plane, reinterpret_cast<uint4*>(nm));
     return cudaGetLastError();
 }
 

@@ -211,15 +211,26 @@ struct NodeLd {
 };
 
 // The three velocity components of a node as one aligned 16-byte load from the
-// padded node-major copy (nmc = 4).
-template <int I>
+// padded node-major copy (float32: nmc = 4; split-bf16: the three hi/lo pairs,
+// each value formed as float(hi) + float(lo) as in fetch()).
+template <int I, int STORE>
 struct NodeLd4 {
     static constexpr bool kShared = false, kNode4 = true;
-    const float4* nm;
+    const void* nm;
     int base, NP;
     __device__ __forceinline__ float4 node(int a1, int a2, int a3) const
     {
-        return __ldg(nm + (base + (a3 * NP + a2) * NP + a1));
+        const int i = base + (a3 * NP + a2) * NP + a1;
+        if constexpr (STORE == ST_F32) {
+            return __ldg(reinterpret_cast<const float4*>(nm) + i);
+        } else {
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(nm) + i);
+            auto val = [](uint32_t x) {
+                return __bfloat162float(__ushort_as_bfloat16((unsigned short)(x & 0xffffu))) +
+                       __bfloat162float(__ushort_as_bfloat16((unsigned short)(x >> 16)));
+            };
+            return make_float4(val(w.x), val(w.y), val(w.z), 0.0f);
+        }
     }
 };
 
@@ -880,11 +891,12 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     const bool writer = (lane & 7) == 0 && rcomp < 3;                 // lanes 0, 8, 16
 
     // a stencil from global memory at cell (c1, c2, c3) in [0, N)^3, components k0 + k (clamped to kmax)
-    static_assert(NM == NM_NONE || (!HALO && STORE == ST_F32), "node-major gathers: direct path, float32 storage");
+    static_assert(NM == NM_NONE || (!HALO && (STORE == ST_F32 || (STORE == ST_BF16X2 && NM == NM_VEC4))),
+                  "node-major gathers: direct path, float32 or (three components) split-bf16 storage");
     auto gload = [&](int c1, int c2, int c3, int k0, int kmax) {
         const int base = (int)padded_index(a.f.NP, c1 - LO, c2 - LO, c3 - LO);
-        if constexpr (NM == NM_VEC4)   // three components, padded to four floats per node
-            L.load(NodeLd4<I>{reinterpret_cast<const float4*>(a.f.nm), base, a.f.NP});
+        if constexpr (NM == NM_VEC4)   // three components, 16 bytes per node
+            L.load(NodeLd4<I, STORE>{a.f.nm, base, a.f.NP});
         else if constexpr (NM == NM_SCALAR)
             L.load(NodeLd<T, I>{a.f.nm, base, a.f.NP, a.f.nmc, k0, kmax});
         else
@@ -1138,12 +1150,19 @@ template <typename T, int I, int DEG, int MODE, int STORE>
 cudaError_t launch_direct_t(const BlockArgs& a, cudaStream_t st)
 {
     if (a.np <= 0) return cudaSuccess;
+    constexpr bool STEP = MODE == MODE_RK2 || MODE == MODE_AB2;
     if constexpr (STORE == ST_F32) {
         if (!a.f.nm) return cudaErrorInvalidValue;   // the node-major copy is required
-        constexpr bool STEP = MODE == MODE_RK2 || MODE == MODE_AB2;
         if (STEP || (a.f.C == 3 && a.f.nmc == 4)) return launch_direct_nm<T, I, DEG, MODE, STORE, NM_VEC4>(a, st);
         if constexpr (!STEP) return launch_direct_nm<T, I, DEG, MODE, STORE, NM_SCALAR>(a, st);
         return cudaErrorInvalidValue;
+    } else if constexpr (STORE == ST_BF16X2) {
+        // three-component fields (all time steps) read the node-major copy
+        if (a.f.C == 3) {
+            if (!a.f.nm) return cudaErrorInvalidValue;
+            return launch_direct_nm<T, I, DEG, MODE, STORE, NM_VEC4>(a, st);
+        }
+        return launch_direct_nm<T, I, DEG, MODE, STORE, NM_NONE>(a, st);
     } else {
         return launch_direct_nm<T, I, DEG, MODE, STORE, NM_NONE>(a, st);
     }

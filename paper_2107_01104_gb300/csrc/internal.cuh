@@ -43,8 +43,9 @@ struct FieldView {
     const float* f32;         // [C][NP^3]                (ST_F32)
     const __nv_bfloat16* hi;  // [C][NP^3] high parts     (ST_BF16X2)
     const __nv_bfloat16* lo;  // [C][NP^3] low parts      (ST_BF16X2)
-    const float* nm;          // [NP^3][nmc] node-major copy of f32 for the direct path, or null
-    int nmc;                  // floats per node in nm: 4 for C = 3 (padded: one 16-byte load per node), else C
+    const float* nm;          // node-major copy for the direct path, or null: float32 fields [NP^3][nmc];
+                              // split-bf16 fields with C = 3: 16 bytes per node (hi0 lo0 hi1 lo1 hi2 lo2 0 0)
+    int nmc;                  // float32: floats per node in nm, 4 for C = 3 (one 16-byte load per node), else C
 };
 
 __host__ __device__ __forceinline__ int64_t padded_index(int NP, int x1, int x2, int x3)
@@ -229,6 +230,9 @@ cudaError_t launch_convert_field(int storage, int src_f64, const void* src, int 
 // node-major copy nm[node][nmc] of the padded float32 field f[C][node] (plane nodes);
 // floats C .. nmc-1 of a node are zero
 cudaError_t launch_node_major(const float* f, int C, int nmc, int64_t plane, float* nm, cudaStream_t st);
+// node-major copy of a three-component split-bf16 field (hi planes, then lo planes): 16 bytes per node
+cudaError_t launch_node_major_bf16(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t plane, void* nm,
+                                   cudaStream_t st);
 
 // dLoss/dfield from the per-block partial sums: every node adds, in a fixed
 // order, the partials of the non-empty blocks whose halo holds it

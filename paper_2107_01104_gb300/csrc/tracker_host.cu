@@ -119,7 +119,7 @@ struct tracker {
     // field
     int C = 0;
     void* field = nullptr;
-    float* field_nm = nullptr;        // node-major copy of a float32 field (direct path), built on first use
+    float* field_nm = nullptr;        // node-major copy of the field for the direct path (float32; split-bf16 with C = 3), built on first use
     size_t nm_bytes = 0;
     bool nm_valid = false;
     // sort scratch
@@ -424,11 +424,12 @@ bool column_available(const tracker* t)
 // needs it; never inside a graph capture (the first step of a call is eager).
 int ensure_node_major(tracker* t)
 {
-    if (t->storage != ST_F32 || t->nm_valid) return TRK_OK;
+    const bool f32 = t->storage == ST_F32, bf16 = t->storage == ST_BF16X2 && t->C == 3;
+    if (!(f32 || bf16) || t->nm_valid) return TRK_OK;
     const int64_t NP = t->N + 2 * PAD;
     const int64_t plane = NP * NP * NP;
     const int nmc = t->C == 3 ? 4 : t->C;
-    const size_t bytes = (size_t)plane * nmc * sizeof(float);
+    const size_t bytes = (size_t)plane * nmc * sizeof(float);   // 16 bytes per node for C = 3
     if (t->nm_bytes != bytes) {
         dev_free(t->field_nm);
         t->field_nm = nullptr;
@@ -442,7 +443,12 @@ int ensure_node_major(tracker* t)
     }
     {
         ProfScope ps(t, PROF_OTHER);
-        CUDA_TRY(launch_node_major(reinterpret_cast<const float*>(t->field), t->C, nmc, plane, t->field_nm, t->stream));
+        if (f32) {
+            CUDA_TRY(launch_node_major(reinterpret_cast<const float*>(t->field), t->C, nmc, plane, t->field_nm, t->stream));
+        } else {
+            const __nv_bfloat16* hi = reinterpret_cast<const __nv_bfloat16*>(t->field);
+            CUDA_TRY(launch_node_major_bf16(hi, hi + plane * 3, plane, t->field_nm, t->stream));
+        }
     }
     t->launches += 1;
     t->nm_valid = true;
@@ -456,6 +462,14 @@ int ensure_node_major(tracker* t)
 // 0.652 vs 0.693 ms at 1/16; AB2 steps favour the direct path down to 1/16.
 constexpr double kDirectDensity = 0.05;
 
+// Without a column kernel (float64 or split-bf16 storage, I = 8, other block
+// shapes) the choice is between the block and the direct kernel, whose
+// binnings differ, so it is a density threshold, measured on GB300 (256^3,
+// RK2, block vs direct ms per step): float32 I = 8 1.24 vs 0.73 at 1/16 per
+// cell, 2.61 vs 2.65 at 1/4; float64 7.12 vs 6.02 and 24.7 vs 23.9;
+// split-bf16 (node-major copy) 1.19 vs 0.59 and 2.45 vs 2.20.
+double direct_threshold(const tracker* t) { return column_available(t) ? kDirectDensity : 0.25; }
+
 // Densities (particles per cell) between which AUTO times the column and the
 // direct kernel on the first tracker_advance call of a (np, scheme) and keeps
 // the faster: the crossover moves with the grid (L2 holds a 256^3 float32
@@ -468,7 +482,7 @@ constexpr int kProbeSteps = 4;   // two timed steps per kernel (the first launch
 int step_path(const tracker* t, int64_t np)
 {
     if (t->step_kernel != TRK_STEP_AUTO) return t->step_kernel;
-    if ((double)np < kDirectDensity * (double)t->N * t->N * t->N) return TRK_STEP_DIRECT;
+    if ((double)np < direct_threshold(t) * (double)t->N * t->N * t->N) return TRK_STEP_DIRECT;
     return column_available(t) ? TRK_STEP_COLUMN : TRK_STEP_BLOCK;
 }
 
@@ -1086,8 +1100,8 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
     if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
     int rc = check_block_kernel_shape(t);
     if (rc) return rc;
-    // the direct items of float32 sets read the node-major copy of the field
-    if (t->storage == TRK_F32 && nsets > 0 && steps > 0 && (rc = ensure_node_major(t))) return rc;
+    // the direct items of the sets read the node-major copy of the field
+    if (nsets > 0 && steps > 0 && (rc = ensure_node_major(t))) return rc;
     std::vector<int> tabs(nsets);
     int64_t npmax = 0;
     for (int s = 0; s < nsets; ++s) {

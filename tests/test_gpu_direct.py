@@ -5,7 +5,8 @@ Per particle it performs the same floating-point operations in the same order
 as the block kernel, so positions, AB histories and interpolated values must
 agree bit for bit; at the paper's sparse density (about 1.5e-3 tracers per
 grid cell) it is also checked against the oracle.  The automatic choice picks
-it below 0.05 particles per cell.
+it below 0.05 particles per cell where a column kernel exists (and times the
+two between 0.01 and 0.25), else below 0.25.
 """
 import math
 
@@ -174,8 +175,17 @@ def test_automatic_choice():
     assert t32.step_kernel_for(0) == trk.TRK_STEP_DIRECT
     assert t32.step_kernel_for(thr - 1) == trk.TRK_STEP_DIRECT
     assert t32.step_kernel_for(thr + 1) == trk.TRK_STEP_COLUMN
+    # without a column kernel: block vs direct by a threshold per storage
     t64 = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F64)
-    assert t64.step_kernel_for(thr + 1) == trk.TRK_STEP_BLOCK
+    assert t64.step_kernel_for(thr + 1) == trk.TRK_STEP_DIRECT
+    assert t64.step_kernel_for(N ** 3 // 4 - 1) == trk.TRK_STEP_DIRECT
+    assert t64.step_kernel_for(N ** 3 // 4 + 1) == trk.TRK_STEP_BLOCK
+    t8 = trk.Tracker(N, family=trk.TRK_SPLINE, I=8, m=3, storage=trk.TRK_F32)
+    assert t8.step_kernel_for(N ** 3 // 4 + 1) == trk.TRK_STEP_BLOCK
+    assert t8.step_kernel_for(N ** 3 // 8) == trk.TRK_STEP_DIRECT
+    tb = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_BF16X2)
+    assert tb.step_kernel_for(N ** 3 // 8) == trk.TRK_STEP_DIRECT
+    assert tb.step_kernel_for(N ** 3 // 4 + 1) == trk.TRK_STEP_BLOCK
     t64.set_step_kernel(trk.TRK_STEP_DIRECT)
     assert t64.step_kernel_for(10 ** 9) == trk.TRK_STEP_DIRECT
     t32.set_step_kernel(trk.TRK_STEP_BLOCK)
@@ -185,16 +195,18 @@ def test_automatic_choice():
     del f
 
 
-def test_direct_sees_a_replaced_field():
-    """The direct path of a float32 tracker reads a node-major copy of the field:
-    after set_field it must gather the new values (interpolation and steps)."""
+@pytest.mark.parametrize("storage", [trk.TRK_F32, trk.TRK_BF16X2])
+def test_direct_sees_a_replaced_field(storage):
+    """The direct path of a float32 or split-bf16 tracker reads a node-major copy
+    of the field: after set_field it must gather the new values (interpolation
+    and steps)."""
     N, n = 32, 500
     fa = synth.velocity_field_np(N, 10, 410).astype(np.float32)
     fb = synth.velocity_field_np(N, 10, 411).astype(np.float32)
     pos = synth.uniform_particles_np(n, 25)
-    td = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    td = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=storage)
     td.set_step_kernel(trk.TRK_STEP_DIRECT)
-    tb = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    tb = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=storage)
     tb.set_step_kernel(trk.TRK_STEP_BLOCK)
     x = torch.from_numpy(pos).to(DEV)
     for f in (fa, fb, fa):
