@@ -179,17 +179,22 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(sha, kind="column"):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it matches the source."""
+def ncu_record(sha, kind="column"):
+    """The committed ncu summary of the step kernel (profiles/traffic.json), if it matches the source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None
+        return {}
     with open(p) as fh:
         d = json.load(fh)
     e = d.get(STEP_KERNELS[kind][1])
     if not e or e.get("source_sha") != sha:
-        return None
-    return e.get("dram_bytes_per_launch")
+        return {}
+    return e
+
+
+def ncu_traffic(sha, kind="column"):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it matches the source."""
+    return ncu_record(sha, kind).get("dram_bytes_per_launch")
 
 
 def sync_flags(tr, trk, notes):
@@ -440,6 +445,7 @@ def run_gb300(args):
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": ncu_traffic(sha, kind), "kernel": STEP_KERNELS[kind][0],
+                         "l2_hit_rate": ncu_record(sha, kind).get("l2_hit_rate"),
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                          "launches_timed": step_n, "peak_kind": peak_kind, "source_sha": sha},
             "fma_roofline": {"achieved": NP * fma_per_ps * 2 / avg_launch_s / 1e12, "peak": fp32_peak,
@@ -716,32 +722,34 @@ def run_config6(args):
     alg = ns * (2 * I ** 3 * 3 * 4 + 52)
     peak, peak_kind = measured_peaks()
     achieved = alg / launch_s / 1e9
-    per_particle = sparse_traffic_per_particle(kind)
+    rec = sparse_ncu_record(kind)
+    per_particle = rec.get("dram_bytes_per_particle")
     _line("particle-steps/s", ns / (ms * 1e-3), "particle-steps/s", args, ms * inner,
           f"{Ns}^3 fp32 velocity |k|<={Ns // 3}, {ns} uniform tracers (1.5e-3 per cell, the paper's density), "
           f"spline I={I} m={M}, {inner} RK2 steps dt={dt} per call, re-binned every step",
           {"roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": per_particle * ns if per_particle else None, "kernel": kind,
+                        "l2_hit_rate": rec.get("l2_hit_rate"),
                         "alg_bytes_per_launch": alg, "avg_launch_ms": launch_s * 1e3, "peak_kind": peak_kind,
                         "alg_def": "2 stencils x I^3 x 3 x 4 B + 52 B state per particle-step"},
            "phase_ms_per_step": {"step_kernel": step_ms / inner, "binning": prof["bin"][0] / inner},
            "gpu_launches": launches, "notes": notes})
 
 
-def sparse_traffic_per_particle(kind):
-    """DRAM bytes per particle of the sparse direct step kernel from the committed
-    ncu summary (captured on a smaller grid at the same density; the traffic of
-    this kernel grows with the particle count), if it matches the source."""
+def sparse_ncu_record(kind):
+    """The committed ncu summary of the sparse direct step kernel (captured on a
+    smaller grid at the same density; the traffic of this kernel grows with the
+    particle count), if it matches the source."""
     if kind != "direct":
-        return None
+        return {}
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None
+        return {}
     with open(p) as fh:
         e = json.load(fh).get("k_direct_rk2_f32_i6_sparse")
     if not e or e.get("source_sha") != kernel_source_sha("direct"):
-        return None
-    return e.get("dram_bytes_per_particle")
+        return {}
+    return e
 
 
 def run_config5(args):
