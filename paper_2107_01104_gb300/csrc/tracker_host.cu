@@ -470,6 +470,15 @@ constexpr double kDirectDensity = 0.05;
 // split-bf16 (node-major copy) 1.19 vs 0.59 and 2.45 vs 2.20.
 double direct_threshold(const tracker* t) { return column_available(t) ? kDirectDensity : 0.25; }
 
+// Remembers a timing decision; the oldest is dropped beyond kCacheMax entries
+// (a caller whose particle counts keep changing re-times now and then).
+constexpr size_t kCacheMax = 256;
+void remember(std::vector<std::pair<uint64_t, int>>& cache, uint64_t sig, int choice)
+{
+    if (cache.size() >= kCacheMax) cache.erase(cache.begin());
+    cache.emplace_back(sig, choice);
+}
+
 // Densities (particles per cell) between which AUTO times the column and the
 // direct kernel on the first tracker_advance call of a (np, scheme) and keeps
 // the faster: the crossover moves with the grid (L2 holds a 256^3 float32
@@ -894,7 +903,7 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
         if (rc) return rc;
-        t->interp_cache.emplace_back(sig, td < tb ? TRK_STEP_DIRECT : TRK_STEP_BLOCK);
+        remember(t->interp_cache, sig, td < tb ? TRK_STEP_DIRECT : TRK_STEP_BLOCK);
         t->last_kernel = td < tb ? TRK_STEP_DIRECT : TRK_STEP_BLOCK;
         return TRK_OK;
     }
@@ -1001,7 +1010,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
             dir = std::min(dir, ms[kProbeSteps / 2 + i]);
         }
         path = dir < col ? TRK_STEP_DIRECT : TRK_STEP_COLUMN;
-        t->path_cache.emplace_back(sig, path);
+        remember(t->path_cache, sig, path);
     }
     for (; rest > 0 && k && hist < k - 1;)
         if ((rc = eager(path))) return rc;
@@ -1238,7 +1247,7 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             choice = best[1] < best[0] ? 1 : 0;
-            t->tune_cache.emplace_back(sig, choice);
+            remember(t->tune_cache, sig, choice);
         }
         direct[s] = choice;
         for (int v = 0; v < 3; ++v) h[(size_t)v * nsets + s].direct = choice;
