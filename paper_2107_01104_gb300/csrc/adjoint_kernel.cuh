@@ -98,8 +98,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
     Lane<T, I, true> L;
     L.init(lane);
 
+    constexpr bool ASYNC = STORE != ST_BF16X2;
     for (int batch = j0; batch < j1; batch += PBA) {
         const int nbat = min(PBA, j1 - batch);
+        // the first batch's halo copies run while P1 splits (later batches re-use the
+        // halo buffer as the previous batch's accumulator until it is flushed)
+        if (ASYNC && batch == j0) stage_halo<T, STORE, H, G, S2, S3, SC, 3, false>(halo, a.f, 0, 3, o1, o2, o3);
         // ---------------- P1 ----------------
         double lam[3] = {0, 0, 0};
         int id = 0;
@@ -125,7 +129,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             p_cell[tid] = pack_cell(c[0], c[1], c[2]);
         }
         if (batch != j0) __syncthreads();   // the accumulator of the previous batch is flushed
-        stage_halo<T, STORE, H, G, S2, S3, SC, 3, true>(halo, a.f, 0, 3, o1, o2, o3);
+        if (!ASYNC || batch != j0) stage_halo<T, STORE, H, G, S2, S3, SC, 3, true>(halo, a.f, 0, 3, o1, o2, o3);
+        else cp_async_wait_all();
         __syncthreads();
         // ---------------- Q1: u(X), J(X), J(X*) ----------------
         for (int q = warp; q < nbat; q += NW) {
@@ -304,31 +309,56 @@ template <typename T, int H>
 __global__ void k_adj_gather(const __grid_constant__ AdjArgs a)
 {
     constexpr int G = (H - BLK - 1) / 2;                     // I / 2 for H = BLK + I + 1
+    constexpr int H3 = H * H * H;
     const int N = a.g.N;
     const int64_t NN3 = (int64_t)N * N * N;
     const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= NN3) return;
-    const int x1 = (int)(node % N), x2 = (int)((node / N) % N), x3 = (int)(node / ((int64_t)N * N));
-    auto fdiv = [](int p, int q) { return p >= 0 ? p / q : -((-p + q - 1) / q); };   // floor
-    auto cdiv = [&](int p, int q) { return -fdiv(-p, q); };                           // ceiling
-    auto pmod = [](int p, int q) { return ((p % q) + q) % q; };
-    double s0 = 0, s1 = 0, s2 = 0;
-    constexpr int H3 = H * H * H;
-    for (int bzi = cdiv(x3 + G - H + 1, BLK); bzi <= fdiv(x3 + G, BLK); ++bzi) {
-        const int hz = x3 + G - BLK * bzi, bz = pmod(bzi, a.g.nb3);
-        for (int byi = cdiv(x2 + G - H + 1, BLK); byi <= fdiv(x2 + G, BLK); ++byi) {
-            const int hy = x2 + G - BLK * byi, by = pmod(byi, a.g.nb2);
-            for (int bxi = cdiv(x1 + G - H + 1, BLK); bxi <= fdiv(x1 + G, BLK); ++bxi) {
-                const int hx = x1 + G - BLK * bxi, bx = pmod(bxi, a.g.nb1);
-                const int64_t b = ((int64_t)bz * a.g.nb2 + by) * a.g.nb1 + bx;
-                if (a.offsets[b + 1] == a.offsets[b]) continue;      // empty block: no partials
-                const T* sb = reinterpret_cast<const T*>(a.gscratch) + b * 3 * H3 + (hz * H + hy) * H + hx;
-                s0 += (double)sb[0];
-                s1 += (double)sb[H3];
-                s2 += (double)sb[2 * H3];
+    const int lg = __ffs(N) - 1;                              // log2 N (N a power of two)
+    const int x1 = (int)(node & (N - 1)), x2 = (int)((node >> lg) & (N - 1)), x3 = (int)(node >> (2 * lg));
+    // per axis: the blocks bi whose halo [BLK bi - G, BLK bi - G + H) holds x, i.e.
+    // bi in [ceil((x + G - H + 1) / BLK), floor((x + G) / BLK)]; arithmetic shifts floor for negatives
+    auto range = [&](int x, int& lo, int& hi) {
+        hi = (x + G) >> LBLK;
+        lo = -((-(x + G - H + 1)) >> LBLK);                   // ceiling of (x + G - H + 1) / BLK
+    };
+    int z0, z1, y0, y1, w0, w1;
+    range(x3, z0, z1);
+    range(x2, y0, y1);
+    range(x1, w0, w1);
+    const int m3 = a.g.nb3 - 1, m2 = a.g.nb2 - 1, m1 = a.g.nb1 - 1;   // block counts are powers of two
+    // fixed trip counts (at most H / BLK + 1 blocks per axis) with predicates, so
+    // that every emptiness check, then every partial read, is issued at once
+    constexpr int NA = H / BLK + 1;
+    int64_t bidx[NA * NA * NA];
+    int hoff[NA * NA * NA];
+    bool use[NA * NA * NA];
+#pragma unroll
+    for (int iz = 0; iz < NA; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < NA; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < NA; ++ix) {
+                const int c = (iz * NA + iy) * NA + ix;
+                const int bzi = z0 + iz, byi = y0 + iy, bxi = w0 + ix;
+                const int hz = x3 + G - BLK * bzi, hy = x2 + G - BLK * byi, hx = x1 + G - BLK * bxi;
+                bidx[c] = ((int64_t)(bzi & m3) * a.g.nb2 + (byi & m2)) * a.g.nb1 + (bxi & m1);
+                hoff[c] = (hz * H + hy) * H + hx;
+                use[c] = bzi <= z1 && byi <= y1 && bxi <= w1;
             }
+#pragma unroll
+    for (int c = 0; c < NA * NA * NA; ++c)
+        if (use[c]) use[c] = a.offsets[bidx[c] + 1] != a.offsets[bidx[c]];   // empty block: no partials
+    double s0 = 0, s1 = 0, s2 = 0;
+    const T* gs = reinterpret_cast<const T*>(a.gscratch);
+#pragma unroll
+    for (int c = 0; c < NA * NA * NA; ++c)
+        if (use[c]) {
+            const T* sb = gs + bidx[c] * 3 * H3 + hoff[c];
+            s0 += (double)sb[0];
+            s1 += (double)sb[H3];
+            s2 += (double)sb[2 * H3];
         }
-    }
     a.gfield[node] += s0;
     a.gfield[NN3 + node] += s1;
     a.gfield[2 * NN3 + node] += s2;

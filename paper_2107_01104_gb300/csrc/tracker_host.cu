@@ -1394,7 +1394,7 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
             a.flags = t->d_flags;
             CUDA_TRY(launch_adjoint(t, a));
             if (a.gscratch) {
-                ProfScope ps(t, PROF_STEP);
+                ProfScope ps(t, PROF_OTHER);   // the node gather of the field gradient
                 t->launches += 1;
                 CUDA_TRY(launch_adjoint_gather(t->I, a, t->stream));
             }
