@@ -119,6 +119,13 @@ __global__ void __launch_bounds__(CS_THREADS) k_count_scan(uint32_t* __restrict_
 // of the preceding tiles and scans its own tile, CT_PER counts per thread
 // read and written as 16-byte vectors.
 constexpr int CT_THREADS = 256, CT_PER = 16, CT_TILE = CT_THREADS * CT_PER;
+// Largest grid one CTA scans.  At 2^15 blocks (256^3 in 8^3 blocks) the two
+// launches over all SMs already win: 9.5 us less per step of the 256^3
+// headline workload on GB300 (0.5454 -> 0.5359 ms).
+#ifndef TRK_SCAN_ONE_CTA
+#define TRK_SCAN_ONE_CTA 16384
+#endif
+constexpr int64_t COUNT_SCAN_ONE_CTA = TRK_SCAN_ONE_CTA;
 
 __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t* red)
 {

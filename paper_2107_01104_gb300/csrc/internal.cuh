@@ -266,9 +266,8 @@ cudaError_t launch_column_i6(int mode, const ColumnArgs& ca, int deg_hi, int nsm
 // offsets + cursors (counts zeroed); scatter of the state into its blocks
 cudaError_t launch_keys_count(const GridGeom& g, int64_t np, const double* pos, uint32_t* keys, uint32_t* counts,
                               int* flags, cudaStream_t st);
-// Up to COUNT_SCAN_ONE_CTA blocks one CTA scans (one launch); larger grids
-// take two launches over all SMs with count_scan_scratch_bytes of scratch.
-constexpr int64_t COUNT_SCAN_ONE_CTA = 65536;
+// Small grids are scanned by one CTA (one launch); larger grids take two
+// launches over all SMs with count_scan_scratch_bytes of scratch.
 size_t count_scan_scratch_bytes(int64_t nblocks);
 cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor,
                               uint32_t* scratch, cudaStream_t st, int64_t* launches);
