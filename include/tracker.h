@@ -7,7 +7,8 @@
  * dX/dt = u(X) (Eq. tracers) in a frozen periodic field on [0, L)^3 sampled on
  * an N^3 grid (Sec. 2.1), interpolated with separable kernels of I nodes per
  * axis (Sec. 2.2, Eq. triple_sum), particles kept grouped by cell block with
- * an offset array (Sec. 3.3.1), advanced by RK2 (Heun) or AB2.
+ * an offset array (Sec. 3.3.1), advanced by RK2 (Heun) or Adams-Bashforth
+ * (orders 2-4).
  *
  * Conventions shared by every entry point
  * ---------------------------------------

@@ -11,14 +11,14 @@
 //
 //   P1  one thread per particle: read X through the sort permutation, split it
 //       into cell c and offset t (float64, Sec. 2.2 steps 1-3), keep X, the
-//       caller id and the AB2 history in shared memory for P3;
+//       caller id and the AB history in shared memory for P3;
 //   Q   one warp per particle: evaluate the 1-D weights beta_i per axis, gather
 //       the I x I x I stencil from shared memory into registers and contract it
 //       (Eq. triple_sum, separably as in Sec. 3.3), reduce across the warp.
 //       For RK2 the warp then forms the stage-2 point in cell-relative
 //       coordinates, t* = t + dt u(X) / delta, and contracts again, re-using
 //       the stencil registers when X* lies in the same cell;
-//   P3  one thread per particle: float64 position update (RK2 or AB2) from the
+//   P3  one thread per particle: float64 position update (RK2 or AB) from the
 //       staged X, new cell split and block key for the next re-binning,
 //       coalesced write-out.
 //

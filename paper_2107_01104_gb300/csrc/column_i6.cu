@@ -1,4 +1,4 @@
-// Column step kernels for kernel width I = 6 (float32 fields, RK2 and AB2).
+// Column step kernels for kernel width I = 6 (float32 fields, RK2 and Adams-Bashforth).
 #include "column_kernel.cuh"
 
 namespace trk {

@@ -68,7 +68,7 @@ struct GridGeom {
     double inv_delta;         // fl(N / L)
 };
 
-// Arguments of the block kernels (interpolation, RK2 step, AB2 step).
+// Arguments of the block and direct kernels (interpolation, RK2 step, AB step).
 struct BlockArgs {
     GridGeom g;
     FieldView f;
@@ -145,7 +145,7 @@ struct BatchSet {
     int I, deg_hi, deriv, direct;
 };
 
-// Arguments of the column step kernel (RK2 / AB2 over column segments of cell
+// Arguments of the column step kernel (RK2 / AB over column segments of cell
 // blocks, float32 fields, I = 4 or 6).  The state arrays a.pos_out / a.rhs_out
 // hold the particles grouped by block and are updated in place; a.perm and
 // a.id_* are unused (the scatter kernel has grouped the state).

@@ -457,9 +457,9 @@ int ensure_node_major(tracker* t)
 
 // Below this many particles per grid cell the automatic choice gathers every
 // stencil straight from global memory (direct path) instead of sweeping the
-// field.  Measured crossover on GB300 (float32 field, spline I = 6): RK2 steps
-// at 256^3 take 0.533 (column) vs 0.477 ms (direct) at 1/24 per cell and
-// 0.652 vs 0.693 ms at 1/16; AB2 steps favour the direct path down to 1/16.
+// field, without timing: on GB300 (float32, spline I = 6) the direct step wins
+// there for RK2 and AB on every grid measured (256^3: RK2 0.381 vs 0.534 ms at
+// 1/24 per cell, AB2 0.287 vs 0.328 ms).  Above it the kernels are timed.
 constexpr double kDirectDensity = 0.05;
 
 // Without a column kernel (float64 or split-bf16 storage, I = 8, other block
