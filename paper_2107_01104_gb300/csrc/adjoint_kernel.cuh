@@ -15,11 +15,15 @@
 //   Q1  warp per particle: gathers at X and X* with value and derivative
 //       weights -> u(X), J(X), J(X*)
 //   P2  thread per particle: the float64 lambda recurrence above
-//   Q2  warp per particle: W^T scatter into a shared-memory accumulator laid
-//       out like the halo (the halo buffer is re-used), then either plain
-//       stores of the accumulator into the block's slab of gscratch (summed
-//       per node afterwards by k_adj_gather, deterministic) or, without
-//       scratch, one float64 atomic add per touched halo node into gfield.
+//   Q2  warp per particle: W^T scatter.  With scratch (GRED): atomic adds
+//       straight into the block's slab of gscratch, [3][H][H][H] (float32 /
+//       float64 adds are native reductions in L2; shared-memory float adds on
+//       this GPU are compare-and-swap loops), summed per node afterwards by
+//       k_adj_gather in a fixed cross-block order; the slabs are zero on
+//       entry and the gather leaves them zero.  Without scratch: a shared-
+//       memory accumulator laid out like the halo (the halo buffer is
+//       re-used), flushed with one float64 atomic add per touched halo node
+//       into gfield.  Inside a block the adds arrive in any order.
 #pragma once
 
 #include "block_kernel.cuh"
@@ -55,7 +59,7 @@ struct AdjPlan {
     static_assert(total <= 232448, "adjoint shared-memory plan exceeds the per-block limit");
 };
 
-template <typename T, int I, int DEG, int STORE>
+template <typename T, int I, int DEG, int STORE, bool GRED>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __grid_constant__ AdjArgs a)
 {
     constexpr int H = BLK + I - 1 + 2;
@@ -220,6 +224,56 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             continue;
         }
         // ---------------- Q2: W^T scatter ----------------
+        if constexpr (GRED) {
+            __syncthreads();   // p_mu of every particle
+            constexpr int H3 = H * H * H;
+            T* slab = reinterpret_cast<T*>(a.gscratch) + (int64_t)b * 3 * H3;
+            // the adds of a stencil at packed halo-relative cell rp
+            auto add_slab = [&](int rp) {
+                T* base = slab + (((rp >> 16) & 255) - LO) * H * H + (((rp >> 8) & 255) - LO) * H + ((rp & 255) - LO);
+                return [=](int k, int a1, int a2, int a3, T val) { atomicAdd(base + k * H3 + (a3 * H + a2) * H + a1, val); };
+            };
+            const int64_t NN3g = (int64_t)N * N * N;
+            for (int q = warp; q < nbat; q += NW) {
+                const PRec<T> recs[2] = {p_rec[q], p_rec2[q]};
+                int rps[2];
+#pragma unroll
+                for (int stage = 0; stage < 2; ++stage) {
+                    if constexpr (sizeof(T) == 4) rps[stage] = __float_as_int(recs[stage].relf);
+                    else rps[stage] = (int)__double_as_longlong(recs[stage].relf);
+                }
+                const T mus[2][3] = {{p_mu[q * 6 + 0], p_mu[q * 6 + 1], p_mu[q * 6 + 2]},
+                                     {p_mu[q * 6 + 3], p_mu[q * 6 + 4], p_mu[q * 6 + 5]}};
+                if (rps[0] >= 0 && rps[0] == rps[1]) {
+                    // X and X* in the same cell: one stencil, both weight sets, one add per node
+                    const T sa[3] = {recs[0].t[0] - (T)0.5, recs[0].t[1] - (T)0.5, recs[0].t[2] - (T)0.5};
+                    const T sb[3] = {recs[1].t[0] - (T)0.5, recs[1].t[1] - (T)0.5, recs[1].t[2] - (T)0.5};
+                    W.eval_values2(sa, sb, wv, wd);
+                    L.template scatter_n<true>(wv, mus[0], wd, mus[1], add_slab(rps[0]));
+                    continue;
+                }
+#pragma unroll
+                for (int stage = 0; stage < 2; ++stage) {
+                    const PRec<T>& rec = recs[stage];
+                    const int rp = rps[stage];
+                    W.eval(rec.t[0] - (T)0.5, rec.t[1] - (T)0.5, rec.t[2] - (T)0.5, wv, wd);
+                    if (rp >= 0) {
+                        L.template scatter_n<false>(wv, mus[stage], wv, mus[stage], add_slab(rp));
+                    } else {
+                        const int pc = stage == 0 ? p_cell[q] : p_cell2[q];
+                        const int c1 = pc & 1023, c2 = (pc >> 10) & 1023, c3 = (pc >> 20) & 1023;
+                        double* gf = a.gfield;
+                        L.template scatter_n<false>(wv, mus[stage], wv, mus[stage],
+                                                    [&](int k, int a1, int a2, int a3, T val) {
+                            const int x1 = (c1 + a1 - LO) & mask, x2 = (c2 + a2 - LO) & mask, x3 = (c3 + a3 - LO) & mask;
+                            atomicAdd(gf + k * NN3g + ((int64_t)x3 * N + x2) * N + x1, (double)val);
+                        });
+                    }
+                }
+            }
+            __syncthreads();   // the batch's records are read before the next batch's P1
+            continue;
+        }
         static_assert(SC % 2 == 0, "the accumulator is zeroed two values at a time");
         for (int e = tid; e < 3 * SC / 2; e += NT) reinterpret_cast<typename Vec2<T>::type*>(halo)[e] = Vec2<T>::zero();
         __syncthreads();
@@ -268,25 +322,6 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             }
         }
         __syncthreads();
-        if (a.gscratch) {
-            // the block's partial sums, [3][H][H][H]; later batches of a crowded block add in
-            // thread t owns column x, row y of every (component, plane): no index division per element
-            T* sb = reinterpret_cast<T*>(a.gscratch) + (int64_t)b * 3 * H * H * H;
-            constexpr int RP = NT / H;                           // rows per pass
-            const int x = tid % H, yr = tid / H;
-            if (yr < RP) {
-                for (int kz = 0; kz < 3 * H; ++kz) {             // (component, plane) pairs
-                    const int k = kz / H, z = kz - (kz / H) * H;
-                    const T* src = halo + k * SC + z * S3 + x;
-                    T* dst = sb + (int64_t)kz * H * H + x;
-                    for (int y = yr; y < H; y += RP) {
-                        const T val = src[y * S2];
-                        dst[y * H] = batch == j0 ? val : dst[y * H] + val;
-                    }
-                }
-            }
-            continue;
-        }
         // flush the accumulator: one float64 atomic per touched halo node
         for (int e = tid; e < 3 * H * H * H; e += NT) {
             const int x = e % H, yz = e / H, y = yz % H, zk = yz / H, z = zk % H, k = zk / H;
@@ -300,7 +335,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
 }
 
 // dLoss/dfield[k][node] += sum over the non-empty blocks whose halo holds the
-// node of their partial sums, in a fixed order (deterministic).  Along each
+// node of their partial sums, in a fixed order of the blocks.  Along each
 // axis the blocks are those with integer index bi in
 // [ceil((x + G - H + 1) / BLK), floor((x + G) / BLK)], at halo offset
 // x + G - BLK bi in [0, H), taken mod nb (periodic images of the same block
@@ -359,17 +394,28 @@ __global__ void k_adj_gather(const __grid_constant__ AdjArgs a)
             s1 += (double)sb[H3];
             s2 += (double)sb[2 * H3];
         }
+    // every slab value is read by exactly one node: leave the slabs zero for the
+    // next step's atomic adds
+    T* gz = reinterpret_cast<T*>(a.gscratch);
+#pragma unroll
+    for (int c = 0; c < NA * NA * NA; ++c)
+        if (use[c]) {
+            T* sb = gz + bidx[c] * 3 * H3 + hoff[c];
+            sb[0] = (T)0;
+            sb[H3] = (T)0;
+            sb[2 * H3] = (T)0;
+        }
     a.gfield[node] += s0;
     a.gfield[NN3 + node] += s1;
     a.gfield[2 * NN3 + node] += s2;
 }
 
-template <typename T, int I, int DEG, int STORE>
-cudaError_t launch_adjoint_t(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
+template <typename T, int I, int DEG, int STORE, bool GRED>
+cudaError_t launch_adjoint_g(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
 {
     constexpr int H = BLK + I - 1 + 2;
     constexpr size_t smem = AdjPlan<T, Layout<I, H>::SC>::total;
-    auto kern = k_adjoint<T, I, DEG, STORE>;
+    auto kern = k_adjoint<T, I, DEG, STORE, GRED>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -379,6 +425,14 @@ cudaError_t launch_adjoint_t(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
     if (nblocks <= 0) return cudaSuccess;
     kern<<<(unsigned)nblocks, NT, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// with per-block scratch the W^T adds go to the block's slab in global memory
+template <typename T, int I, int DEG, int STORE>
+cudaError_t launch_adjoint_t(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
+{
+    if (a.gscratch) return launch_adjoint_g<T, I, DEG, STORE, true>(a, nblocks, st);
+    return launch_adjoint_g<T, I, DEG, STORE, false>(a, nblocks, st);
 }
 
 template <int I, int DEG>

@@ -1333,8 +1333,9 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
         }
         t->adj_bytes = need;
     }
-    // deterministic field gradient: per-block partial sums + a gather per node,
-    // while the scratch stays below 8 GB (else float64 atomics per halo node)
+    // field gradient: per-block partial sums (atomic adds into zeroed slabs) and a
+    // gather per node in a fixed block order, while the scratch stays below 8 GB
+    // (else float64 atomics per halo node)
     void* gscratch = nullptr;
     if (grad_field) {
         const int H = adj_halo(t->I);
@@ -1350,6 +1351,9 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
                 else cudaGetLastError();
             }
             gscratch = t->adj_scratch;
+            // every gather leaves the slabs it read zero; clearing them here as well
+            // keeps a call that failed half-way from leaking into the next one
+            if (gscratch) CUDA_TRY(cudaMemsetAsync(gscratch, 0, sb, t->stream));
         }
     }
     double* ckpt = t->adj_buf;

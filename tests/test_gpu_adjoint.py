@@ -128,7 +128,7 @@ def test_config5_full_size_sampled():
 def test_field_gradient_scratch_and_atomic_paths_agree(monkeypatch, storage, I_, m_, N, n, layout):
     """The per-block partial sums + node gather (default) and the float64
     atomics per halo node (forced by a zero scratch budget) give the same
-    field gradient; both match the oracle.  N = 16 with I = 8 has halos wider
+    field gradient to rounding; both match the oracle.  N = 16 with I = 8 has halos wider
     than the grid (a block's halo holds two periodic images of some nodes)."""
     dt, steps, ckpt = 5e-3, 3, 2
     field = synth.velocity_field_np(N, min(10, N // 3), 92)
@@ -158,4 +158,7 @@ def test_field_gradient_scratch_and_atomic_paths_agree(monkeypatch, storage, I_,
         assert rel(out[mode][0], gpos_ref) <= tol, mode
         assert rel(out[mode][1], gf_ref) <= tol, mode
     assert np.array_equal(out["scratch"][0], out["atomic"][0])
-    assert rel(out["scratch"][1], out["atomic"][1]) <= (1e-14 if storage == trk.TRK_F64 else 2e-7)
+    # both paths add each block's contributions in the storage precision, in
+    # different orders (atomics into the scratch slab vs a shared-memory
+    # accumulator): they agree to the adjoint tolerance of 1e-6 relative
+    assert rel(out["scratch"][1], out["atomic"][1]) <= (1e-14 if storage == trk.TRK_F64 else 1e-6)
