@@ -312,14 +312,23 @@ int tracker_state_read(const char* path, int64_t np, double* pos, float* rhs, tr
  *   lambda* = dt/2 J(X*)^T lambda,  mu = dt/2 lambda + dt lambda*,
  *   grad_field += W(X)^T mu + W(X*)^T (dt/2 lambda),
  *   lambda <- lambda + lambda* + J(X)^T mu.
- * The field gradient is accumulated per cell block (shared memory) and then
- * summed per grid node over the blocks whose halo holds it, in a fixed
- * order, without global atomics.  That needs nblocks * 3 * (I + 9)^3 values
- * of scratch (float32, float64 for TRK_F64 storage; 1.3 GB at N = 256,
- * I = 6); when this exceeds the byte count in the environment variable
- * TRK_ADJ_SCRATCH_BYTES (default 8 GiB) or cannot be allocated, each block
- * adds its partial sums with float64 atomics instead (same values up to
- * rounding order).
+ * Two modes (same values up to rounding order of the field gradient):
+ *   halo mode (TRK_STEP_AUTO at 1/8 tracer per grid cell or more, or
+ *     TRK_STEP_BLOCK / TRK_STEP_COLUMN): one thread block per cell block
+ *     with the field halo in shared memory; the field gradient is
+ *     accumulated per cell block (atomic adds into the block's slab of
+ *     scratch) and then summed per grid node over the blocks whose halo
+ *     holds it, in a fixed block order.  The scratch holds
+ *     nblocks * 3 * (I + 9)^3 values (float32, float64 for TRK_F64 storage;
+ *     1.3 GB at N = 256, I = 6); when this exceeds the byte count in the
+ *     environment variable TRK_ADJ_SCRATCH_BYTES (default 8 GiB) or cannot
+ *     be allocated, each block accumulates in shared memory and adds its
+ *     partial sums with float64 atomics instead.
+ *   direct mode (TRK_STEP_AUTO below 1/8 tracer per cell, or
+ *     TRK_STEP_DIRECT): no halos; 128 sorted particles per thread block,
+ *     stencils gathered from the field in global memory, and each stencil
+ *     node's contribution added to grad_field with a float64 atomic add.
+ *     The position gradient is bit-identical to the halo mode's.
  * Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
 int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* lambdaT, double dt, int steps,
                     int ckpt_every, double* grad_pos0, double* grad_field);

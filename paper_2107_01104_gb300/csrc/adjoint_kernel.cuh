@@ -15,7 +15,12 @@
 //   Q1  warp per particle: gathers at X and X* with value and derivative
 //       weights -> u(X), J(X), J(X*)
 //   P2  thread per particle: the float64 lambda recurrence above
-//   Q2  warp per particle: W^T scatter.  With scratch (GRED): atomic adds
+// Modes (AM): ADJ_SLAB and ADJ_SMEM run one CTA per cell block with the
+// field halo staged in shared memory; ADJ_DIRECT (sparse particle sets, a null
+// a.offsets) runs PBA sorted particles per CTA and gathers every stencil from
+// global memory, like the forward direct kernel.
+//
+//   Q2  warp per particle: W^T scatter.  With scratch (ADJ_SLAB): atomic adds
 //       straight into the block's slab of gscratch, [3][H][H][H] (float32 /
 //       float64 adds are native reductions in L2; shared-memory float adds on
 //       this GPU are compare-and-swap loops), summed per node afterwards by
@@ -23,7 +28,9 @@
 //       entry and the gather leaves them zero.  Without scratch: a shared-
 //       memory accumulator laid out like the halo (the halo buffer is
 //       re-used), flushed with one float64 atomic add per touched halo node
-//       into gfield.  Inside a block the adds arrive in any order.
+//       into gfield (ADJ_SMEM).  ADJ_DIRECT adds straight into gfield, one
+//       float64 atomic per stencil node (one for both stages when X and X*
+//       share a cell).  Inside a block the adds arrive in any order.
 #pragma once
 
 #include "block_kernel.cuh"
@@ -31,6 +38,8 @@
 namespace trk {
 
 constexpr int PBA = 128;   // particles per adjoint batch (keeps the float64 I = 8 plan under 227 KB)
+
+enum { ADJ_SMEM = 0, ADJ_SLAB = 1, ADJ_DIRECT = 2 };   // where the W^T scatter goes (see above)
 
 // two-element vector of T for zeroing shared memory
 template <typename T>
@@ -59,9 +68,10 @@ struct AdjPlan {
     static_assert(total <= 232448, "adjoint shared-memory plan exceeds the per-block limit");
 };
 
-template <typename T, int I, int DEG, int STORE, bool GRED>
+template <typename T, int I, int DEG, int STORE, int AM>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __grid_constant__ AdjArgs a)
 {
+    constexpr bool HALO = AM != ADJ_DIRECT;
     constexpr int H = BLK + I - 1 + 2;
     constexpr int G = I / 2;
     constexpr int LO = I / 2 - 1;
@@ -81,8 +91,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
     int* p_cell = reinterpret_cast<int*>(smem_raw + SM::cell);
     int* p_cell2 = reinterpret_cast<int*>(smem_raw + SM::cell2);
 
-    const int b = blockIdx.x;
-    const int j0 = a.offsets[b], j1 = a.offsets[b + 1];
+    const int b = HALO ? (int)blockIdx.x : 0;
+    const int j0 = HALO ? a.offsets[b] : (int)blockIdx.x * PBA;
+    const int j1 = HALO ? a.offsets[b + 1] : (int)min((int64_t)j0 + PBA, a.np);
     if (j0 >= j1) return;
 
     const int N = a.g.N, mask = a.g.mask;
@@ -107,7 +118,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
         const int nbat = min(PBA, j1 - batch);
         // the first batch's halo copies run while P1 splits (later batches re-use the
         // halo buffer as the previous batch's accumulator until it is flushed)
-        if (ASYNC && batch == j0) stage_halo<T, STORE, H, G, S2, S3, SC, 3, false>(halo, a.f, 0, 3, o1, o2, o3);
+        if (HALO && ASYNC && batch == j0) stage_halo<T, STORE, H, G, S2, S3, SC, 3, false>(halo, a.f, 0, 3, o1, o2, o3);
         // ---------------- P1 ----------------
         double lam[3] = {0, 0, 0};
         int id = 0;
@@ -125,7 +136,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             }
             if (!ok) atomicOr(a.flags + FLAG_NONFINITE, 1);
             const int r1 = (c[0] - o1) & mask, r2 = (c[1] - o2) & mask, r3 = (c[2] - o3) & mask;
-            const bool in = r1 >= LO && r1 <= RMAX && r2 >= LO && r2 <= RMAX && r3 >= LO && r3 <= RMAX;
+            const bool in = HALO && r1 >= LO && r1 <= RMAX && r2 >= LO && r2 <= RMAX && r3 >= LO && r3 <= RMAX;
             const int rp = in ? pack_rel(r1, r2, r3) : -1;
             if constexpr (sizeof(T) == 4) rec.relf = __int_as_float(rp);
             else rec.relf = __longlong_as_double((long long)rp);
@@ -133,8 +144,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             p_cell[tid] = pack_cell(c[0], c[1], c[2]);
         }
         if (batch != j0) __syncthreads();   // the accumulator of the previous batch is flushed
-        if (!ASYNC || batch != j0) stage_halo<T, STORE, H, G, S2, S3, SC, 3, true>(halo, a.f, 0, 3, o1, o2, o3);
-        else cp_async_wait_all();
+        if constexpr (HALO) {
+            if (!ASYNC || batch != j0) stage_halo<T, STORE, H, G, S2, S3, SC, 3, true>(halo, a.f, 0, 3, o1, o2, o3);
+            else cp_async_wait_all();
+        }
         __syncthreads();
         // ---------------- Q1: u(X), J(X), J(X*) ----------------
         for (int q = warp; q < nbat; q += NW) {
@@ -167,11 +180,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             const int s1 = r1 + dc[0], s2 = r2 + dc[1], s3 = r3 + dc[2];
             const bool in2 = rp >= 0 && s1 >= LO && s1 <= RMAX && s2 >= LO && s2 <= RMAX && s3 >= LO && s3 <= RMAX;
             const int cs1 = (c1 + dc[0]) & mask, cs2 = (c2 + dc[1]) & mask, cs3 = (c3 + dc[2]) & mask;
-            if ((dc[0] | dc[1] | dc[2]) != 0 || rp < 0) {
+            // (direct: in the same cell the stage-1 stencil in L is re-used)
+            if ((dc[0] | dc[1] | dc[2]) != 0 || (HALO && rp < 0)) {
                 if (in2) {
                     L.load(SL{halo + (s3 - LO) * S3 + (s2 - LO) * S2 + (s1 - LO)});
                 } else {
-                    if (lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
+                    // left the staged halo, or (direct) moved more than one cell
+                    const bool far = HALO || abs(dc[0]) > 1 || abs(dc[1]) > 1 || abs(dc[2]) > 1;
+                    if (far && lane == 0) atomicOr(a.flags + FLAG_CFL, 1);
                     L.load(global_ld<T, STORE, I>(a.f, cs1, cs2, cs3, 0, 2));
                 }
             }
@@ -224,7 +240,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
             continue;
         }
         // ---------------- Q2: W^T scatter ----------------
-        if constexpr (GRED) {
+        if constexpr (AM != ADJ_SMEM) {
             __syncthreads();   // p_mu of every particle
             constexpr int H3 = H * H * H;
             T* slab = reinterpret_cast<T*>(a.gscratch) + (int64_t)b * 3 * H3;
@@ -244,12 +260,23 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
                 }
                 const T mus[2][3] = {{p_mu[q * 6 + 0], p_mu[q * 6 + 1], p_mu[q * 6 + 2]},
                                      {p_mu[q * 6 + 3], p_mu[q * 6 + 4], p_mu[q * 6 + 5]}};
-                if (rps[0] >= 0 && rps[0] == rps[1]) {
+                const bool same = HALO ? (rps[0] >= 0 && rps[0] == rps[1]) : p_cell[q] == p_cell2[q];
+                if (same) {
                     // X and X* in the same cell: one stencil, both weight sets, one add per node
                     const T sa[3] = {recs[0].t[0] - (T)0.5, recs[0].t[1] - (T)0.5, recs[0].t[2] - (T)0.5};
                     const T sb[3] = {recs[1].t[0] - (T)0.5, recs[1].t[1] - (T)0.5, recs[1].t[2] - (T)0.5};
                     W.eval_values2(sa, sb, wv, wd);
-                    L.template scatter_n<true>(wv, mus[0], wd, mus[1], add_slab(rps[0]));
+                    if constexpr (HALO) {
+                        L.template scatter_n<true>(wv, mus[0], wd, mus[1], add_slab(rps[0]));
+                    } else {
+                        const int pc = p_cell[q];
+                        const int c1 = pc & 1023, c2 = (pc >> 10) & 1023, c3 = (pc >> 20) & 1023;
+                        double* gf = a.gfield;
+                        L.template scatter_n<true>(wv, mus[0], wd, mus[1], [&](int k, int a1, int a2, int a3, T val) {
+                            const int x1 = (c1 + a1 - LO) & mask, x2 = (c2 + a2 - LO) & mask, x3 = (c3 + a3 - LO) & mask;
+                            atomicAdd(gf + k * NN3g + ((int64_t)x3 * N + x2) * N + x1, (double)val);
+                        });
+                    }
                     continue;
                 }
 #pragma unroll
@@ -257,7 +284,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
                     const PRec<T>& rec = recs[stage];
                     const int rp = rps[stage];
                     W.eval(rec.t[0] - (T)0.5, rec.t[1] - (T)0.5, rec.t[2] - (T)0.5, wv, wd);
-                    if (rp >= 0) {
+                    if (HALO && rp >= 0) {
                         L.template scatter_n<false>(wv, mus[stage], wv, mus[stage], add_slab(rp));
                     } else {
                         const int pc = stage == 0 ? p_cell[q] : p_cell2[q];
@@ -410,12 +437,12 @@ __global__ void k_adj_gather(const __grid_constant__ AdjArgs a)
     a.gfield[2 * NN3 + node] += s2;
 }
 
-template <typename T, int I, int DEG, int STORE, bool GRED>
+template <typename T, int I, int DEG, int STORE, int AM>
 cudaError_t launch_adjoint_g(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
 {
     constexpr int H = BLK + I - 1 + 2;
     constexpr size_t smem = AdjPlan<T, Layout<I, H>::SC>::total;
-    auto kern = k_adjoint<T, I, DEG, STORE, GRED>;
+    auto kern = k_adjoint<T, I, DEG, STORE, AM>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -427,12 +454,14 @@ cudaError_t launch_adjoint_g(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// with per-block scratch the W^T adds go to the block's slab in global memory
+// no offsets: the direct mode over a.np sorted particles; with per-block
+// scratch the W^T adds go to the block's slab in global memory
 template <typename T, int I, int DEG, int STORE>
 cudaError_t launch_adjoint_t(const AdjArgs& a, int64_t nblocks, cudaStream_t st)
 {
-    if (a.gscratch) return launch_adjoint_g<T, I, DEG, STORE, true>(a, nblocks, st);
-    return launch_adjoint_g<T, I, DEG, STORE, false>(a, nblocks, st);
+    if (!a.offsets) return launch_adjoint_g<T, I, DEG, STORE, ADJ_DIRECT>(a, (a.np + PBA - 1) / PBA, st);
+    if (a.gscratch) return launch_adjoint_g<T, I, DEG, STORE, ADJ_SLAB>(a, nblocks, st);
+    return launch_adjoint_g<T, I, DEG, STORE, ADJ_SMEM>(a, nblocks, st);
 }
 
 template <int I, int DEG>

@@ -470,6 +470,13 @@ constexpr double kDirectDensity = 0.05;
 // split-bf16 (node-major copy) 1.19 vs 0.59 and 2.45 vs 2.20.
 double direct_threshold(const tracker* t) { return column_available(t) ? kDirectDensity : 0.25; }
 
+// Below this many particles per grid cell the adjoint runs without halos
+// (direct mode); above it one CTA per cell block stages the block's halo.
+// Measured on GB300 (256^3 float32, spline I = 6, 20 RK2 steps, direct vs
+// halo ms per call): 23 vs 72 at 1/64 per cell, 74 vs 100 at 1/16, 282 vs
+// 221 at 1/4.
+constexpr double kAdjDirectDensity = 0.125;
+
 // Remembers a timing decision; the oldest is dropped beyond kCacheMax entries
 // (a caller whose particle counts keep changing re-times now and then).
 constexpr size_t kCacheMax = 256;
@@ -1310,7 +1317,12 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
     if (steps < 0) return fail(TRK_EINVAL, "steps=%d < 0", steps);
     if (ckpt_every < 1) return fail(TRK_EINVAL, "ckpt_every=%d < 1", ckpt_every);
     if (np > 0 && (!pos0 || !lambdaT || !grad_pos0)) return fail(TRK_EINVAL, "pos0, lambdaT and grad_pos0 must not be NULL");
-    if ((rc = check_block_kernel_shape(t))) return rc;
+    // sparse sets: the direct adjoint (no halos, stencils from global memory,
+    // float64 atomic adds straight into grad_field)
+    const bool adj_direct = t->step_kernel == TRK_STEP_DIRECT ||
+                            (t->step_kernel == TRK_STEP_AUTO &&
+                             (double)np < kAdjDirectDensity * (double)t->N * t->N * t->N);
+    if (!adj_direct && (rc = check_block_kernel_shape(t))) return rc;
     if (np == 0) return TRK_OK;
     const size_t vec = (size_t)3 * np;                 // doubles per position / lambda array
     if (steps == 0) {
@@ -1337,7 +1349,7 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
     // gather per node in a fixed block order, while the scratch stays below 8 GB
     // (else float64 atomics per halo node)
     void* gscratch = nullptr;
-    if (grad_field) {
+    if (grad_field && !adj_direct) {
         const int H = adj_halo(t->I);
         const size_t sb = (size_t)t->nblocks * 3 * H * H * H * (t->storage == TRK_F64 ? 8 : 4);
         size_t cap = (size_t)8 << 30;
@@ -1387,7 +1399,7 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
             a.cf = b.cf;
             a.cd = b.cd;
             a.np = np;
-            a.offsets = t->offsets;
+            a.offsets = adj_direct ? nullptr : t->offsets;   // null: the direct mode
             a.perm = t->perm;
             a.pos = X;
             a.lam_in = lam[cur];

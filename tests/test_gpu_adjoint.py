@@ -162,3 +162,59 @@ def test_field_gradient_scratch_and_atomic_paths_agree(monkeypatch, storage, I_,
     # different orders (atomics into the scratch slab vs a shared-memory
     # accumulator): they agree to the adjoint tolerance of 1e-6 relative
     assert rel(out["scratch"][1], out["atomic"][1]) <= (1e-14 if storage == trk.TRK_F64 else 1e-6)
+
+
+def stored_any(field, storage):
+    if storage != trk.TRK_BF16X2:
+        return stored(field, storage)
+    hi, lo = synth.bf16_split(torch.from_numpy(field.astype(np.float32)))
+    return hi.double().numpy() + lo.double().numpy()
+
+
+@pytest.mark.parametrize("storage", [trk.TRK_F64, trk.TRK_F32, trk.TRK_BF16X2])
+@pytest.mark.parametrize("I_,m_", [(4, 1), (6, 2), (8, 3)])
+@pytest.mark.parametrize("layout", ["sparse", "cluster"])
+def test_direct_adjoint_matches_oracle(storage, I_, m_, layout):
+    """The direct adjoint (no halos; float64 atomic adds straight into the
+    field gradient), forced, on a sparse set and on one crowded block."""
+    N, dt, steps, ckpt = 32, 5e-3, 4, 2
+    rng = np.random.default_rng(12)
+    if layout == "sparse":
+        pos = rng.uniform(0, L, (3, 60))
+    else:
+        pos = rng.uniform(0.01, 8 * L / N - 0.01, (3, 500))
+    field = synth.velocity_field_np(N, 10, 93)
+    fs = stored_any(field, storage)
+    posT = oracle.advance(fs, pos, dt, steps, FAM, I_, m_)
+    lam = 2 * posT
+    gpos_ref, gf_ref = oracle.adjoint_rk2(fs, pos, lam, dt, steps, FAM, I_, m_)
+    t = trk.Tracker(N, family=FAM, I=I_, m=m_, storage=storage)
+    t.set_step_kernel(trk.TRK_STEP_DIRECT)
+    t.set_field(torch.from_numpy(field).cuda())
+    gf = torch.zeros((3, N, N, N), dtype=torch.float64, device="cuda")
+    gpos, _ = t.adjoint(torch.from_numpy(pos).cuda(), torch.from_numpy(lam).cuda(), dt, steps, ckpt, grad_field=gf)
+    t.sync()
+    tol = 1e-10 if storage == trk.TRK_F64 else 1e-6
+    assert rel(gpos.cpu().numpy(), gpos_ref) <= tol
+    assert rel(gf.cpu().numpy(), gf_ref) <= tol
+
+
+@pytest.mark.parametrize("storage", [trk.TRK_F64, trk.TRK_F32])
+def test_direct_and_halo_adjoints_agree(storage):
+    N, n, dt, steps, ckpt = 32, 3000, 5e-3, 3, 2
+    field = synth.velocity_field_np(N, 10, 94)
+    pos = synth.uniform_particles_np(n, 14)
+    lam = 2 * pos
+    out = []
+    for kind in (trk.TRK_STEP_DIRECT, trk.TRK_STEP_BLOCK):
+        t = trk.Tracker(N, family=FAM, I=I, m=M, storage=storage)
+        t.set_step_kernel(kind)
+        t.set_field(torch.from_numpy(field).cuda())
+        gf = torch.zeros((3, N, N, N), dtype=torch.float64, device="cuda")
+        gpos, _ = t.adjoint(torch.from_numpy(pos).cuda(), torch.from_numpy(lam).cuda(), dt, steps, ckpt,
+                            grad_field=gf)
+        t.sync()
+        out.append((gpos.cpu().numpy(), gf.cpu().numpy()))
+        t.close()
+    assert np.array_equal(out[0][0], out[1][0])          # the position gradient: same float64 arithmetic
+    assert rel(out[0][1], out[1][1]) <= (1e-14 if storage == trk.TRK_F64 else 1e-6)
