@@ -199,7 +199,12 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     from the field in global memory, so no field sweep and no halo per
  *     cell block (all storages and kernels, any block shape; float32 and
  *     three-component split-bf16 fields are read from a node-major copy the
- *     tracker keeps, 16 bytes per node, made on first use).  The stage-2
+ *     tracker keeps, 16 bytes per node, made on first use; where that copy
+ *     is at most four times the L2 size (or the byte count in the
+ *     environment variable TRK_NM_TEXTURE_BYTES, 0 for never) it is read
+ *     through a texture object: the same bits, on the texture data path
+ *     instead of the load/store one, which the gathers of a copy that
+ *     mostly hits in L2 otherwise saturate).  The stage-2
  *     point of RK2 is gathered wherever it lies; TRK_ECFL is raised when it
  *     is more than one cell away.
  *   TRK_STEP_AUTO (default): DIRECT below 0.05 particles per grid cell
@@ -229,6 +234,12 @@ int tracker_step_kernel_for(const tracker* t, int64_t np);
  * with, or the latest tracker_interpolate used (after any timing);
  * TRK_STEP_AUTO before the first call; negative status on error. */
 int tracker_last_step_kernel(const tracker* t);
+
+/* 1 if the direct kernel reads the node-major copy of the current field
+ * through a texture object, 0 if by plain loads or if no copy has been made
+ * yet (the copy is made by the first direct launch after tracker_set_field);
+ * negative status on error. */
+int tracker_field_texture(const tracker* t);
 
 /* ---------------------------------------------------------------------- */
 /* Batched advection: many particle sets, one persistent launch per step  */

@@ -44,6 +44,7 @@ ABI_FUNCTIONS = (
     "tracker_profile", "tracker_profile_read", "tracker_bin_static", "tracker_set_step_kernel",
     "tracker_step_kernel_for", "tracker_state_write", "tracker_state_read_info", "tracker_state_read",
     "tracker_last_step_kernel",
+    "tracker_field_texture",
 )
 
 
@@ -104,6 +105,7 @@ def load_library(path: str = LIB_PATH):
             "tracker_set_step_kernel": (c_int, [vp, c_int]),
             "tracker_step_kernel_for": (c_int, [vp, c_i64]),
             "tracker_last_step_kernel": (c_int, [vp]),
+            "tracker_field_texture": (c_int, [vp]),
             "tracker_state_write": (c_int, [ctypes.c_char_p, vp, vp, vp]),
             "tracker_state_read_info": (c_int, [ctypes.c_char_p, vp]),
             "tracker_state_read": (c_int, [ctypes.c_char_p, c_i64, vp, vp, vp]),
@@ -400,6 +402,12 @@ class Tracker:
         r = int(load_library().tracker_last_step_kernel(self.h))
         _check(min(r, 0))
         return r
+
+    def field_texture(self):
+        """True if the direct kernel reads the node-major field copy through a texture object."""
+        r = int(load_library().tracker_field_texture(self.h))
+        _check(min(r, 0))
+        return bool(r)
 
     def save_state(self, path, pos, rhs=None, scheme=TRK_RK2, history_valid=0, step=0, time=0.0, dt=0.0):
         """Checkpoint a tracer set with this tracker's grid and kernel in the header."""

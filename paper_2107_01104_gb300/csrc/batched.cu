@@ -17,10 +17,16 @@ namespace {
 template <int I, int DEG, int STORE>
 __device__ __noinline__ void run_item(const BatchSet& S, int b, int j0, int j1, unsigned char* smem)
 {
-    constexpr int NM = NM_VEC4;   // batched fields have three components: 16-byte node loads
+    // batched fields have three components: 16-byte node loads, by texture
+    // fetches where the node-major copy has a texture
     if (S.direct) {
-        if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, false, NM>(S.a, b, j0, j1, smem);
-        else process_block<float, I, DEG, MODE_AB2, STORE, false, NM>(S.a, b, j0, j1, smem);
+        if (S.a.f.nm_tex) {
+            if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, false, NM_TEX4>(S.a, b, j0, j1, smem);
+            else process_block<float, I, DEG, MODE_AB2, STORE, false, NM_TEX4>(S.a, b, j0, j1, smem);
+        } else {
+            if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, false, NM_VEC4>(S.a, b, j0, j1, smem);
+            else process_block<float, I, DEG, MODE_AB2, STORE, false, NM_VEC4>(S.a, b, j0, j1, smem);
+        }
     } else {
         if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, true>(S.a, b, j0, j1, smem);
         else process_block<float, I, DEG, MODE_AB2, STORE, true>(S.a, b, j0, j1, smem);

@@ -212,19 +212,28 @@ struct NodeLd {
 
 // The three velocity components of a node as one aligned 16-byte load from the
 // padded node-major copy (float32: nmc = 4; split-bf16: the three hi/lo pairs,
-// each value formed as float(hi) + float(lo) as in fetch()).
-template <int I, int STORE>
+// each value formed as float(hi) + float(lo) as in fetch()).  Where the copy
+// has a texture object the load is a texture fetch (element type, no
+// filtering: the same bits), on the texture data path; the loads a caller
+// marks plain (about a quarter of the stencil rows) stay on the load/store
+// data path, so that the two paths, which the gathers otherwise saturate one
+// at a time, share the stencil.
+template <int I, int STORE, bool TEX = false>
 struct NodeLd4 {
     static constexpr bool kShared = false, kNode4 = true;
-    const void* nm;
+    const void* nm;             // the node-major copy
     int base, NP;
-    __device__ __forceinline__ float4 node(int a1, int a2, int a3) const
+    unsigned long long tex;     // texture fetches: the texture object over nm
+    // plain: a compile-time constant once the caller's loops are unrolled
+    __device__ __forceinline__ float4 node(int a1, int a2, int a3, bool plain = false) const
     {
         const int i = base + (a3 * NP + a2) * NP + a1;
         if constexpr (STORE == ST_F32) {
+            if (TEX && !plain) return tex1Dfetch<float4>((cudaTextureObject_t)tex, i);
             return __ldg(reinterpret_cast<const float4*>(nm) + i);
         } else {
-            const uint4 w = __ldg(reinterpret_cast<const uint4*>(nm) + i);
+            const uint4 w = TEX && !plain ? tex1Dfetch<uint4>((cudaTextureObject_t)tex, i)
+                                          : __ldg(reinterpret_cast<const uint4*>(nm) + i);
             auto val = [](uint32_t x) {
                 return __bfloat162float(__ushort_as_bfloat16((unsigned short)(x & 0xffffu))) +
                        __bfloat162float(__ushort_as_bfloat16((unsigned short)(x >> 16)));
@@ -324,7 +333,7 @@ struct Lane<T, 8, D> {
             for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int i3 = 0; i3 < 8; ++i3) {
-                    const float4 v = ld.node(i1, j + 4 * h, i3);
+                    const float4 v = ld.node(i1, j + 4 * h, i3, (i3 & 3) == 1);   // rows i3 = 1, 5 plain
                     f[0][h][i3] = v.x;
                     f[1][h][i3] = v.y;
                     f[2][h][i3] = v.z;
@@ -432,8 +441,10 @@ struct Lane<T, 6, D> {
         } else if constexpr (LD::kNode4) {
 #pragma unroll
             for (int i3 = 0; i3 < 8; ++i3) {
-                // pass A: row (i1, j) at i3 < 6; pass B: node (i1, 5, j); pass C: node (i1, 5, 5)
-                const float4 v = i3 < 6 ? ld.node(i1, j, i3) : (i3 == 6 ? ld.node(i1, 5, j) : ld.node(i1, 5, 5));
+                // pass A: row (i1, j) at i3 < 6; pass B: node (i1, 5, j); pass C: node (i1, 5, 5);
+                // pass A at i3 = 2 and pass B plain (10 of the 36 stencil rows)
+                const float4 v = i3 < 6 ? ld.node(i1, j, i3, i3 == 2)
+                                        : (i3 == 6 ? ld.node(i1, 5, j, true) : ld.node(i1, 5, 5));
                 f[0][i3] = v.x;
                 f[1][i3] = v.y;
                 f[2][i3] = v.z;
@@ -891,12 +902,14 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     const bool writer = (lane & 7) == 0 && rcomp < 3;                 // lanes 0, 8, 16
 
     // a stencil from global memory at cell (c1, c2, c3) in [0, N)^3, components k0 + k (clamped to kmax)
-    static_assert(NM == NM_NONE || (!HALO && (STORE == ST_F32 || (STORE == ST_BF16X2 && NM == NM_VEC4))),
+    static_assert(NM == NM_NONE || (!HALO && (STORE == ST_F32 || (STORE == ST_BF16X2 && NM >= NM_VEC4))),
                   "node-major gathers: direct path, float32 or (three components) split-bf16 storage");
     auto gload = [&](int c1, int c2, int c3, int k0, int kmax) {
         const int base = (int)padded_index(a.f.NP, c1 - LO, c2 - LO, c3 - LO);
-        if constexpr (NM == NM_VEC4)   // three components, 16 bytes per node
-            L.load(NodeLd4<I, STORE>{a.f.nm, base, a.f.NP});
+        if constexpr (NM == NM_TEX4)   // three components, one 16-byte texel per node
+            L.load(NodeLd4<I, STORE, true>{a.f.nm, base, a.f.NP, a.f.nm_tex});
+        else if constexpr (NM == NM_VEC4)   // three components, 16 bytes per node
+            L.load(NodeLd4<I, STORE>{a.f.nm, base, a.f.NP, 0});
         else if constexpr (NM == NM_SCALAR)
             L.load(NodeLd<T, I>{a.f.nm, base, a.f.NP, a.f.nmc, k0, kmax});
         else
@@ -1144,8 +1157,17 @@ cudaError_t launch_direct_nm(const BlockArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// 16-byte node loads: texture fetches where the copy has a texture, else plain loads
+template <typename T, int I, int DEG, int MODE, int STORE>
+cudaError_t launch_direct_vec(const BlockArgs& a, cudaStream_t st)
+{
+    if (a.f.nm_tex) return launch_direct_nm<T, I, DEG, MODE, STORE, NM_TEX4>(a, st);
+    return launch_direct_nm<T, I, DEG, MODE, STORE, NM_VEC4>(a, st);
+}
+
 // float32 fields read the node-major copy (16-byte node loads for three
-// components, which the time steps always have), other storages the field
+// components, which the time steps always have, as texture fetches where the
+// copy has textures), other storages the field
 template <typename T, int I, int DEG, int MODE, int STORE>
 cudaError_t launch_direct_t(const BlockArgs& a, cudaStream_t st)
 {
@@ -1153,14 +1175,14 @@ cudaError_t launch_direct_t(const BlockArgs& a, cudaStream_t st)
     constexpr bool STEP = MODE == MODE_RK2 || MODE == MODE_AB2;
     if constexpr (STORE == ST_F32) {
         if (!a.f.nm) return cudaErrorInvalidValue;   // the node-major copy is required
-        if (STEP || (a.f.C == 3 && a.f.nmc == 4)) return launch_direct_nm<T, I, DEG, MODE, STORE, NM_VEC4>(a, st);
+        if (STEP || (a.f.C == 3 && a.f.nmc == 4)) return launch_direct_vec<T, I, DEG, MODE, STORE>(a, st);
         if constexpr (!STEP) return launch_direct_nm<T, I, DEG, MODE, STORE, NM_SCALAR>(a, st);
         return cudaErrorInvalidValue;
     } else if constexpr (STORE == ST_BF16X2) {
         // three-component fields (all time steps) read the node-major copy
         if (a.f.C == 3) {
             if (!a.f.nm) return cudaErrorInvalidValue;
-            return launch_direct_nm<T, I, DEG, MODE, STORE, NM_VEC4>(a, st);
+            return launch_direct_vec<T, I, DEG, MODE, STORE>(a, st);
         }
         return launch_direct_nm<T, I, DEG, MODE, STORE, NM_NONE>(a, st);
     } else {

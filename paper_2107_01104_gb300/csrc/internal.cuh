@@ -46,6 +46,7 @@ struct FieldView {
     const float* nm;          // node-major copy for the direct path, or null: float32 fields [NP^3][nmc];
                               // split-bf16 fields with C = 3: 16 bytes per node (hi0 lo0 hi1 lo1 hi2 lo2 0 0)
     int nmc;                  // float32: floats per node in nm, 4 for C = 3 (one 16-byte load per node), else C
+    unsigned long long nm_tex; // texture object over nm (16-byte texels, C = 3), or 0 for plain loads
 };
 
 __host__ __device__ __forceinline__ int64_t padded_index(int NP, int x1, int x2, int x3)
@@ -97,8 +98,9 @@ constexpr int AB_MAX_HIST = 3;   // history entries of the highest supported ord
 
 // where the direct path gathers a float32 stencil from: the component-major
 // field, the node-major copy per component, or the node-major copy as one
-// 16-byte load per node (three components padded to four floats)
-enum { NM_NONE = 0, NM_SCALAR = 1, NM_VEC4 = 2 };
+// 16-byte load per node (three components padded to four floats), by plain
+// loads or by texture fetches (the same bits, on the texture data path)
+enum { NM_NONE = 0, NM_SCALAR = 1, NM_VEC4 = 2, NM_TEX4 = 3 };
 
 // dt-free Adams-Bashforth increment of order q (1..4): sum_j beta^q_j u_{n-j}
 // with u_n = f0 and u_{n-j} = hist(j - 1), summed newest first; beta^q are the

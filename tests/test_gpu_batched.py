@@ -68,6 +68,37 @@ def test_batched_sets_match_oracle(storage):
             assert np.abs(st["out"].cpu().numpy() - u).max() <= 3 * 2e-6
 
 
+@pytest.mark.parametrize("storage", [trk.TRK_F32, trk.TRK_BF16X2])
+def test_batched_texture_and_plain_loads_agree(monkeypatch, storage):
+    """Direct items read the node-major copy through a texture object (by
+    default for a copy this small) or by plain loads (TRK_NM_TEXTURE_BYTES=0):
+    the same bits either way (and whichever path each set takes, direct and
+    halo-staged agree bit for bit)."""
+    N, dt, steps = 32, 4e-3, 4
+    f32 = synth.velocity_field_np(N, 10, 97).astype(np.float32)
+    rng = np.random.default_rng(2)
+    specs = [dict(np=12, family=trk.TRK_SPLINE, I=8, m=3, deriv=1),
+             dict(np=40, family=trk.TRK_LAGRANGE, I=6, m=0, deriv=0),
+             dict(np=3000, family=trk.TRK_SPLINE, I=4, m=1, deriv=1)]
+    for sp in specs:
+        sp["pos"] = rng.uniform(-L, 2 * L, (3, sp["np"]))
+    res = []
+    for cap in (None, "0"):
+        if cap is None:
+            monkeypatch.delenv("TRK_NM_TEXTURE_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("TRK_NM_TEXTURE_BYTES", cap)
+        t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=storage)
+        t.set_field(torch.from_numpy(f32).cuda())
+        sets = run_sets(t, specs, dt, steps)
+        assert t.field_texture() == (cap is None)   # the first call times the direct path for every set
+        res.append([st[k].cpu() for st in sets for k in ("pos", "rhs", "out")])
+        t.close()
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert torch.equal(a, b)
+
+
 def test_batched_equals_single_set_path():
     N, dt, steps = 32, 4e-3, 5
     field = synth.velocity_field_np(N, 10, 96).astype(np.float32)

@@ -83,6 +83,36 @@ def test_direct_bit_identical_to_block(storage, I, m, scheme, N, n, layout):
         assert torch.equal(rb, rd)
 
 
+@pytest.mark.parametrize("storage", [trk.TRK_F32, trk.TRK_BF16X2])
+@pytest.mark.parametrize("I,m", [(4, 1), (6, 2), (8, 3)])
+@pytest.mark.parametrize("scheme", [trk.TRK_RK2, trk.TRK_AB4])
+def test_direct_texture_and_plain_loads_agree(monkeypatch, storage, I, m, scheme):
+    """The 16-byte node loads go through a texture object where the node-major
+    copy is small enough (by default at most four times the L2 size, as here),
+    else through plain loads (TRK_NM_TEXTURE_BYTES=0 forces these): the same
+    bits either way, stepping and interpolating."""
+    N, n = 64, 5000
+    field = synth.velocity_field_np(N, 10, 470)
+    pos = positions("edges", N, n, 23)
+    res = []
+    for cap in (None, "0"):
+        if cap is None:
+            monkeypatch.delenv("TRK_NM_TEXTURE_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("TRK_NM_TEXTURE_BYTES", cap)
+        p, r = advance(N, I, m, storage, field, pos, trk.TRK_STEP_DIRECT, scheme, 5, 4e-3)
+        t = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=m, storage=storage)
+        t.set_step_kernel(trk.TRK_STEP_DIRECT)
+        t.set_field(torch.from_numpy(field).to(DEV))
+        u = t.interpolate(torch.from_numpy(pos).to(DEV), out_dtype=torch.float64, deriv=True).cpu()
+        t.sync()
+        assert t.field_texture() == (cap is None)
+        res.append((p, r, u))
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("I,m", KERNELS)
 @pytest.mark.parametrize("C,deriv", [(3, 0), (3, 1), (9, 0), (4, 1)])
