@@ -17,16 +17,13 @@ namespace {
 template <int I, int DEG, int STORE>
 __device__ __noinline__ void run_item(const BatchSet& S, int b, int j0, int j1, unsigned char* smem)
 {
-    // batched fields have three components: 16-byte node loads, by texture
-    // fetches where the node-major copy has a texture
+    // batched fields have three components: 16-byte node loads, plain ones (a
+    // texture-fetch variant beside them in this function made the compiler
+    // spill several KB per item on the float32 paths)
+    constexpr int NM = NM_VEC4;
     if (S.direct) {
-        if (S.a.f.nm_tex) {
-            if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, false, NM_TEX4>(S.a, b, j0, j1, smem);
-            else process_block<float, I, DEG, MODE_AB2, STORE, false, NM_TEX4>(S.a, b, j0, j1, smem);
-        } else {
-            if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, false, NM_VEC4>(S.a, b, j0, j1, smem);
-            else process_block<float, I, DEG, MODE_AB2, STORE, false, NM_VEC4>(S.a, b, j0, j1, smem);
-        }
+        if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, false, NM>(S.a, b, j0, j1, smem);
+        else process_block<float, I, DEG, MODE_AB2, STORE, false, NM>(S.a, b, j0, j1, smem);
     } else {
         if (S.deriv) process_block<float, I, DEG, MODE_AB2_D, STORE, true>(S.a, b, j0, j1, smem);
         else process_block<float, I, DEG, MODE_AB2, STORE, true>(S.a, b, j0, j1, smem);

@@ -70,10 +70,11 @@ def test_batched_sets_match_oracle(storage):
 
 @pytest.mark.parametrize("storage", [trk.TRK_F32, trk.TRK_BF16X2])
 def test_batched_texture_and_plain_loads_agree(monkeypatch, storage):
-    """Direct items read the node-major copy through a texture object (by
-    default for a copy this small) or by plain loads (TRK_NM_TEXTURE_BYTES=0):
-    the same bits either way (and whichever path each set takes, direct and
-    halo-staged agree bit for bit)."""
+    """The batched kernel's direct items read the node-major copy by plain
+    loads whether or not the tracker made a texture object over it (by
+    default for a copy this small; TRK_NM_TEXTURE_BYTES=0: none): the
+    texture setting must not change a bit of the results (and whichever path
+    each set takes, direct and halo-staged agree bit for bit)."""
     N, dt, steps = 32, 4e-3, 4
     f32 = synth.velocity_field_np(N, 10, 97).astype(np.float32)
     rng = np.random.default_rng(2)
@@ -91,7 +92,7 @@ def test_batched_texture_and_plain_loads_agree(monkeypatch, storage):
         t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=storage)
         t.set_field(torch.from_numpy(f32).cuda())
         sets = run_sets(t, specs, dt, steps)
-        assert t.field_texture() == (cap is None)   # the first call times the direct path for every set
+        assert t.field_texture() == (cap is None)   # the first call makes the copy (it times both paths per set)
         res.append([st[k].cpu() for st in sets for k in ("pos", "rhs", "out")])
         t.close()
     for other in res[1:]:
