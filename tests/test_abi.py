@@ -49,6 +49,11 @@ def test_binding_loads_and_reports_errors_without_gpu(lib):
         trk.tracker_create(64, I=5)          # unsupported kernel width
     with pytest.raises(trk.TrackerError):
         trk.tracker_create(64, family=trk.TRK_SPLINE, I=6, m=4)
+    # queries on a NULL tracker return TRK_EINVAL without touching a device
+    L = trk.load_library()
+    assert L.tracker_field_texture(None) == trk.TRK_EINVAL
+    assert L.tracker_last_step_kernel(None) == trk.TRK_EINVAL
+    assert L.tracker_launch_count(None) == -1
 
 
 def test_oracle_and_library_share_no_code():
