@@ -362,6 +362,8 @@ def run_gb300(args):
     achieved = alg_bytes / avg_launch_s / 1e9
     kind = {trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_COLUMN: "column",
             trk.TRK_STEP_DIRECT: "direct"}[tr.last_step_kernel()]
+    if kind == "direct":   # node loads through the texture object (three quarters of the rows) or plain loads
+        notes["direct_node_loads"] = "texture" if tr.field_texture() else "plain"
     sha = kernel_source_sha(kind)
     gather_bytes = NP * 2 * I ** 3 * 3 * 4            # two stencil gathers per RK2 step, float32
     sm_mhz = clk.get("sm_mhz") or 1900.0
@@ -455,7 +457,9 @@ def run_gb300(args):
             "smem_roofline": {"achieved": gather_bytes / avg_launch_s / 1e9, "peak": smem_peak, "unit": "GB/s",
                               "frac": gather_bytes / avg_launch_s / 1e9 / smem_peak,
                               "gather_bytes_per_launch": gather_bytes,
-                              "path": "shared memory" if kind != "direct" else "L1 (global gathers)",
+                              "path": "shared memory" if kind != "direct" else
+                              ("L1 (gathers: texture and load/store data paths)" if tr.field_texture()
+                               else "L1 (global gathers)"),
                               "peak_def": "SMs x 128 B/clk (the L1 / shared-memory data path) x median SM clock under load"},
             "phase_ms_per_step": {"step_kernel": step_ms / psteps, "binning": prof["bin"][0] / psteps,
                                   "other": prof["other"][0] / psteps, "profiled_steps": psteps,
@@ -702,6 +706,8 @@ def run_config6(args):
     for _ in range(args.warmup):
         t.advance(p, dt, inner, trk.TRK_RK2)
     sync_flags(t, trk, notes)
+    if kind == "direct":
+        notes["direct_node_loads"] = "texture" if t.field_texture() else "plain"
     l0 = t.launch_count
     e0, e1 = _events()
     e0.record(stream)

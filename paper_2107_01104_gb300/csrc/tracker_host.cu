@@ -485,8 +485,10 @@ int ensure_node_major(tracker* t)
             return fail(TRK_ENOMEM, "cannot allocate the node-major field copy (%zu bytes)", bytes);
         }
         t->nm_bytes = bytes;
-        if (nmc == 4) create_nm_texture(t, plane, bytes, f32);
     }
+    // the 16-byte node loads of the direct kernel (a copy first made for C = 4
+    // has the same size but no texture)
+    if (t->C == 3 && !t->nm_tex) create_nm_texture(t, plane, bytes, f32);
     {
         ProfScope ps(t, PROF_OTHER);
         if (f32) {
@@ -887,7 +889,7 @@ int tracker_last_step_kernel(const tracker* t)
 int tracker_field_texture(const tracker* t)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
-    return t->nm_valid && t->nm_tex ? 1 : 0;
+    return t->nm_valid && t->nm_tex && t->C == 3 ? 1 : 0;
 }
 
 int64_t tracker_launch_count(const tracker* t) { return t ? t->launches : -1; }
