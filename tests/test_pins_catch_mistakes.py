@@ -1,0 +1,129 @@
+"""The oracle's pins are sensitive: a plausible mistake planted in the oracle
+(on the CPU, by wrapping its Python entry points) makes at least one of the
+pin tests fail.
+
+Planted mistakes: a transposed node order, a flipped sign, a dropped term, a
+mirrored or shifted cell offset in the weights; swapped axes, swapped
+components, a one-cell index shift in the triple sum; a wrong step size, a
+flipped velocity sign, a reversed Adams-Bashforth history in the steppers.
+Nothing here runs the library."""
+import numpy as np
+import pytest
+
+import oracle
+import test_golden as G
+import test_oracle_interp as PI
+import test_oracle_steppers as PS
+import test_oracle_weights as PW
+
+L = 2 * np.pi
+
+
+def fails(pin, *args):
+    try:
+        pin(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def any_pin_fails(pins):
+    return sum(fails(pin, *args) for pin, args in pins)
+
+
+# ---- weights ---------------------------------------------------------------
+WEIGHT_MUTATIONS = {
+    "transposed node order": lambda w, t, f: w[::-1].copy(),
+    "flipped sign of one term": lambda w, t, f: w * np.where(np.arange(len(w)) == 1, -1.0, 1.0),
+    "dropped term": lambda w, t, f: np.where(np.arange(len(w)) == 0, 0.0, w),
+    "mirrored offset t -> 1 - t": lambda w, t, f: f(1.0 - t),
+    "index shifted by one node": lambda w, t, f: np.roll(w, 1),
+}
+
+
+def weight_pins():
+    pins = []
+    for fam, I, m in [(oracle.LAGRANGE, 4, 0), (oracle.LAGRANGE, 6, 0), (oracle.SPLINE, 4, 1), (oracle.SPLINE, 6, 2)]:
+        pins += [(PW.test_partition_of_unity, (fam, I, m)), (PW.test_interpolates_nodes, (fam, I, m)),
+                 (PW.test_polynomial_reproduction_degree, (fam, I, m))]
+    pins += [(G.test_lagrange_midpoint_weights, (r,)) for r in G.rows("lagrange_midpoint_weights.txt")]
+    pins += [(G.test_spline_I4_m1_is_the_cubic_convolution_kernel, (r,)) for r in G.rows("keys_cubic_convolution.txt")]
+    return pins
+
+
+@pytest.mark.parametrize("name", list(WEIGHT_MUTATIONS))
+def test_weight_mistakes_are_caught(monkeypatch, name):
+    orig = oracle.weights
+    mut = WEIGHT_MUTATIONS[name]
+
+    def planted(family, I, m, t, deriv=False):
+        return mut(orig(family, I, m, t, deriv), t, lambda s: orig(family, I, m, s, deriv))
+
+    monkeypatch.setattr(oracle, "weights", planted)
+    assert any_pin_fails(weight_pins()) > 0
+
+
+# ---- triple sum --------------------------------------------------------------
+def shift_one_cell(orig, field, pos, *a, **k):
+    N = field.shape[-1]
+    return orig(field, pos + L / N, *a, **k)
+
+
+INTERP_MUTATIONS = {
+    "axes x1 and x2 swapped": lambda orig, field, pos, *a, **k: orig(field, pos[[1, 0, 2]], *a, **k),
+    "components swapped": lambda orig, field, pos, *a, **k: orig(field, pos, *a, **k)[[1, 0, 2] if field.shape[0] == 3
+                                                                                       else slice(None)],
+    "one-cell index shift": shift_one_cell,
+}
+
+
+def interp_pins():
+    pins = []
+    for fam, I, m in [(oracle.LAGRANGE, 4, 0), (oracle.SPLINE, 6, 2)]:
+        pins += [(PI.test_constant_field, (fam, I, m)), (PI.test_polynomial_field_reproduced_on_local_window, (fam, I, m))]
+    pins += [(PI.test_lagrange_separable_field_vs_scipy, (4,))]
+    return pins
+
+
+@pytest.mark.parametrize("name", list(INTERP_MUTATIONS))
+def test_interpolation_mistakes_are_caught(monkeypatch, name):
+    orig = oracle.interp
+    mut = INTERP_MUTATIONS[name]
+    monkeypatch.setattr(oracle, "interp", lambda field, pos, *a, **k: mut(orig, field, pos, *a, **k))
+    assert any_pin_fails(interp_pins()) > 0
+
+
+# ---- time steppers -------------------------------------------------------------
+def reversed_history(orig, field, pos, dt, steps, *a, **k):
+    rhs = k.get("rhs")
+    if rhs is not None and np.asarray(rhs).shape[0] > 1:
+        k = dict(k, rhs=np.asarray(rhs)[::-1].copy())
+    return orig(field, pos, dt, steps, *a, **k)
+
+
+STEP_MUTATIONS = {
+    "step size off by 0.1%": lambda orig, field, pos, dt, steps, *a, **k: orig(field, pos, dt * 1.001, steps, *a, **k),
+    "velocity sign flipped": lambda orig, field, pos, dt, steps, *a, **k: orig(-field, pos, dt, steps, *a, **k),
+    "history entries reversed": reversed_history,
+}
+
+
+def step_pins():
+    pins = [(PS.test_uniform_flow_is_exact, (oracle.RK2,)), (PS.test_uniform_flow_is_exact, (oracle.AB2,)),
+            (PS.test_rk2_rotation_closed_form, (oracle.SPLINE, 6, 2)), (PS.test_ab2_rotation_recurrence, ())]
+    pins += [(PS.test_ab_weights_match_their_definition, (s, k)) for s, k in [(oracle.AB3, 3), (oracle.AB4, 4)]]
+    pins += [(G.test_adams_bashforth_coefficients, (r,)) for r in G.rows("adams_bashforth_coefficients.txt")]
+    return pins
+
+
+@pytest.mark.parametrize("name", list(STEP_MUTATIONS))
+def test_stepper_mistakes_are_caught(monkeypatch, name):
+    orig = oracle.advance
+    mut = STEP_MUTATIONS[name]
+    monkeypatch.setattr(oracle, "advance", lambda field, pos, dt, steps, *a, **k: mut(orig, field, pos, dt, steps, *a, **k))
+    assert any_pin_fails(step_pins()) > 0
+
+
+def test_unmutated_oracle_passes_every_pin_used_here():
+    for pin, args in weight_pins() + interp_pins() + step_pins():
+        pin(*args)
