@@ -5,13 +5,15 @@ pin tests fail.
 Planted mistakes: a transposed node order, a flipped sign, a dropped term, a
 mirrored or shifted cell offset in the weights; swapped axes, swapped
 components, a one-cell index shift in the triple sum; a wrong step size, a
-flipped velocity sign, a reversed Adams-Bashforth history in the steppers.
+flipped velocity sign, a reversed Adams-Bashforth history in the steppers; a
+missing Jacobian term, transposed axes, a scaled cotangent in the adjoint.
 Nothing here runs the library."""
 import numpy as np
 import pytest
 
 import oracle
 import test_golden as G
+import test_oracle_adjoint as PA
 import test_oracle_interp as PI
 import test_oracle_steppers as PS
 import test_oracle_weights as PW
@@ -124,6 +126,34 @@ def test_stepper_mistakes_are_caught(monkeypatch, name):
     assert any_pin_fails(step_pins()) > 0
 
 
+# ---- adjoint ----------------------------------------------------------------------
+def adjoint_transposed_axes(orig, field, pos0, lam, *a, **k):
+    gpos, gf = orig(field, pos0, lam, *a, **k)
+    return gpos, (gf.transpose(0, 1, 3, 2).copy() if gf is not None else gf)
+
+
+ADJOINT_MUTATIONS = {
+    "position gradient missing the J^T term": lambda orig, field, pos0, lam, *a, **k:
+        (lam.copy(), orig(field, pos0, lam, *a, **k)[1]),
+    "field gradient with x1, x2 transposed": adjoint_transposed_axes,
+    "lambda scaled by 1.001": lambda orig, field, pos0, lam, *a, **k: orig(field, pos0, lam * 1.001, *a, **k),
+}
+
+
+def adjoint_pins():
+    return [(PA.test_position_gradient_matches_central_differences, ()),
+            (PA.test_field_gradient_matches_central_differences, ()),
+            (PA.test_interpolation_transpose_identity, ())]
+
+
+@pytest.mark.parametrize("name", list(ADJOINT_MUTATIONS))
+def test_adjoint_mistakes_are_caught(monkeypatch, name):
+    orig = oracle.adjoint_rk2
+    mut = ADJOINT_MUTATIONS[name]
+    monkeypatch.setattr(oracle, "adjoint_rk2", lambda field, pos0, lam, *a, **k: mut(orig, field, pos0, lam, *a, **k))
+    assert any_pin_fails(adjoint_pins()) > 0
+
+
 def test_unmutated_oracle_passes_every_pin_used_here():
-    for pin, args in weight_pins() + interp_pins() + step_pins():
+    for pin, args in weight_pins() + interp_pins() + step_pins() + adjoint_pins():
         pin(*args)
