@@ -2,8 +2,10 @@
 (on the CPU, by wrapping its Python entry points) makes at least one of the
 pin tests fail.
 
-Planted mistakes: a transposed node order, a flipped sign, a dropped term, a
-mirrored or shifted cell offset in the weights; swapped axes, swapped
+Planted mistakes: the nearest cell instead of the one below, an unwrapped cell
+index, an unstable order among equal keys, swapped key axes, offsets off by
+one in the split and binning; a transposed node order, a flipped sign, a
+dropped term, a mirrored or shifted cell offset in the weights; swapped axes, swapped
 components, a one-cell index shift in the triple sum; a wrong step size, a
 flipped velocity sign, a reversed Adams-Bashforth history in the steppers; a
 missing Jacobian term, transposed axes, a scaled cotangent in the adjoint.
@@ -59,10 +61,74 @@ def test_weight_mistakes_are_caught(monkeypatch, name):
     mut = WEIGHT_MUTATIONS[name]
 
     def planted(family, I, m, t, deriv=False):
-        return mut(orig(family, I, m, t, deriv), t, lambda s: orig(family, I, m, s, deriv))
+        if deriv:   # the pins used here read the values only
+            return orig(family, I, m, t, deriv)
+        return mut(orig(family, I, m, t), t, lambda s: orig(family, I, m, s))
 
     monkeypatch.setattr(oracle, "weights", planted)
     assert any_pin_fails(weight_pins()) > 0
+
+
+# ---- split and binning --------------------------------------------------------
+def unstable_ties(orig, pos, *a, **k):
+    keys, perm, offsets = orig(pos, *a, **k)
+    perm = perm.copy()
+    for b in range(len(offsets) - 1):          # reverse the order inside every block
+        perm[offsets[b]:offsets[b + 1]] = perm[offsets[b]:offsets[b + 1]][::-1]
+    return keys, perm, offsets
+
+
+def offsets_off_by_one(orig, pos, *a, **k):
+    keys, perm, offsets = orig(pos, *a, **k)
+    offsets = offsets.copy()
+    offsets[1:-1] += 1
+    return keys, perm, offsets
+
+
+BIN_MUTATIONS = {
+    "unstable order among equal keys": unstable_ties,
+    "key axes x1 and x2 swapped": lambda orig, pos, *a, **k: orig(pos[[1, 0, 2]], *a, **k),
+    "offsets off by one": offsets_off_by_one,
+}
+
+
+def round_to_nearest_cell(orig, pos, N, *a, **k):
+    c, t = orig(pos, N, *a, **k)
+    up = t >= 0.5
+    return np.where(up, (c + 1) % N, c).astype(c.dtype), np.where(up, t - 1.0, t)
+
+
+def no_periodic_wrap(orig, pos, N, *a, **k):
+    c, t = orig(pos, N, *a, **k)
+    L_ = k.get("L", L)
+    return (c + N * np.floor(pos / L_).astype(c.dtype)), t
+
+
+SPLIT_MUTATIONS = {
+    "nearest cell instead of the cell below": round_to_nearest_cell,
+    "cell index not wrapped": no_periodic_wrap,
+}
+
+
+def bin_pins():
+    return [(PI.test_split_geometry_and_ranges, ()), (PI.test_binning_slices_like_the_paper, ())] + [
+        (PI.test_binning_is_stable_sort_by_block, (B,)) for B in [(2, 2, 2), (4, 2, 8)]]
+
+
+@pytest.mark.parametrize("name", list(BIN_MUTATIONS))
+def test_binning_mistakes_are_caught(monkeypatch, name):
+    orig = oracle.bin_particles
+    mut = BIN_MUTATIONS[name]
+    monkeypatch.setattr(oracle, "bin_particles", lambda pos, *a, **k: mut(orig, pos, *a, **k))
+    assert any_pin_fails(bin_pins()) > 0
+
+
+@pytest.mark.parametrize("name", list(SPLIT_MUTATIONS))
+def test_split_mistakes_are_caught(monkeypatch, name):
+    orig = oracle.split
+    mut = SPLIT_MUTATIONS[name]
+    monkeypatch.setattr(oracle, "split", lambda pos, N, *a, **k: mut(orig, pos, N, *a, **k))
+    assert any_pin_fails(bin_pins()) > 0
 
 
 # ---- triple sum --------------------------------------------------------------
@@ -155,5 +221,5 @@ def test_adjoint_mistakes_are_caught(monkeypatch, name):
 
 
 def test_unmutated_oracle_passes_every_pin_used_here():
-    for pin, args in weight_pins() + interp_pins() + step_pins() + adjoint_pins():
+    for pin, args in weight_pins() + bin_pins() + interp_pins() + step_pins() + adjoint_pins():
         pin(*args)
