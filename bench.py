@@ -362,8 +362,10 @@ def run_gb300(args):
     achieved = alg_bytes / avg_launch_s / 1e9
     kind = {trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_COLUMN: "column",
             trk.TRK_STEP_DIRECT: "direct"}[tr.last_step_kernel()]
+    kernel_label = STEP_KERNELS[kind][0]
     if kind == "direct":   # node loads through the texture object (three quarters of the rows) or plain loads
         notes["direct_node_loads"] = "texture" if tr.field_texture() else "plain"
+        kernel_label = kernel_label[:-1] + (",NM_TEX4>" if tr.field_texture() else ",NM_VEC4>")
     sha = kernel_source_sha(kind)
     gather_bytes = NP * 2 * I ** 3 * 3 * 4            # two stencil gathers per RK2 step, float32
     sm_mhz = clk.get("sm_mhz") or 1900.0
@@ -446,7 +448,7 @@ def run_gb300(args):
                        "positions": "f64", "l2": "inputs larger than L2 (201 MB field vs 129 MB L2)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": ncu_traffic(sha, kind), "kernel": STEP_KERNELS[kind][0],
+                         "traffic": ncu_traffic(sha, kind), "kernel": kernel_label,
                          "l2_hit_rate": ncu_record(sha, kind).get("l2_hit_rate"),
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                          "launches_timed": step_n, "peak_kind": peak_kind, "source_sha": sha},
