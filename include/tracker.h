@@ -30,6 +30,11 @@
  *   with 16 <= N <= 1024; I in {4, 6, 8}.
  * - There is no CPU fallback: every computation runs in this library's
  *   CUDA kernels (sm_103a).  A missing GPU is TRK_ECUDA.
+ * - A tracker belongs to the CUDA device that was current when it was
+ *   created, where all its buffers live.  Every later call that launches
+ *   work or allocates must be made with that device current; otherwise it
+ *   returns TRK_EINVAL without touching the GPU.  tracker_destroy makes the
+ *   tracker's device current by itself and restores the caller's device.
  */
 #ifndef TRACKER_H
 #define TRACKER_H
@@ -132,8 +137,10 @@ int64_t tracker_num_blocks(const tracker* t);
  * perm[np] (perm[j] = incoming index of the j-th particle in sorted
  * order, ties kept in incoming order), offsets[nblocks+1] (offsets[b] =
  * first sorted position of block b, offsets[nblocks] = np: the paper's
- * offset array).  Errors: TRK_EINVAL, TRK_ENOMEM; non-finite positions
- * raise the TRK_ENONFINITE device flag. */
+ * offset array).  pos and the outputs must be device memory of the
+ * tracker's device (checked, TRK_EINVAL otherwise); the caller sizes them
+ * (np, np, nblocks + 1 entries).  Errors: TRK_EINVAL, TRK_ENOMEM;
+ * non-finite positions raise the TRK_ENONFINITE device flag. */
 int tracker_bin(tracker* t, int64_t np, const double* pos, int32_t* keys, int32_t* perm, int32_t* offsets);
 
 /* ---------------------------------------------------------------------- */
@@ -143,9 +150,10 @@ int tracker_bin(tracker* t, int64_t np, const double* pos, int32_t* keys, int32_
 /* out[k][p] = u_k(X_p) for every field component k < C (deriv = 0), or
  * out[(3k + j)][p] = d u_k / d X_j at X_p (deriv = 1; derivative kernels
  * beta' on axis j, times N/L).  out_dtype is TRK_DTYPE_F32 or
- * TRK_DTYPE_F64 (any storage).  Particles are binned internally; results
- * are written in the caller's order.  Errors: TRK_EINVAL, TRK_ENOFIELD,
- * TRK_ENOMEM. */
+ * TRK_DTYPE_F64 (any storage).  Particles are binned internally (a counting
+ * sort by block: block counts, one scan, a scatter of the permutation; the
+ * order inside a block does not change any result); results are written in
+ * the caller's order.  Errors: TRK_EINVAL, TRK_ENOFIELD, TRK_ENOMEM. */
 int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, int out_dtype, int deriv);
 
 /* ---------------------------------------------------------------------- */
@@ -361,6 +369,15 @@ int64_t tracker_launch_count(const tracker* t);
 int tracker_profile(tracker* t, int enable);
 int tracker_profile_read(tracker* t, double* ms, int64_t* launches);
 
+/* Instrumentation (no counterpart in the paper): the fused multiply-add rate
+ * of the current device, float32 (dtype TRK_DTYPE_F32) or float64
+ * (TRK_DTYPE_F64), measured by a short kernel of independent FMA chains on
+ * every SM (about 10 ms, on the legacy default stream, synchronous).
+ * *fma_per_s receives FMAs per second (one FMA = 2 flops): the denominator
+ * of the FMA-bound fraction of the float32 and float64 interpolation forms.
+ * Errors: TRK_EINVAL, TRK_ENOMEM, TRK_ECUDA. */
+int tracker_probe_fma(int dtype, double* fma_per_s);
+
 /* ---------------------------------------------------------------------- */
 /* Binning without allocation                                              */
 /* ---------------------------------------------------------------------- */
@@ -376,8 +393,11 @@ int tracker_profile_read(tracker* t, double* ms, int64_t* launches);
  * Arguments as in tracker_bin, plus the grid (N, L) and block shape
  * (bx, by, bz) that a tracker would hold; nonfinite (device int32, may be
  * NULL) receives 1 if a position was non-finite, else 0.  stream is a
- * cudaStream_t.  np may not exceed 262144 (2^18): larger calls return
- * TRK_EINVAL with a message.  The first call on a device looks up the
+ * cudaStream_t of the current device.  pos and every output must be device
+ * memory of the current device (checked: TRK_EINVAL otherwise), sized by the
+ * caller: keys and perm np entries, offsets nblocks + 1 =
+ * (N/bx)(N/by)(N/bz) + 1 entries, nonfinite one.  np may not exceed 262144
+ * (2^18): larger calls return TRK_EINVAL with a message.  The first call on a device looks up the
  * array's device address, so make that first call before any stream
  * capture.  Every call reuses the same array, which keeps the last call's
  * contents; calls that overlap on the GPU (other streams, other threads)

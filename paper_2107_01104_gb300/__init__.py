@@ -44,7 +44,7 @@ ABI_FUNCTIONS = (
     "tracker_profile", "tracker_profile_read", "tracker_bin_static", "tracker_set_step_kernel",
     "tracker_step_kernel_for", "tracker_state_write", "tracker_state_read_info", "tracker_state_read",
     "tracker_last_step_kernel",
-    "tracker_field_texture",
+    "tracker_field_texture", "tracker_probe_fma",
 )
 
 
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH):
             "tracker_step_kernel_for": (c_int, [vp, c_i64]),
             "tracker_last_step_kernel": (c_int, [vp]),
             "tracker_field_texture": (c_int, [vp]),
+            "tracker_probe_fma": (c_int, [c_int, vp]),
             "tracker_state_write": (c_int, [ctypes.c_char_p, vp, vp, vp]),
             "tracker_state_read_info": (c_int, [ctypes.c_char_p, vp]),
             "tracker_state_read": (c_int, [ctypes.c_char_p, c_i64, vp, vp, vp]),
@@ -133,23 +134,31 @@ def _ptr(x):
     return ctypes.c_void_p(x.data_ptr())
 
 
-def _stream_ptr():
+def _stream_ptr(device=None):
     if not torch.cuda.is_available():
         return ctypes.c_void_p(None)
-    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
-def _dev(x, dtype, name, shape0=None):
+def _dev(x, dtype, name, shape0=None, device=None, numel=None, min_numel=None):
+    """Checks a device array argument: dtype, on the GPU (on `device` if given),
+    contiguous, and optionally its leading dimension or element count."""
     if not isinstance(x, torch.Tensor):
         raise TypeError(f"{name} must be a torch tensor")
     if x.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
     if not x.is_cuda:
         raise ValueError(f"{name} must be on the GPU")
+    if device is not None and x.device != device:
+        raise ValueError(f"{name} must be on {device}, got {x.device}")
     if not x.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if shape0 is not None and (x.dim() != 2 or x.shape[0] != shape0):
         raise ValueError(f"{name} must have shape ({shape0}, n), got {tuple(x.shape)}")
+    if numel is not None and x.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} values, got {x.numel()}")
+    if min_numel is not None and x.numel() < min_numel:
+        raise ValueError(f"{name} must hold at least {min_numel} values, got {x.numel()}")
     return x
 
 
@@ -266,15 +275,31 @@ def tracker_profile_read(h):
     return {"step": (ms[0], n[0]), "bin": (ms[1], n[1]), "other": (ms[2], n[2])}
 
 
+def _bin_outputs(dev, n, nb, keys, perm, offsets):
+    """Caller-given (or new) int32 outputs of a binning call, checked against the
+    sizes the kernels write: keys and perm n entries, offsets nb + 1."""
+    keys = torch.empty(n, dtype=torch.int32, device=dev) if keys is None else keys
+    perm = torch.empty(n, dtype=torch.int32, device=dev) if perm is None else perm
+    offsets = torch.empty(nb + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
+    _dev(keys, torch.int32, "keys", device=dev, numel=n)
+    _dev(perm, torch.int32, "perm", device=dev, numel=n)
+    _dev(offsets, torch.int32, "offsets", device=dev, numel=nb + 1)
+    return keys, perm, offsets
+
+
+def tracker_probe_fma(dtype=TRK_DTYPE_F32) -> float:
+    """Measured fused multiply-adds per second of the current GPU (float32 or float64)."""
+    r = ctypes.c_double(0.0)
+    _check(load_library().tracker_probe_fma(int(dtype), ctypes.byref(r)))
+    return r.value
+
+
 def tracker_bin(h, pos, keys=None, perm=None, offsets=None):
     pos = _dev(pos, torch.float64, "pos", 3)
     n = pos.shape[1]
-    dev = pos.device
-    keys = torch.empty(n, dtype=torch.int32, device=dev) if keys is None else keys
-    perm = torch.empty(n, dtype=torch.int32, device=dev) if perm is None else perm
-    nb = tracker_num_blocks(h)
-    offsets = torch.empty(nb + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
-    _check(load_library().tracker_bin(h, n, _ptr(pos), _ptr(keys), _ptr(perm), _ptr(offsets)))
+    keys, perm, offsets = _bin_outputs(pos.device, n, tracker_num_blocks(h), keys, perm, offsets)
+    with torch.cuda.device(pos.device):
+        _check(load_library().tracker_bin(h, n, _ptr(pos), _ptr(keys), _ptr(perm), _ptr(offsets)))
     return keys, perm, offsets
 
 
@@ -284,14 +309,17 @@ def tracker_bin_static(pos, N, L=2 * math.pi, block=(8, 8, 8), keys=None, perm=N
     pos = _dev(pos, torch.float64, "pos", 3)
     n = pos.shape[1]
     dev = pos.device
+    if any(int(b) <= 0 or int(N) % int(b) for b in block):
+        raise ValueError(f"block edges {tuple(block)} must divide N={N}")
     nb = (N // block[0]) * (N // block[1]) * (N // block[2])
-    keys = torch.empty(n, dtype=torch.int32, device=dev) if keys is None else keys
-    perm = torch.empty(n, dtype=torch.int32, device=dev) if perm is None else perm
-    offsets = torch.empty(nb + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
-    st = ctypes.c_void_p(stream) if stream is not None else _stream_ptr()
-    _check(load_library().tracker_bin_static(n, _ptr(pos), int(N), float(L), int(block[0]), int(block[1]),
-                                             int(block[2]), _ptr(keys), _ptr(perm), _ptr(offsets), _ptr(nonfinite),
-                                             st))
+    keys, perm, offsets = _bin_outputs(dev, n, nb, keys, perm, offsets)
+    if nonfinite is not None:
+        _dev(nonfinite, torch.int32, "nonfinite", device=dev, min_numel=1)
+    with torch.cuda.device(dev):
+        st = ctypes.c_void_p(stream) if stream is not None else _stream_ptr(dev)
+        _check(load_library().tracker_bin_static(n, _ptr(pos), int(N), float(L), int(block[0]), int(block[1]),
+                                                 int(block[2]), _ptr(keys), _ptr(perm), _ptr(offsets),
+                                                 _ptr(nonfinite), st))
     return keys, perm, offsets
 
 
@@ -358,16 +386,22 @@ def tracker_adjoint(h, pos0, lambdaT, dt, steps, ckpt_every=5, grad_pos0=None, g
 class Tracker:
     """One tracker handle: an N^3 periodic grid with a kernel (family, I, m) and a field."""
 
-    def __init__(self, N, L=2 * math.pi, family=TRK_SPLINE, I=6, m=None, storage=TRK_F32):
+    def __init__(self, N, L=2 * math.pi, family=TRK_SPLINE, I=6, m=None, storage=TRK_F32, device=None):
         if m is None:
             m = I // 2 - 1 if family == TRK_SPLINE else 0
         self.N, self.L, self.family, self.I, self.m, self.storage = N, L, family, I, m, storage
         self.C = 0
-        self.h = tracker_create(N, L, family, I, m, storage)
+        # every call runs with this device current (the library checks it)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.field_generation = 0     # bumped by every set_field (autograd checks it)
+        self.h = None
+        with torch.cuda.device(self.device):
+            self.h = tracker_create(N, L, family, I, m, storage, stream=_stream_ptr(self.device).value)
 
     def close(self):
         if self.h is not None:
-            tracker_destroy(self.h)
+            tracker_destroy(self.h)   # the library switches to the tracker's device itself
             self.h = None
 
     def __del__(self):
@@ -383,12 +417,17 @@ class Tracker:
         self.close()
 
     def _stream(self):
-        tracker_set_stream(self.h)
+        tracker_set_stream(self.h, _stream_ptr(self.device).value)
+
+    def _on_device(self):
+        return torch.cuda.device(self.device)
 
     def set_field(self, field):
-        self._stream()
-        tracker_set_field(self.h, field)
+        with self._on_device():
+            self._stream()
+            tracker_set_field(self.h, field)
         self.C = int(field.shape[0])
+        self.field_generation += 1
 
     def set_step_kernel(self, kind):
         """TRK_STEP_AUTO, _BLOCK, _COLUMN or _DIRECT (see tracker_set_step_kernel)."""
@@ -424,27 +463,33 @@ class Tracker:
         return pos, rhs, info
 
     def bin(self, pos):
-        self._stream()
-        return tracker_bin(self.h, pos)
+        with self._on_device():
+            self._stream()
+            return tracker_bin(self.h, pos)
 
     def interpolate(self, pos, out_dtype=torch.float32, deriv=False, out=None):
-        self._stream()
-        return tracker_interpolate(self.h, pos, self.C, out=out, out_dtype=out_dtype, deriv=deriv)
+        with self._on_device():
+            self._stream()
+            return tracker_interpolate(self.h, pos, self.C, out=out, out_dtype=out_dtype, deriv=deriv)
 
     def advance(self, pos, dt, steps, scheme=TRK_RK2, rhs=None, history_valid=False):
-        self._stream()
-        return tracker_advance(self.h, pos, dt, steps, scheme, rhs, history_valid)
+        with self._on_device():
+            self._stream()
+            return tracker_advance(self.h, pos, dt, steps, scheme, rhs, history_valid)
 
     def advance_batched(self, sets, dt, steps, history_valid=False):
-        self._stream()
-        tracker_advance_batched(self.h, sets, dt, steps, history_valid)
+        with self._on_device():
+            self._stream()
+            tracker_advance_batched(self.h, sets, dt, steps, history_valid)
 
     def adjoint(self, pos0, lambdaT, dt, steps, ckpt_every=5, grad_field=None):
-        self._stream()
-        return tracker_adjoint(self.h, pos0, lambdaT, dt, steps, ckpt_every, grad_field=grad_field)
+        with self._on_device():
+            self._stream()
+            return tracker_adjoint(self.h, pos0, lambdaT, dt, steps, ckpt_every, grad_field=grad_field)
 
     def sync(self):
-        tracker_sync(self.h)
+        with self._on_device():
+            tracker_sync(self.h)
 
     @property
     def launch_count(self):

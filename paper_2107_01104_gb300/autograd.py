@@ -16,17 +16,24 @@ import torch
 class TrackerAdvect(torch.autograd.Function):
     @staticmethod
     def forward(ctx, pos0, field, tracker, dt, steps, ckpt_every):
-        tracker.set_field(field.detach().contiguous())
+        f = field.detach().contiguous()
+        tracker.set_field(f)
         posT = pos0.detach().clone().contiguous()
         tracker.advance(posT, dt, steps)
         ctx.tracker, ctx.dt, ctx.steps, ctx.ckpt = tracker, float(dt), int(steps), int(ckpt_every)
         ctx.field_shape, ctx.field_dtype = tuple(field.shape), field.dtype
+        # the field this graph was advanced in: another advect() or set_field on
+        # the same tracker before backward replaces the tracker's copy
+        ctx.field, ctx.field_generation = f, tracker.field_generation
         ctx.save_for_backward(pos0)
         return posT
 
     @staticmethod
     def backward(ctx, grad_posT):
         (pos0,) = ctx.saved_tensors
+        if ctx.tracker.field_generation != ctx.field_generation:
+            ctx.tracker.set_field(ctx.field)
+            ctx.field_generation = ctx.tracker.field_generation
         gfield = None
         if ctx.needs_input_grad[1]:
             gfield = torch.zeros(ctx.field_shape, dtype=torch.float64, device=pos0.device)

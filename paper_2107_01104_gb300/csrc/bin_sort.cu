@@ -5,12 +5,13 @@
 //
 // The paper orders particles by x3 slice with an incomplete quicksort and
 // keeps an offset[] array of group starts.  Here the groups are blocks of
-// cells.  tracker_bin and the block-kernel steps use a stable radix sort, so
-// the permutation is unique and reproducible (ties keep the incoming order).
-// The column-kernel steps re-bin with a counting sort (block counts from the
-// update phase, one scan, one scatter of the state): the blocks and their
-// offsets are the same, the order inside a block is not reproducible, and no
-// result depends on it.
+// cells.  tracker_bin (and tracker_bin_static) use a stable radix sort, so the
+// permutation is unique and reproducible (ties keep the incoming order).
+// Everything else re-bins with a counting sort: block counts (from the update
+// phase of a step, or from the keys), one scan, then one scatter of either the
+// particle state (time steps) or a permutation (interpolation, the adjoint,
+// batched sets).  The blocks and their offsets are those of the stable sort;
+// the order inside a block is not reproducible, and no result depends on it.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -244,6 +245,45 @@ __global__ void k_scatter_state(int64_t np, const uint32_t* __restrict__ keys, i
     for (int r = 0; r < rhs_rows; ++r) rhs_out[r * np + d] = rhs_in[r * np + j];
 }
 
+// Counting-sort permutation: perm[d] = j, d the next free slot of particle
+// j's block (cursor from the count scan).  Warp-aggregated like
+// k_scatter_state; the order inside a block follows the atomics.  Used where
+// every particle's result is independent of that order (interpolation, the
+// adjoint, batched sets): the blocks and their offsets are those of the
+// stable sort.
+__global__ void k_scatter_perm(int64_t np, const uint32_t* __restrict__ keys, int32_t* __restrict__ cursor,
+                               int32_t* __restrict__ perm, int* flags)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned valid = __ballot_sync(0xffffffffu, j < np);
+    if (j >= np) return;
+    const uint32_t key = keys[j];
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(valid, key);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cursor + key, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int64_t d = (int64_t)base + __popc(peers & ((1u << lane) - 1u));
+    if (d < 0 || d >= np) {
+        atomicOr(flags + FLAG_BINNING, 1);
+        return;
+    }
+    perm[d] = (int32_t)j;
+}
+
+// Block counts of np keys, one atomic add per group of equal keys in a warp
+// (keys written by a step kernel arrive grouped by the previous binning).
+__global__ void k_count_keys(int64_t np, const uint32_t* __restrict__ keys, uint32_t* __restrict__ counts)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned valid = __ballot_sync(0xffffffffu, j < np);
+    if (j >= np) return;
+    const uint32_t key = keys[j];
+    const unsigned peers = __match_any_sync(valid, key);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(counts + key, (uint32_t)__popc(peers));
+}
+
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
                              uint32_t* __restrict__ tile_hist)
 {
@@ -392,13 +432,21 @@ cudaError_t scan_exclusive(uint32_t* data, int64_t len, uint32_t* scratch, cudaS
     return cudaGetLastError();
 }
 
+// offsets[b] = first sorted position whose key is >= b (b = 0 .. nblocks): a
+// binary search per block over the sorted keys, grid-stride, so the work is
+// spread over all threads whatever the gaps between occupied blocks.
 __global__ void k_offsets(const uint32_t* __restrict__ keys, int64_t n, int64_t nblocks, int32_t* __restrict__ offsets)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > n) return;
-    const int64_t prev = (i == 0) ? -1 : (int64_t)keys[i - 1];
-    const int64_t cur = (i == n) ? nblocks : (int64_t)keys[i];
-    for (int64_t b = prev + 1; b <= cur; ++b) offsets[b] = (int32_t)i;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nblocks;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n;   // lower bound of b in keys[0, n)
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)keys[mid] < b) lo = mid + 1;
+            else hi = mid;
+        }
+        offsets[b] = (int32_t)lo;
+    }
 }
 
 __global__ void k_unpermute_pos(int64_t np, const double* __restrict__ src, const int32_t* __restrict__ id,
@@ -579,7 +627,23 @@ cudaError_t radix_sort(const uint32_t* keys, int64_t n, int bits, uint32_t* keys
 
 cudaError_t launch_offsets(const uint32_t* keys_sorted, int64_t n, int64_t nblocks, int32_t* offsets, cudaStream_t st)
 {
-    k_offsets<<<grid_for(n + 1, 256), 256, 0, st>>>(keys_sorted, n, nblocks, offsets);
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(nblocks + 1, 256), 152 * 64);
+    k_offsets<<<grid, 256, 0, st>>>(keys_sorted, n, nblocks, offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_perm(int64_t np, const uint32_t* keys, int32_t* cursor, int32_t* perm, int* flags,
+                                cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_scatter_perm<<<grid_for(np, 256), 256, 0, st>>>(np, keys, cursor, perm, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_keys(int64_t np, const uint32_t* keys, uint32_t* counts, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_count_keys<<<grid_for(np, 256), 256, 0, st>>>(np, keys, counts);
     return cudaGetLastError();
 }
 

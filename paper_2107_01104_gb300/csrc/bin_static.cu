@@ -79,7 +79,26 @@ int ilog2_ceil(int64_t x)
 
 bool pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 
+int check_dev_ptr(const void* p, int dev, const char* name)
+{
+    if (!p || device_pointer_ok(p, dev)) return TRK_OK;
+    char msg[160];
+    snprintf(msg, sizeof(msg), "tracker_bin_static: %s must be device memory of the current device %d", name, dev);
+    return fail(TRK_EINVAL, msg);
+}
+
 }  // namespace
+
+bool trk::device_pointer_ok(const void* p, int dev)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
 
 extern "C" {
 
@@ -99,6 +118,12 @@ int tracker_bin_static(int64_t np, const double* pos, int N, double L, int bx, i
     unsigned char* s = nullptr;
     int rc = scratch_for_current_device(&s);
     if (rc) return rc;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if ((rc = check_dev_ptr(np > 0 ? pos : nullptr, dev, "pos")) || (rc = check_dev_ptr(keys, dev, "keys")) ||
+        (rc = check_dev_ptr(np > 0 ? perm : nullptr, dev, "perm")) || (rc = check_dev_ptr(offsets, dev, "offsets")) ||
+        (rc = check_dev_ptr(nonfinite, dev, "nonfinite")))
+        return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
     GridGeom g{};

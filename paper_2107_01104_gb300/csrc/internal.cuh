@@ -260,6 +260,10 @@ cudaError_t launch_batched(int storage, const BatchSet* sets, int nsets, int* ct
 // Sets the thread-local message returned by tracker_last_error().
 void set_error_message(const char* msg);
 
+// True if p points into memory of device dev (or managed memory): the check
+// the binning entry points make on caller arrays that their kernels write.
+bool device_pointer_ok(const void* p, int dev);
+
 // Block kernels, one entry per kernel width I (block_i4.cu, block_i6.cu, block_i8.cu).
 // deg_hi selects the degree-(I+1) instantiation (spline with m = I/2).
 cudaError_t launch_column_i4(int mode, const ColumnArgs& ca, int deg_hi, int nsm, cudaStream_t st);
@@ -273,6 +277,11 @@ cudaError_t launch_keys_count(const GridGeom& g, int64_t np, const double* pos, 
 size_t count_scan_scratch_bytes(int64_t nblocks);
 cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offsets, int32_t* cursor,
                               uint32_t* scratch, cudaStream_t st, int64_t* launches);
+// counting-sort permutation of keys (cursor from launch_count_scan): perm[d] = j
+cudaError_t launch_scatter_perm(int64_t np, const uint32_t* keys, int32_t* cursor, int32_t* perm, int* flags,
+                                cudaStream_t st);
+// counts[key] += number of particles with that key
+cudaError_t launch_count_keys(int64_t np, const uint32_t* keys, uint32_t* counts, cudaStream_t st);
 cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,
                                  const int32_t* id_in, const float* rhs_in, int rhs_rows, double* pos_out,
                                  int32_t* id_out, float* rhs_out, int* flags, cudaStream_t st);

@@ -86,8 +86,9 @@ struct GraphCache {
 // Per-set buffers of tracker_advance_batched.
 struct SetState {
     int64_t cap = 0;
+    int64_t nb = 0;                   // block count the per-block arrays were sized for
     uint32_t* keys = nullptr;
-    uint32_t* keys_sorted = nullptr;
+    uint32_t* counts = nullptr;       // [nblocks] block counts of the next binning (zero between binnings)
     int32_t* perm = nullptr;
     int32_t* offsets = nullptr;
     int32_t* list = nullptr;
@@ -108,6 +109,7 @@ uint64_t mix(uint64_t h, uint64_t v)
 void trk::set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
 
 struct tracker {
+    int device = -1;                  // CUDA device the tracker's buffers live on (current at create)
     int N = 0;
     double L = 0;
     int family = 0, I = 0, m = 0, storage = 0;
@@ -124,7 +126,8 @@ struct tracker {
     size_t nm_bytes = 0;
     bool nm_valid = false;
     // sort scratch
-    int64_t sort_cap = 0;
+    int64_t sort_cap = 0;             // keys, perm
+    int64_t radix_cap = 0;            // sort_scratch, keys_sorted (stable binning)
     void* sort_scratch = nullptr;
     uint32_t* keys = nullptr;
     uint32_t* keys_sorted = nullptr;
@@ -161,6 +164,7 @@ struct tracker {
     std::vector<std::pair<uint64_t, int>> interp_cache; // (np, C, deriv, out dtype) -> interpolation kernel
     int last_kernel = TRK_STEP_AUTO;  // kernel of the latest tracker_advance or tracker_interpolate
     int* d_colctr = nullptr;          // work counter of the column kernel
+    int col_seg = 8;                  // column kernel: x3 slabs per work item (power of two)
     uint32_t* d_counts = nullptr;     // [nblocks] block counts (counting-sort binning of the column path)
     int32_t* d_cursor = nullptr;      // [nblocks] scatter cursors
     uint32_t* d_scan_tmp = nullptr;   // tile sums of the multi-CTA count scan
@@ -237,25 +241,39 @@ int set_geometry(tracker* t, int bx, int by, int bz)
     return TRK_OK;
 }
 
+// keys and permutation of np particles (every binning)
 int ensure_sort(tracker* t, int64_t np)
 {
     if (np <= t->sort_cap) return TRK_OK;
     t->gen += 1;
-    dev_free(t->sort_scratch);
     dev_free(t->keys);
-    dev_free(t->keys_sorted);
     dev_free(t->perm);
-    t->sort_scratch = nullptr;
-    t->keys = t->keys_sorted = nullptr;
+    t->keys = nullptr;
     t->perm = nullptr;
     t->sort_cap = 0;
-    if (dev_alloc(&t->sort_scratch, radix_scratch_bytes(np)) != cudaSuccess ||
-        dev_alloc(&t->keys, (size_t)np * 4) != cudaSuccess || dev_alloc(&t->keys_sorted, (size_t)np * 4) != cudaSuccess ||
-        dev_alloc(&t->perm, (size_t)np * 4) != cudaSuccess) {
+    if (dev_alloc(&t->keys, (size_t)np * 4) != cudaSuccess || dev_alloc(&t->perm, (size_t)np * 4) != cudaSuccess) {
         cudaGetLastError();
-        return fail(TRK_ENOMEM, "cannot allocate sort scratch for %lld particles", (long long)np);
+        return fail(TRK_ENOMEM, "cannot allocate binning buffers for %lld particles", (long long)np);
     }
     t->sort_cap = np;
+    return TRK_OK;
+}
+
+// radix-sort scratch and sorted keys of the stable binning (tracker_bin only)
+int ensure_radix(tracker* t, int64_t np)
+{
+    if (np <= t->radix_cap) return TRK_OK;
+    dev_free(t->sort_scratch);
+    dev_free(t->keys_sorted);
+    t->sort_scratch = nullptr;
+    t->keys_sorted = nullptr;
+    t->radix_cap = 0;
+    if (dev_alloc(&t->sort_scratch, radix_scratch_bytes(np)) != cudaSuccess ||
+        dev_alloc(&t->keys_sorted, (size_t)np * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TRK_ENOMEM, "cannot allocate radix-sort scratch for %lld particles", (long long)np);
+    }
+    t->radix_cap = np;
     return TRK_OK;
 }
 
@@ -324,18 +342,46 @@ cudaError_t launch_direct(tracker* t, int mode, const BlockArgs& a)
     }
 }
 
-// keys (caller order) -> sorted keys, perm, offsets (offsets may be NULL: the
-// direct path needs only the permutation)
+// Stable binning (tracker_bin): keys (caller order) -> sorted keys, perm, offsets.
 int bin_into(tracker* t, int64_t np, const double* pos, uint32_t* keys, int32_t* perm, int32_t* offsets)
 {
     ProfScope ps(t, PROF_BIN);
     CUDA_TRY(launch_keys(t->g, np, pos, keys, t->d_flags, t->stream));
     t->launches += 1;
     CUDA_TRY(radix_sort(keys, np, t->key_bits, t->keys_sorted, perm, t->sort_scratch, t->stream, &t->launches));
-    if (offsets) {
-        CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, offsets, t->stream));
-        t->launches += 1;
+    CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, offsets, t->stream));
+    t->launches += 1;
+    return TRK_OK;
+}
+
+// Counting-sort binning of interpolation and the adjoint: keys and block
+// counts from the positions, offsets and cursors from one scan, then the
+// permutation t->perm (grouped by block; the order inside a block is not
+// reproducible, and every particle's result is independent of it).
+int bin_counting(tracker* t, int64_t np, const double* pos)
+{
+    ProfScope ps(t, PROF_BIN);
+    CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
+    CUDA_TRY(launch_keys_count(t->g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
+    CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->d_scan_tmp, t->stream,
+                               &t->launches));
+    CUDA_TRY(launch_scatter_perm(np, t->keys, t->d_cursor, t->perm, t->d_flags, t->stream));
+    t->launches += 2;
+    return TRK_OK;
+}
+
+// Every call that launches work or allocates must run with the tracker's
+// device current: its buffers live there, and a launch on another device
+// would hand that device foreign pointers.
+int check_device(const tracker* t)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TRK_ECUDA, "no current CUDA device");
     }
+    if (dev != t->device)
+        return fail(TRK_EINVAL, "the tracker lives on CUDA device %d but device %d is current", t->device, dev);
     return TRK_OK;
 }
 
@@ -414,6 +460,9 @@ int replay_graph(tracker* t, GraphCache& gc, uint64_t key, int reps, F&& body)
     CUDA_TRY(cudaStreamWaitEvent(user, t->gev[1], 0));
     return TRK_OK;
 }
+
+// slabs per column-kernel work item: the tracker's setting, at most the column height
+int column_segment(const tracker* t) { return std::max(1, std::min(t->g.nb3, t->col_seg)); }
 
 bool column_available(const tracker* t)
 {
@@ -551,55 +600,30 @@ int step_path(const tracker* t, int64_t np)
 }
 
 // One RK2/ABk step of tracker_advance: re-bin, then the fused step kernel.
-// Column and direct paths: counting-sort binning (block counts from the
-// previous step's update or from the initial keys, scan, scatter of the
-// state into its blocks), then the column kernel, or the direct kernel (PB
-// grouped particles per CTA, stencils gathered from global memory), updating
-// the grouped state in place and counting the new keys.  Block path: stable
-// radix sort, then the block kernel reading through perm.  first: read the
-// caller's arrays (identity ids).  AB steps: order k = ab_order, `hist` valid
-// history entries for this step.
+// Every path re-bins with the counting sort: block counts (from the previous
+// step's update phase, or from the initial keys), one scan giving the offsets
+// and cursors, one scatter of the particle state into its blocks.  Then the
+// column kernel, the block kernel (one CTA per cell block), or the direct
+// kernel (PB grouped particles per CTA, stencils gathered from global
+// memory) updates the grouped state in place and counts the new keys.
+// first: read the caller's arrays (identity ids).  AB steps: order
+// k = ab_order, `hist` valid history entries for this step.
 int advance_step(tracker* t, int64_t np, int path, int mode, int ab_order, int hist, double dt, int cur, bool first,
                  const double* pos, const float* rhs)
 {
-    const bool col = path == TRK_STEP_COLUMN || path == TRK_STEP_DIRECT;   // counting-sort binning
     const int nxt = cur ^ 1;
     const bool ab = mode == MODE_AB2;
     {
         ProfScope ps(t, PROF_BIN);
-        if (col) {
-            const float* rin = ab && hist > 0 ? (first ? rhs : t->rhs_s[cur]) : nullptr;
-            CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->d_scan_tmp, t->stream,
-                                       &t->launches));
-            CUDA_TRY(launch_scatter_state(np, t->keys, t->d_cursor, first ? pos : t->pos_s[cur],
-                                          first ? nullptr : t->id_s[cur], rin, 3 * (ab_order - 1),
-                                          t->pos_s[nxt], t->id_s[nxt], t->rhs_s[nxt], t->d_flags, t->stream));
-            t->launches += 1;
-        } else {
-            CUDA_TRY(radix_sort(t->keys, np, t->key_bits, t->keys_sorted, t->perm, t->sort_scratch, t->stream,
-                                &t->launches));
-            if (path == TRK_STEP_BLOCK) {
-                CUDA_TRY(launch_offsets(t->keys_sorted, np, t->nblocks, t->offsets, t->stream));
-                t->launches += 1;
-            }
-        }
+        const float* rin = ab && hist > 0 ? (first ? rhs : t->rhs_s[cur]) : nullptr;
+        CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->d_scan_tmp, t->stream,
+                                   &t->launches));
+        CUDA_TRY(launch_scatter_state(np, t->keys, t->d_cursor, first ? pos : t->pos_s[cur],
+                                      first ? nullptr : t->id_s[cur], rin, 3 * (ab_order - 1), t->pos_s[nxt],
+                                      t->id_s[nxt], t->rhs_s[nxt], t->d_flags, t->stream));
+        t->launches += 1;
     }
-    if (path == TRK_STEP_DIRECT) {
-        BlockArgs a = base_args(t);
-        a.np = np;
-        a.dt = dt;
-        a.perm = nullptr;   // the state is grouped: read and written at j
-        a.pos_in = a.pos_out = t->pos_s[nxt];
-        a.id_in = a.id_out = t->id_s[nxt];
-        a.rhs_in = a.rhs_out = t->rhs_s[nxt];
-        a.history_valid = ab ? hist : 0;
-        a.ab_order = ab_order;
-        a.key_out = t->keys;
-        a.counts = t->d_counts;
-        CUDA_TRY(launch_direct(t, mode, a));
-        return TRK_OK;
-    }
-    if (col) {
+    if (path == TRK_STEP_COLUMN) {
         ColumnArgs ca{};
         ca.a = base_args(t);
         ca.a.np = np;
@@ -609,7 +633,7 @@ int advance_step(tracker* t, int64_t np, int path, int mode, int ab_order, int h
         ca.a.key_out = t->keys;
         ca.a.history_valid = ab ? hist : 0;
         ca.a.ab_order = ab_order;
-        ca.nseg = std::min(t->g.nb3, 8);
+        ca.nseg = column_segment(t);
         ca.nitems = (int64_t)t->g.nb1 * t->g.nb2 * (t->g.nb3 / ca.nseg);
         ca.ctr = t->d_colctr;
         ca.counts = t->d_counts;
@@ -622,24 +646,17 @@ int advance_step(tracker* t, int64_t np, int path, int mode, int ab_order, int h
     }
     BlockArgs a = base_args(t);
     a.np = np;
-    a.perm = t->perm;
     a.dt = dt;
-    if (first) {
-        a.pos_in = pos;
-        a.id_in = nullptr;
-        a.rhs_in = rhs;
-    } else {
-        a.pos_in = t->pos_s[cur];
-        a.id_in = t->id_s[cur];
-        a.rhs_in = t->rhs_s[cur];
-    }
+    a.perm = nullptr;   // the state is grouped: read and written at j
+    a.pos_in = a.pos_out = t->pos_s[nxt];
+    a.id_in = a.id_out = t->id_s[nxt];
+    a.rhs_in = a.rhs_out = t->rhs_s[nxt];
     a.history_valid = ab ? hist : 0;
     a.ab_order = ab_order;
-    a.pos_out = t->pos_s[nxt];
-    a.id_out = t->id_s[nxt];
-    a.rhs_out = t->rhs_s[nxt];
     a.key_out = t->keys;
-    CUDA_TRY(launch_block(t, mode, a));
+    a.counts = t->d_counts;
+    if (path == TRK_STEP_DIRECT) CUDA_TRY(launch_direct(t, mode, a));
+    else CUDA_TRY(launch_block(t, mode, a));
     return TRK_OK;
 }
 
@@ -675,6 +692,11 @@ int tracker_create(tracker** out, int N, double L, int family, int I, int m, int
         return fail(TRK_ECUDA, "no CUDA device");
     }
     tracker* t = new tracker();
+    if (cudaGetDevice(&t->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete t;
+        return fail(TRK_ECUDA, "no current CUDA device");
+    }
     t->N = N;
     t->L = L;
     t->family = family;
@@ -715,6 +737,10 @@ int tracker_create(tracker** out, int N, double L, int family, int I, int m, int
 int tracker_destroy(tracker* t)
 {
     if (!t) return TRK_OK;
+    // release the buffers on the device that holds them, then restore the caller's device
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) cudaGetLastError();
+    if (t->device >= 0 && cur != t->device) cudaSetDevice(t->device);
     if (t->stream) cudaStreamSynchronize(t->stream);
     else cudaDeviceSynchronize();
     dev_free(t->field);
@@ -735,7 +761,7 @@ int tracker_destroy(tracker* t)
     if (t->adv_graph.exec) cudaGraphExecDestroy(t->adv_graph.exec);
     if (t->batch_graph.exec) cudaGraphExecDestroy(t->batch_graph.exec);
     for (SetState& ss : t->sets) {
-        for (void* p : {(void*)ss.keys, (void*)ss.keys_sorted, (void*)ss.perm, (void*)ss.offsets, (void*)ss.list,
+        for (void* p : {(void*)ss.keys, (void*)ss.counts, (void*)ss.perm, (void*)ss.offsets, (void*)ss.list,
                         (void*)ss.count, (void*)ss.pos_s[0], (void*)ss.pos_s[1], (void*)ss.id_s[0], (void*)ss.id_s[1],
                         (void*)ss.rhs_s[0], (void*)ss.rhs_s[1]})
             dev_free(p);
@@ -753,6 +779,7 @@ int tracker_destroy(tracker* t)
     if (t->gev[1]) cudaEventDestroy(t->gev[1]);
     if (t->gstream) cudaStreamDestroy(t->gstream);
     for (cudaEvent_t e : t->ev_pool) cudaEventDestroy(e);
+    if (cur >= 0 && cur != t->device) cudaSetDevice(cur);
     delete t;
     return TRK_OK;
 }
@@ -760,6 +787,7 @@ int tracker_destroy(tracker* t)
 int tracker_profile(tracker* t, int enable)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     if (enable) {
         CUDA_TRY(cudaStreamSynchronize(t->stream));
         t->ev_used = 0;
@@ -775,6 +803,7 @@ int tracker_profile(tracker* t, int enable)
 int tracker_profile_read(tracker* t, double* ms, int64_t* launches)
 {
     if (!t || !ms || !launches) return fail(TRK_EINVAL, "NULL argument");
+    if (int rc_dev = check_device(t)) return rc_dev;
     CUDA_TRY(cudaStreamSynchronize(t->stream));
     for (int c = 0; c < 3; ++c) {
         double tot = 0;
@@ -799,6 +828,7 @@ int tracker_set_stream(tracker* t, void* stream)
 int tracker_sync(tracker* t)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     CUDA_TRY(cudaStreamSynchronize(t->stream));
     int h[NUM_FLAGS];
     CUDA_TRY(cudaMemcpy(h, t->d_flags, sizeof(h), cudaMemcpyDeviceToHost));
@@ -812,6 +842,7 @@ int tracker_sync(tracker* t)
 int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src_on_host)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     if (!src) return fail(TRK_EINVAL, "src is NULL");
     if (C < 1 || C > 16) return fail(TRK_EINVAL, "C=%d outside [1, 16]", C);
     if (src_dtype != TRK_DTYPE_F64 && src_dtype != TRK_DTYPE_F32) return fail(TRK_EINVAL, "unknown src_dtype %d", src_dtype);
@@ -856,6 +887,7 @@ int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src
 int tracker_set_block(tracker* t, int bx, int by, int bz)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     return set_geometry(t, bx, by, bz);
 }
 
@@ -897,11 +929,16 @@ int64_t tracker_launch_count(const tracker* t) { return t ? t->launches : -1; }
 int tracker_bin(tracker* t, int64_t np, const double* pos, int32_t* keys, int32_t* perm, int32_t* offsets)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     int rc = check_np(np);
     if (rc) return rc;
     if (np > 0 && (!pos || !perm)) return fail(TRK_EINVAL, "pos and perm must not be NULL");
     if (!offsets) return fail(TRK_EINVAL, "offsets must not be NULL");
-    if ((rc = ensure_sort(t, np))) return rc;
+    for (const void* p : {(const void*)(np > 0 ? pos : nullptr), (const void*)keys, (const void*)(np > 0 ? perm : nullptr),
+                          (const void*)offsets})
+        if (p && !device_pointer_ok(p, t->device))
+            return fail(TRK_EINVAL, "tracker_bin: every array must be device memory of the tracker's device %d", t->device);
+    if ((rc = ensure_sort(t, np)) || (rc = ensure_radix(t, np))) return rc;
     uint32_t* k = keys ? reinterpret_cast<uint32_t*>(keys) : t->keys;
     return bin_into(t, np, pos, k, perm, offsets);
 }
@@ -909,6 +946,7 @@ int tracker_bin(tracker* t, int64_t np, const double* pos, int32_t* keys, int32_
 int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, int out_dtype, int deriv)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     int rc = check_np(np);
     if (rc) return rc;
     if (!t->field) return fail(TRK_ENOFIELD, "no field set");
@@ -938,7 +976,7 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     if (np == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
     if ((direct || probe) && (rc = ensure_node_major(t))) return rc;
-    if ((rc = bin_into(t, np, pos, t->keys, t->perm, direct && !probe ? nullptr : t->offsets))) return rc;
+    if ((rc = bin_counting(t, np, pos))) return rc;
     BlockArgs a = base_args(t);
     a.np = np;
     a.perm = t->perm;
@@ -979,6 +1017,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
                     int history_valid)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     int rc = check_np(np);
     if (rc) return rc;
     if (!t->field) return fail(TRK_ENOFIELD, "no field set");
@@ -1018,15 +1057,11 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     if ((rc = ensure_sort(t, np))) return rc;
     if ((rc = ensure_state(t, np))) return rc;
     if ((path == TRK_STEP_DIRECT || probe) && (rc = ensure_node_major(t))) return rc;
-    // initial keys from the caller's positions (with block counts on the column path)
+    // initial keys and block counts from the caller's positions
     {
         ProfScope ps(t, PROF_BIN);
-        if (path == TRK_STEP_COLUMN || path == TRK_STEP_DIRECT) {
-            CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
-            CUDA_TRY(launch_keys_count(t->g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
-        } else {
-            CUDA_TRY(launch_keys(t->g, np, pos, t->keys, t->d_flags, t->stream));
-        }
+        CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
+        CUDA_TRY(launch_keys_count(t->g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
         t->launches += 1;
     }
     // the first step reads the caller's arrays; the others ping-pong between
@@ -1115,14 +1150,15 @@ static cudaError_t launch_adjoint(tracker* t, const AdjArgs& a)
 
 static int ensure_set(tracker* t, SetState& ss, int64_t np)
 {
-    if (np <= ss.cap) return TRK_OK;
+    if (np <= ss.cap && ss.nb == t->nblocks) return TRK_OK;
     t->gen += 1;
-    for (void* p : {(void*)ss.keys, (void*)ss.keys_sorted, (void*)ss.perm, (void*)ss.offsets, (void*)ss.list,
+    for (void* p : {(void*)ss.keys, (void*)ss.counts, (void*)ss.perm, (void*)ss.offsets, (void*)ss.list,
                     (void*)ss.count, (void*)ss.pos_s[0], (void*)ss.pos_s[1], (void*)ss.id_s[0], (void*)ss.id_s[1],
                     (void*)ss.rhs_s[0], (void*)ss.rhs_s[1]})
         dev_free(p);
     ss = SetState{};
-    bool ok = dev_alloc(&ss.keys, (size_t)np * 4) == cudaSuccess && dev_alloc(&ss.keys_sorted, (size_t)np * 4) == cudaSuccess &&
+    bool ok = dev_alloc(&ss.keys, (size_t)np * 4) == cudaSuccess &&
+              dev_alloc(&ss.counts, (size_t)t->nblocks * 4) == cudaSuccess &&
               dev_alloc(&ss.perm, (size_t)np * 4) == cudaSuccess &&
               dev_alloc(&ss.offsets, (size_t)(t->nblocks + 1) * 4) == cudaSuccess &&
               dev_alloc(&ss.list, (size_t)t->nblocks * 4) == cudaSuccess && dev_alloc(&ss.count, 4) == cudaSuccess;
@@ -1134,15 +1170,31 @@ static int ensure_set(tracker* t, SetState& ss, int64_t np)
         return fail(TRK_ENOMEM, "cannot allocate the buffers of a particle set (%lld particles)", (long long)np);
     }
     ss.cap = np;
+    ss.nb = t->nblocks;
     return TRK_OK;
 }
 
-// Re-binning of one set: sorted keys, permutation, offsets, and (halo path) the non-empty block list.
+// Initial keys and block counts of one set from positions in the caller's order.
+static int keys_set(tracker* t, SetState& ss, int64_t np, const double* pos)
+{
+    ProfScope ps(t, PROF_BIN);
+    CUDA_TRY(cudaMemsetAsync(ss.counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
+    CUDA_TRY(launch_keys_count(t->g, np, pos, ss.keys, ss.counts, t->d_flags, t->stream));
+    t->launches += 1;
+    return TRK_OK;
+}
+
+// Re-binning of one set by counting sort: the block counts (from keys_set, or
+// added by the previous step's kernel) scanned into offsets and cursors (the
+// counts are left zero), the permutation, and (halo path) the non-empty block
+// list.  The cursors and scan scratch are the tracker's, shared by the sets,
+// which are binned one after another on the stream.
 static int bin_set(tracker* t, SetState& ss, int64_t np, bool direct)
 {
     ProfScope ps(t, PROF_BIN);
-    CUDA_TRY(radix_sort(ss.keys, np, t->key_bits, ss.keys_sorted, ss.perm, t->sort_scratch, t->stream, &t->launches));
-    CUDA_TRY(launch_offsets(ss.keys_sorted, np, t->nblocks, ss.offsets, t->stream));
+    CUDA_TRY(launch_count_scan(ss.counts, t->nblocks, ss.offsets, t->d_cursor, t->d_scan_tmp, t->stream,
+                               &t->launches));
+    CUDA_TRY(launch_scatter_perm(np, ss.keys, t->d_cursor, ss.perm, t->d_flags, t->stream));
     t->launches += 1;
     if (!direct) CUDA_TRY(launch_nonempty_list(ss.offsets, t->nblocks, ss.list, ss.count, t->ne_scratch, t->stream,
                                                &t->launches));
@@ -1162,6 +1214,7 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
 {
     history_valid = history_valid ? 1 : 0;   // AB2: one history entry, valid or not
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     if (nsets < 0 || (nsets > 0 && !sets)) return fail(TRK_EINVAL, "bad set list");
     if (!t->field) return fail(TRK_ENOFIELD, "no field set");
     if (t->C != 3) return fail(TRK_EINVAL, "batched advection needs a 3-component field (C=%d)", t->C);
@@ -1188,7 +1241,6 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
         npmax = std::max(npmax, S.np);
     }
     if (nsets == 0 || steps == 0 || npmax == 0) return TRK_OK;
-    if ((rc = ensure_sort(t, npmax))) return rc;
     if ((int)t->sets.size() < nsets) t->sets.resize(nsets);
     for (int s = 0; s < nsets; ++s)
         if ((rc = ensure_set(t, t->sets[s], std::max<int64_t>(sets[s].np, 1)))) return rc;
@@ -1235,6 +1287,7 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
         a.offsets = ss.offsets;
         a.dt = dt;
         a.key_out = ss.keys;
+        a.counts = ss.counts;
         a.out = S.out;
         for (int v = 0; v < 3; ++v) {
             BatchSet& B = h[(size_t)v * nsets + s];
@@ -1280,7 +1333,7 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
             SetState& ss = t->sets[s];
             const size_t vb = (size_t)S.np * 24;
             CUDA_TRY(cudaMemcpyAsync(ss.pos_s[1], S.pos, vb, cudaMemcpyDeviceToDevice, t->stream));
-            CUDA_TRY(launch_keys(t->g, S.np, ss.pos_s[1], ss.keys, t->d_flags, t->stream));
+            if ((rc = keys_set(t, ss, S.np, ss.pos_s[1]))) return rc;
             if ((rc = bin_set(t, ss, S.np, false))) return rc;
             BatchSet probe = h[(size_t)nsets + s];           // parity-0 layout: reads pos_s[0] ...
             probe.a.pos_in = ss.pos_s[1];                     // ... so point it at the copy
@@ -1320,8 +1373,8 @@ int tracker_advance_batched(tracker* t, int nsets, const trk_set* sets, double d
         for (int s = 0; s < nsets; ++s) {
             if (sets[s].np == 0) continue;
             if (v == 0) {
-                CUDA_TRY(launch_keys(t->g, sets[s].np, sets[s].pos, t->sets[s].keys, t->d_flags, t->stream));
-                t->launches += 1;
+                int r = keys_set(t, t->sets[s], sets[s].np, sets[s].pos);
+                if (r) return r;
             }
             int r = bin_set(t, t->sets[s], sets[s].np, direct[s]);
             if (r) return r;
@@ -1364,6 +1417,7 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
                     int ckpt_every, double* grad_pos0, double* grad_field)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (int rc_dev = check_device(t)) return rc_dev;
     int rc = check_np(np);
     if (rc) return rc;
     if (!t->field) return fail(TRK_ENOFIELD, "no field set");
@@ -1446,7 +1500,7 @@ int tracker_adjoint(tracker* t, int64_t np, const double* pos0, const double* la
         }
         for (int i = s1 - s0 - 1; i >= 0; --i) {
             const double* X = seg + (size_t)i * vec;
-            if ((rc = bin_into(t, np, X, t->keys, t->perm, t->offsets))) return rc;
+            if ((rc = bin_counting(t, np, X))) return rc;
             AdjArgs a{};
             const BlockArgs b = base_args(t);
             a.g = b.g;
