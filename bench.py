@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "block", "column", "direct"],
-                    help="step kernel of the headline workload (default: the column kernel)")
+                    help="step kernel of the headline workload (default: auto, the tracker's timed choice)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (precision, batching, differentiation, small, sparse)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6],
                     help="2: the headline workload (default); 1 small, 3 precision, 4 batching, 5 adjoint, "
                          "6 the paper's sparse tracer density")
@@ -143,14 +145,17 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # helpers
 # --------------------------------------------------------------------------
-def field_and_particles():
+def field_and_particles(with_f64=False):
+    """The headline workload's float32 field and tracers (and the float64 field
+    the float32 one was rounded from, for the error against the truth)."""
     import numpy as np
 
     import synth
 
-    field = synth.velocity_field_np(N, KMAX, SEED_FIELD).astype(np.float32)
+    f64 = synth.velocity_field_np(N, KMAX, SEED_FIELD)
+    field = f64.astype(np.float32)
     pos = synth.uniform_particles_np(NP, SEED_POS)
-    return field, pos
+    return (field, pos, f64) if with_f64 else (field, pos)
 
 
 STEP_KERNELS = {"column": ("k_column<6,5,RK2> (float32 field)", "k_column_rk2_f32_i6",
@@ -278,7 +283,99 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
-# GB300 arm
+# GB300 arm: timing helpers
+# --------------------------------------------------------------------------
+def _events():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def timed(fn, stream, dev_index, min_s=0.5, max_reps=50, min_reps=3):
+    """ms per call of fn, timed with CUDA events on `stream` over enough calls to
+    last about min_s (sized from one untimed call), with the SM clocks sampled
+    by nvidia-smi during the timed calls: (ms, reps, clocks)."""
+    import torch
+
+    e0, e1 = _events()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    one = max(e0.elapsed_time(e1), 1e-3)
+    reps = int(min(max_reps, max(min_reps, math.ceil(min_s * 1e3 / one))))
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    time.sleep(0.15)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, reps, clocks.stop()
+
+
+def profiled(tr, trk, fn, reps=1):
+    """Device time per call of each kernel class of tracker tr over `reps`
+    calls of fn (event-bracketed launches; the tracker replays no CUDA graph
+    while it records): {'step'|'bin'|'other': (ms per call, launches per call)}."""
+    import torch
+
+    torch.cuda.synchronize()
+    trk.tracker_profile(tr.h, True)
+    for _ in range(reps):
+        fn()
+    prof = trk.tracker_profile_read(tr.h)
+    trk.tracker_profile(tr.h, False)
+    return {k: (v[0] / reps, v[1] / reps) for k, v in prof.items()}
+
+
+def hbm_roofline(alg_bytes, kernel_ms, label, alg_def, **extra):
+    """HBM roofline of one kernel launch (or one call's kernels): algorithmic
+    bytes over device time against the measured copy bandwidth."""
+    peak, kind = measured_peaks()
+    ach = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    d = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "kernel": label,
+         "alg_bytes": alg_bytes, "kernel_ms": kernel_ms, "alg_def": alg_def, "peak_kind": kind}
+    d.update(extra)
+    return d
+
+
+def fma_bound(fmas, kernel_ms, fma_per_s, what):
+    """FMA-bound fraction: the contraction's FMAs over device time against the probed FMA rate."""
+    ach = fmas / (kernel_ms * 1e-3)
+    return {"achieved_fma_per_s": ach, "peak_fma_per_s": fma_per_s, "frac": ach / fma_per_s,
+            "fmas": fmas, "peak_def": f"tracker_probe_fma ({what}) on this GPU, same run"}
+
+
+def kernel_name(trk, tr):
+    return {trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_COLUMN: "column",
+            trk.TRK_STEP_DIRECT: "direct"}.get(tr.last_step_kernel(), "?")
+
+
+def interp_error(trk, tr, field64, pos_sample, I_, M_, family=None):
+    """Interpolated u at a tracer sample against the oracle on the float64
+    field (the truth): max and rms error over the field rms."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    family = trk.TRK_SPLINE if family is None else family
+    p = torch.from_numpy(np.ascontiguousarray(pos_sample)).cuda()
+    got = tr.interpolate(p, out_dtype=torch.float64).cpu().numpy()
+    ref = oracle.interp(field64, pos_sample, family, I_, M_)
+    rms = float(np.sqrt(np.mean(field64 ** 2)))
+    d = got - ref
+    return {"max_err_over_rms": float(np.abs(d).max()) / rms, "rms_err_over_rms": float(np.sqrt(np.mean(d ** 2))) / rms,
+            "vs": "oracle on the float64 field", "sample": int(pos_sample.shape[1])}
+
+
+FMA_RK2_I6 = 2 * 3 * (I ** 3 + I ** 2 + I)    # separable contraction, two stages, three components
+
+
+# --------------------------------------------------------------------------
+# GB300 arm: the headline workload
 # --------------------------------------------------------------------------
 def run_gb300(args):
     import numpy as np
@@ -296,13 +393,14 @@ def run_gb300(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    dev_index = torch.cuda.current_device()
     if rank == 0:
         lib_build.build()
     if ws > 1:
         dist.barrier()
     trk.load_library()
 
-    field, pos = field_and_particles()
+    field, pos, field64 = field_and_particles(with_f64=True)
     tr = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
     tr.set_step_kernel({"auto": trk.TRK_STEP_AUTO, "block": trk.TRK_STEP_BLOCK,
                         "column": trk.TRK_STEP_COLUMN, "direct": trk.TRK_STEP_DIRECT}[args.step_kernel])
@@ -322,12 +420,12 @@ def run_gb300(args):
     sync_flags(tr, trk, notes)
 
     # ---------------- device-timed region (the step pairs replay from CUDA graphs) ----------------
-    clocks = ClockSampler(torch.cuda.current_device())
+    clocks = ClockSampler(dev_index)
     barrier_sync()
     clocks.start()
     time.sleep(0.2)
     launches0 = tr.launch_count
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events()
     e0.record(stream)
     for _ in range(args.steps):
         tr.advance(p, DT, args.inner, trk.TRK_RK2)
@@ -341,16 +439,9 @@ def run_gb300(args):
     value = job_value(NP * args.inner * args.steps, ws, ms)
 
     # ---------------- per-kernel times: a separate, profiled pass ----------------
-    # (tracker_profile records events around every launch, which turns the
-    # graph replay off; the headline value above is not taken from it)
     psteps = max(1, min(args.steps, 3))
     barrier_sync()
-    trk.tracker_profile(tr.h, True)
-    for _ in range(psteps):
-        tr.advance(p, DT, args.inner, trk.TRK_RK2)
-    barrier_sync()
-    prof = trk.tracker_profile_read(tr.h)
-    trk.tracker_profile(tr.h, False)
+    prof = profiled(tr, trk, lambda: tr.advance(p, DT, args.inner, trk.TRK_RK2), reps=psteps)
     sync_flags(tr, trk, notes)
 
     # ---------------- roofline of the step kernel ----------------
@@ -360,8 +451,7 @@ def run_gb300(args):
     alg_bytes = field_bytes + 52 * NP                 # field once + fp64 positions read and written + key
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    kind = {trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_COLUMN: "column",
-            trk.TRK_STEP_DIRECT: "direct"}[tr.last_step_kernel()]
+    kind = kernel_name(trk, tr)
     kernel_label = STEP_KERNELS[kind][0]
     if kind == "direct":   # node loads through the texture object (three quarters of the rows) or plain loads
         notes["direct_node_loads"] = "texture" if tr.field_texture() else "plain"
@@ -371,15 +461,29 @@ def run_gb300(args):
     sm_mhz = clk.get("sm_mhz") or 1900.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     smem_peak = nsm * 128 * sm_mhz * 1e6 / 1e9
-    # separable contraction: per stage and component I^3 + I^2 + I FMAs (x1 sums, then x2, then x3)
-    fma_per_ps = 2 * 3 * (I ** 3 + I ** 2 + I)
-    fp32_peak = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s, FP32 SIMT FMA
+    fma32 = trk.tracker_probe_fma(trk.TRK_DTYPE_F32)
+    fma64 = trk.tracker_probe_fma(trk.TRK_DTYPE_F64)
+
+    # ---------------- error of the timed form against the oracle ----------------
+    rng = np.random.default_rng(0)
+    sample = rng.choice(NP, 4096, replace=False)
+    error = interp_error(trk, tr, field64, pos[:, sample], I, M)
+    import oracle
+
+    few = sample[:256]
+    q = torch.from_numpy(np.ascontiguousarray(pos[:, few])).to(dev)
+    tr.advance(q, DT, args.inner, trk.TRK_RK2)
+    ref = oracle.advance(field.astype(np.float64), pos[:, few], DT, args.inner, oracle.SPLINE, I, M)
+    error["positions_after_one_step_call"] = {
+        "max_abs_err": float(np.abs(q.cpu().numpy() - ref).max()), "rk2_steps": args.inner, "sample": len(few),
+        "vs": "oracle on the stored float32 values (same input)", "cell_width": 2 * math.pi / N}
+    sync_flags(tr, trk, notes)
 
     # ---------------- end-to-end through the public API ----------------
     host = torch.from_numpy(pos).pin_memory()
     back = torch.empty_like(host).pin_memory()
     barrier_sync()
-    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0, w1 = _events()
     w0.record(stream)
     for _ in range(args.steps):
         p.copy_(host, non_blocking=True)
@@ -393,46 +497,22 @@ def run_gb300(args):
            "h2d_bytes_per_step": host.numel() * 8,
            "d2h_bytes_per_step": back.numel() * 8}
 
-    # ---------------- other precision forms of the same workload ----------------
+    # ---------------- other forms of the same workload ----------------
     variants = {}
     if not args.no_variants:
-        for name, storage, inner in (("f64", trk.TRK_F64, 5), ("bf16x2", trk.TRK_BF16X2, args.inner)):
-            tv = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=M, storage=storage)
-            tv.set_field(torch.from_numpy(field).to(dev))
-            pv = torch.from_numpy(pos).to(dev)
-            tv.advance(pv, DT, 1, trk.TRK_RK2)
-            torch.cuda.synchronize()
-            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            v0.record(stream)
-            reps = 2
-            for _ in range(reps):
-                tv.advance(pv, DT, inner, trk.TRK_RK2)
-            v1.record(stream)
-            torch.cuda.synchronize()
-            vms = v0.elapsed_time(v1)
-            variants[name] = {"value": NP * inner * reps / (vms * 1e-3), "unit": UNIT, "rk2_steps": inner * reps}
-            tv.close()
-        # Adams-Bashforth of orders 2 and 4 (one field evaluation per step), f32 field,
-        # history already full when the timed steps start
-        for name, scheme in (("ab2", trk.TRK_AB2), ("ab4", trk.TRK_AB4)):
-            k = scheme + 1
-            pv = torch.from_numpy(pos).to(dev)
-            hist = torch.zeros((k - 1, 3, NP), dtype=torch.float32, device=dev)
-            tr.advance(pv, DT, k - 1, scheme, rhs=hist, history_valid=0)
-            tr.advance(pv, DT, args.inner, scheme, rhs=hist, history_valid=k - 1)
-            torch.cuda.synchronize()
-            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 2
-            v0.record(stream)
-            for _ in range(reps):
-                tr.advance(pv, DT, args.inner, scheme, rhs=hist, history_valid=k - 1)
-            v1.record(stream)
-            torch.cuda.synchronize()
-            vms = v0.elapsed_time(v1)
-            variants[name] = {"value": NP * args.inner * reps / (vms * 1e-3), "unit": UNIT,
-                              "ab_steps": args.inner * reps, "field_storage": "f32"}
-            del pv, hist
-        variants["sparse_1024"] = sparse_variant(trk, dev, stream, measured_peaks())
+        variants.update(precision_variants(trk, dev, stream, dev_index, field, field64, pos, sample, fma64, args))
+        variants.update(ab_variants(trk, tr, dev, stream, dev_index, pos, args))
+    tr.close()
+    del p, host, back
+    torch.cuda.empty_cache()
+
+    configs = {}
+    if not args.no_configs and ws == 1:
+        for name, fn in (("1_small_plain", config1_block), ("3_precision", config3_block),
+                         ("4_batching", config4_block), ("5_differentiation", config5_block),
+                         ("6_sparse_paper_density", config6_block)):
+            configs[name] = fn(trk, dev, stream, dev_index, args, {"fp32": fma32, "fp64": fma64})
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -452,296 +532,382 @@ def run_gb300(args):
                          "l2_hit_rate": ncu_record(sha, kind).get("l2_hit_rate"),
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                          "launches_timed": step_n, "peak_kind": peak_kind, "source_sha": sha},
-            "fma_roofline": {"achieved": NP * fma_per_ps * 2 / avg_launch_s / 1e12, "peak": fp32_peak,
-                             "unit": "TFLOP/s", "frac": NP * fma_per_ps * 2 / avg_launch_s / 1e12 / fp32_peak,
-                             "fma_per_particle_step": fma_per_ps,
-                             "peak_def": "SMs x 128 FP32 FMA/clk x 2 FLOP x median SM clock under load"},
+            "fma_roofline": {**fma_bound(NP * FMA_RK2_I6, avg_launch_s * 1e3, fma32, "float32"),
+                             "fma_per_particle_step": FMA_RK2_I6},
             "smem_roofline": {"achieved": gather_bytes / avg_launch_s / 1e9, "peak": smem_peak, "unit": "GB/s",
                               "frac": gather_bytes / avg_launch_s / 1e9 / smem_peak,
                               "gather_bytes_per_launch": gather_bytes,
                               "path": "shared memory" if kind != "direct" else
-                              ("L1 (gathers: texture and load/store data paths)" if tr.field_texture()
-                               else "L1 (global gathers)"),
+                              ("L1 (gathers: texture and load/store data paths)" if notes.get("direct_node_loads") ==
+                               "texture" else "L1 (global gathers)"),
                               "peak_def": "SMs x 128 B/clk (the L1 / shared-memory data path) x median SM clock under load"},
-            "phase_ms_per_step": {"step_kernel": step_ms / psteps, "binning": prof["bin"][0] / psteps,
-                                  "other": prof["other"][0] / psteps, "profiled_steps": psteps,
+            "phase_ms_per_step": {"step_kernel": step_ms / args.inner, "binning": prof["bin"][0] / args.inner,
+                                  "other": prof["other"][0] / args.inner, "profiled_calls": psteps,
                                   "note": "event-bracketed launches without graph replay"},
-            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "variants": variants, "notes": notes,
-            "cpu_baseline": cpu,
+            "error": error,
+            "fma_peaks_probed": {"fp32_fma_per_s": fma32, "fp64_fma_per_s": fma64,
+                                 "fp64_fma_per_clk_per_sm": fma64 / (nsm * sm_mhz * 1e6),
+                                 "fp32_fma_per_clk_per_sm": fma32 / (nsm * sm_mhz * 1e6)},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "variants": variants, "configs": configs,
+            "notes": notes, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    tr.close()
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
 
 
+def precision_variants(trk, dev, stream, dev_index, field, field64, pos, sample, fma64, args):
+    """The headline workload with the field stored as float64 (the paper's
+    plain form) and as split-bf16 pairs: rate, HBM roofline of the step kernel,
+    FMA-bound fraction (float64), error against the oracle, clocks."""
+    import torch
+
+    out = {}
+    for name, storage, inner, esz in (("f64", trk.TRK_F64, 10, 8), ("bf16x2", trk.TRK_BF16X2, args.inner, 4)):
+        tv = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=M, storage=storage)
+        tv.set_field(torch.from_numpy(field64 if storage == trk.TRK_F64 else field).to(dev))
+        pv = torch.from_numpy(pos).to(dev)
+        for _ in range(3):
+            tv.advance(pv, DT, inner, trk.TRK_RK2)
+        ms, reps, clk = timed(lambda: tv.advance(pv, DT, inner, trk.TRK_RK2), stream, dev_index, min_s=0.8)
+        prof = profiled(tv, trk, lambda: tv.advance(pv, DT, inner, trk.TRK_RK2))
+        kms = prof["step"][0] / inner
+        alg = 3 * N ** 3 * esz + 52 * NP
+        d = {"value": NP * inner / (ms * 1e-3), "unit": UNIT, "rk2_steps_per_call": inner, "calls_timed": reps,
+             "kernel": kernel_name(trk, tv), "step_kernel_ms": kms, "binning_ms": prof["bin"][0] / inner,
+             "roofline": hbm_roofline(alg, kms, kernel_name(trk, tv), f"field 3 N^3 x {esz} B + 52 B per particle-step"),
+             "error": interp_error(trk, tv, field64, pos[:, sample], I, M), "clocks": clk}
+        if storage == trk.TRK_F64:
+            d["fma_roofline"] = {**fma_bound(NP * FMA_RK2_I6, kms, fma64, "float64"),
+                                 "fma_per_particle_step": FMA_RK2_I6}
+        out[name] = d
+        tv.close()
+        del pv
+        torch.cuda.empty_cache()
+    return out
+
+
+def ab_variants(trk, tr, dev, stream, dev_index, pos, args):
+    """Adams-Bashforth of orders 2 and 4 (one field evaluation per step) on the
+    headline tracker, history full when the timed calls start."""
+    import torch
+
+    out = {}
+    for name, scheme in (("ab2", trk.TRK_AB2), ("ab4", trk.TRK_AB4)):
+        k = scheme + 1
+        pv = torch.from_numpy(pos).to(dev)
+        hist = torch.zeros((k - 1, 3, NP), dtype=torch.float32, device=dev)
+        tr.advance(pv, DT, k - 1, scheme, rhs=hist, history_valid=0)
+        call = lambda: tr.advance(pv, DT, args.inner, scheme, rhs=hist, history_valid=k - 1)  # noqa: E731
+        call()
+        ms, reps, clk = timed(call, stream, dev_index, min_s=0.8)
+        prof = profiled(tr, trk, call)
+        kms = prof["step"][0] / args.inner
+        alg = 3 * N ** 3 * 4 + NP * (52 + 24 * (k - 1))
+        out[name] = {"value": NP * args.inner / (ms * 1e-3), "unit": UNIT, "ab_steps_per_call": args.inner,
+                     "calls_timed": reps, "field_storage": "f32", "kernel": kernel_name(trk, tr),
+                     "step_kernel_ms": kms, "binning_ms": prof["bin"][0] / args.inner,
+                     "roofline": hbm_roofline(alg, kms, kernel_name(trk, tr),
+                                              f"field once + 52 B + {24 * (k - 1)} B history per particle-step"),
+                     "clocks": clk}
+        del pv, hist
+    return out
+
+
 # --------------------------------------------------------------------------
-# other configurations (single GPU; one JSON line each, same keys)
+# the other configurations (single GPU)
 # --------------------------------------------------------------------------
-def sparse_variant(trk, dev, stream, peaks):
-    """The paper's production density, 1.5e-3 tracers per grid cell, on a 1024^3
-    float32 field (spline I = 6, RK2): the automatic choice is the direct path.
-    Its roofline counts, per particle and stage, one stencil of I^3 nodes x 3
-    components x 4 B (no overlap between stencils at this density) plus 52 B of
-    particle state per step."""
+def config1_block(trk, dev, stream, dev_index, args, fma):
+    """32^3 float64 field |k| <= 8, 1e4 tracers, Lagrange I=4: interpolation and
+    one RK2 step dt=1e-3 per call (launch-bound small case), against the oracle."""
+    import numpy as np
     import torch
 
-    import synth
-
-    Ns, ns = 1024, int(1.5e-3 * 1024 ** 3)
-    dt = DT * 256 / Ns                      # the same CFL number as the 256^3 workload
-    field = synth.velocity_field_torch(Ns, Ns // 3, 1006, device=dev, out_dtype=torch.float32)
-    tv = trk.Tracker(Ns, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
-    tv.set_field(field)
-    del field
-    kernel = tv.step_kernel_for(ns)
-    pv = torch.from_numpy(synth.uniform_particles_np(ns, 7)).to(dev)
-    steps = 20
-    tv.advance(pv, dt, steps, trk.TRK_RK2)
-    torch.cuda.synchronize()
-    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    v0.record(stream)
-    tv.advance(pv, dt, steps, trk.TRK_RK2)
-    v1.record(stream)
-    torch.cuda.synchronize()
-    ms = v0.elapsed_time(v1) / steps
-    alg = ns * (2 * I ** 3 * 3 * 4 + 52)
-    tv.close()
-    del pv
-    torch.cuda.empty_cache()
-    gbs = alg / (ms * 1e-3) / 1e9
-    return {"value": ns / (ms * 1e-3), "unit": UNIT, "N": Ns, "np": ns, "per_cell": 1.5e-3, "scheme": "RK2",
-            "kernel": {trk.TRK_STEP_DIRECT: "direct", trk.TRK_STEP_COLUMN: "column",
-                       trk.TRK_STEP_BLOCK: "block"}[kernel],
-            "ms_per_step": ms, "dt": dt, "alg_bytes_per_step": alg, "achieved_gbs": gbs, "hbm_frac": gbs / peaks[0],
-            "note": "whole step incl. binning; alg bytes = 2 stencils x I^3 x 3 x 4 B + 52 B state per particle"}
-
-
-def _events():
-    import torch
-
-    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-
-def _line(metric, value, unit, args, ms_step, workload, extra, dtype="f32", hib=True):
-    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-         "ms_per_step": ms_step, "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-         "data": "synthetic", "config": {"workload": workload}}
-    d.update(extra)
-    print(json.dumps(d), flush=True)
-
-
-def run_config1(args):
-    """32^3 float64 field |k| <= 8, 1e4 tracers, Lagrange I=4, one RK2 step (launch-bound small case)."""
-    import torch
-
-    import paper_2107_01104_gb300 as trk
+    import oracle
     import synth
 
     field = synth.velocity_field_np(32, 8, 1000)
     pos = synth.uniform_particles_np(10_000, 1)
     t = trk.Tracker(32, family=trk.TRK_LAGRANGE, I=4, storage=trk.TRK_F64)
-    t.set_field(torch.from_numpy(field).cuda())
-    p0 = torch.from_numpy(pos).cuda()
+    t.set_field(torch.from_numpy(field).to(dev))
+    p0 = torch.from_numpy(pos).to(dev)
+    u = t.interpolate(p0, out_dtype=torch.float64)
+    p1 = p0.clone()
+    t.advance(p1, 1e-3, 1)
+    t.sync()
+    err_u = float(np.abs(u.cpu().numpy() - oracle.interp(field, pos, oracle.LAGRANGE, 4, 0)).max())
+    err_x = float(np.abs(p1.cpu().numpy() - oracle.advance(field, pos, 1e-3, 1, oracle.LAGRANGE, 4, 0)).max())
     p = p0.clone()
-    for _ in range(args.warmup):
-        t.advance(p, 1e-3, 1)
-    e0, e1 = _events()
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.steps):
+
+    def call():
         t.interpolate(p, out_dtype=torch.float64)
         t.advance(p, 1e-3, 1)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    _line("particle-steps/s", 10_000 / (ms * 1e-3), "particle-steps/s", args, ms,
-          "32^3 f64 velocity |k|<=8, 1e4 tracers, Lagrange I=4, interpolate + one RK2 step dt=1e-3",
-          {"note": "launch-bound (about 13 kernels for 1e4 particles)"}, dtype="f64")
+
+    ms, reps, clk = timed(call, stream, dev_index, min_s=0.3, max_reps=200)
+    t.close()
+    return {"metric": "particle-steps/s", "value": 10_000 / (ms * 1e-3), "unit": "particle-steps/s",
+            "ms_per_call": ms, "calls_timed": reps, "dtype": "f64",
+            "workload": "32^3 f64 velocity |k|<=8, 1e4 tracers, Lagrange I=4, interpolate + one RK2 step dt=1e-3",
+            "error": {"u_max_abs": err_u, "x_max_abs": err_x, "vs": "oracle, same float64 field",
+                      "bar": "1e-12 x max|u| (u), 1e-13 (positions)"},
+            "roofline": None, "note": "launch-bound (a few kernels for 1e4 tracers): no roofline", "clocks": clk}
 
 
-def run_config3(args):
-    """1024^3, u (3) + grad u (9, spectral), float32 and split bf16 storage, 2^27 tracers, I = 8."""
+def config3_block(trk, dev, stream, dev_index, args, fma):
+    """1024^3, u (3) + grad u (9, spectral), float32 and split bf16 storage,
+    2^27 tracers, spline I = 8: interpolation rate, HBM roofline of the
+    interpolation kernel, FMA-bound fraction, error against the oracle on a
+    1e5-tracer subsample (the float64 field is made one component at a time
+    on the GPU and only the subsample's stencil nodes are gathered)."""
     import numpy as np
     import torch
 
     import oracle
-    import paper_2107_01104_gb300 as trk
     import synth
 
-    N, KM, NPART, NSUB, I8, M8 = 1024, 340, 1 << 27, 100_000, 8, 3
-    dev = torch.device("cuda")
+    N3, KM, NPART, NSUB, I8, M8 = 1024, 340, 1 << 27, 100_000, 8, 3
     pos = synth.uniform_particles_torch(NPART, 3, device=dev)
     sub = pos[:, :NSUB].cpu().numpy()
-    cell, frac = oracle.split(sub, N)
+    cell, frac = oracle.split(sub, N3)
     rel = np.arange(1 - I8 // 2, I8 // 2 + 1)
-    c1 = (cell[0][:, None] + rel[None, :]) % N
-    c2 = (cell[1][:, None] + rel[None, :]) % N
-    c3 = (cell[2][:, None] + rel[None, :]) % N
-    idx = ((c3[:, :, None, None] * N + c2[:, None, :, None]) * N + c1[:, None, None, :]).reshape(NSUB, -1)
+    c1 = (cell[0][:, None] + rel[None, :]) % N3
+    c2 = (cell[1][:, None] + rel[None, :]) % N3
+    c3 = (cell[2][:, None] + rel[None, :]) % N3
+    idx = ((c3[:, :, None, None] * N3 + c2[:, None, :, None]) * N3 + c1[:, None, None, :]).reshape(NSUB, -1)
     idx_t = torch.from_numpy(idx).to(dev)
-    f12 = torch.empty((12, N, N, N), dtype=torch.float32, device=dev)
-    stencil = np.empty((NSUB, 12, I8 ** 3), np.float64)
-    for i, comp in enumerate(synth.velocity_components_torch(N, KM, 1002, device=dev)):
+    f12 = torch.empty((12, N3, N3, N3), dtype=torch.float32, device=dev)
+    truth = np.empty((12, NSUB))
+    rms = np.empty(12)
+    t0 = time.perf_counter()
+    for i, comp in enumerate(synth.velocity_components_torch(N3, KM, 1002, device=dev)):
         f12[i] = comp.to(torch.float32)
-        stencil[:, i, :] = comp.reshape(-1)[idx_t].cpu().numpy()
+        rms[i] = float(torch.sqrt(torch.mean(comp * comp)))
+        st = comp.reshape(-1)[idx_t].cpu().numpy()
         del comp
+        truth[i] = oracle.interp_stencil(frac, st.reshape(NSUB, 1, I8, I8, I8), oracle.SPLINE, I8, M8)[0]
+    prep_s = time.perf_counter() - t0
     del idx_t
     torch.cuda.empty_cache()
-    truth = oracle.interp_stencil(frac, stencil.reshape(NSUB, 12, I8, I8, I8), oracle.SPLINE, I8, M8)
-    del stencil
-    rms_u = float(np.sqrt(np.mean(truth[:3] ** 2)))
-    rms_g = float(np.sqrt(np.mean(truth[3:] ** 2)))
-    results, roof = {}, None
-    peak, peak_kind = measured_peaks()
+    rms_u, rms_g = float(np.sqrt(np.mean(rms[:3] ** 2))), float(np.sqrt(np.mean(rms[3:] ** 2)))
+    out = {"workload": "1024^3 u (3) + grad u (9, spectral), |k|<=340, 2^27 uniform tracers (fp64 positions), "
+                       "spline I=8 m=3, interpolation; error vs the fp64 oracle on 1e5 tracers",
+           "metric": "particles/s", "unit": "particles/s", "prep_s": prep_s}
     for sname, storage in (("f32", trk.TRK_F32), ("bf16x2", trk.TRK_BF16X2)):
         for C in (3, 12):
-            t = trk.Tracker(N, family=trk.TRK_SPLINE, I=I8, m=M8, storage=storage)
+            t = trk.Tracker(N3, family=trk.TRK_SPLINE, I=I8, m=M8, storage=storage)
             t.set_field(f12[:C])
-            out = torch.empty((C, NPART), dtype=torch.float32, device=dev)
-            for _ in range(max(1, args.warmup)):
-                t.interpolate(pos, out=out)
-            torch.cuda.synchronize()
-            trk.tracker_profile(t.h, True)
-            e0, e1 = _events()
-            reps = max(1, min(args.steps, 3))
-            e0.record()
-            for _ in range(reps):
-                t.interpolate(pos, out=out)
-            e1.record()
-            torch.cuda.synchronize()
-            prof = trk.tracker_profile_read(t.h)
-            trk.tracker_profile(t.h, False)
-            ms = e0.elapsed_time(e1) / reps
-            err = out[:, :NSUB].double().cpu().numpy() - truth[:C]
+            o = torch.empty((C, NPART), dtype=torch.float32, device=dev)
+            call = lambda: t.interpolate(pos, out=o)  # noqa: E731
+            call()                                    # AUTO: times the block and the direct kernel once
+            ms, reps, clk = timed(call, stream, dev_index, min_s=0.6, max_reps=10)
+            prof = profiled(t, trk, call)
+            kms = prof["step"][0]
+            err = o[:, :NSUB].double().cpu().numpy() - truth[:C]
+            alg = C * N3 ** 3 * 4 + NPART * (24 + 4 * C)
+            fmas = NPART * C * (I8 ** 3 + I8 ** 2 + I8)
             key = f"{sname}_{'u' if C == 3 else 'u+grad'}"
-            results[key] = {"particles_per_s": NPART / (ms * 1e-3), "ms": ms,
-                            "kernel_ms": prof["step"][0] / reps, "binning_ms": prof["bin"][0] / reps,
-                            "rms_err_u_over_rms_u": float(np.sqrt(np.mean(err[:3] ** 2))) / rms_u}
+            kname = kernel_name(trk, t)
+            out[key] = {"value": NPART / (ms * 1e-3), "ms_per_call": ms, "calls_timed": reps, "kernel": kname,
+                        "kernel_ms": kms, "binning_ms": prof["bin"][0], "other_ms": prof["other"][0],
+                        "roofline": hbm_roofline(alg, kms, kname, f"field {C} N^3 x 4 B + (24 + 4 C) B per particle"),
+                        "fma_roofline": fma_bound(fmas, kms, fma["fp32"], "float32"),
+                        "error": {"u_rms_err_over_rms": float(np.sqrt(np.mean(err[:3] ** 2))) / rms_u,
+                                  "u_max_err_over_rms": float(np.abs(err[:3]).max()) / rms_u,
+                                  "vs": "oracle on the float64 field", "sample": NSUB},
+                        "clocks": clk}
             if C == 12:
-                results[key]["rms_err_grad_over_rms_grad"] = float(np.sqrt(np.mean(err[3:] ** 2))) / rms_g
-            if storage == trk.TRK_F32 and C == 3:
-                alg = 3 * N ** 3 * 4 + NPART * 36
-                ach = alg / (prof["step"][0] / reps * 1e-3) / 1e9
-                kname = {trk.TRK_STEP_DIRECT: "k_direct<float,8,7,INTERP,F32>",
-                         trk.TRK_STEP_BLOCK: "k_block<float,8,7,INTERP,F32>"}.get(t.last_step_kernel(), "?")
-                roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                        "traffic": None, "kernel": kname, "alg_bytes_per_launch": alg,
-                        "peak_kind": peak_kind}
-            results[key]["kernel"] = {trk.TRK_STEP_DIRECT: "direct", trk.TRK_STEP_BLOCK: "block"}.get(
-                t.last_step_kernel(), "?")
+                out[key]["error"]["grad_rms_err_over_rms"] = float(np.sqrt(np.mean(err[3:] ** 2))) / rms_g
+                out[key]["error"]["grad_max_err_over_rms"] = float(np.abs(err[3:]).max()) / rms_g
             t.close()
-            del out
+            del o
             torch.cuda.empty_cache()
-    head = results["f32_u"]
-    _line("particles/s", head["particles_per_s"], "particles/s", args, head["ms"],
-          "1024^3 u (3) + grad u (9, spectral), fp32 and split-bf16 storage, |k|<=340, 2^27 tracers, spline I=8 m=3,"
-          " interpolation; error vs the fp64 oracle on 1e5 tracers", {"results": results, "roofline": roof})
+    del f12, pos
+    torch.cuda.empty_cache()
+    out["value"] = out["f32_u"]["value"]
+    return out
 
 
-def run_config4(args):
-    """512^3 float32 u, 8 sets 1e3..2e7 tracers, I cycling 4/6/8, 3 or 9 outputs, 50 AB2 steps per call."""
+def config4_block(trk, dev, stream, dev_index, args, fma):
+    """512^3 float32 u, 8 sets 1e3 .. 2e7 tracers, I cycling 4/6/8, 3 or 9
+    outputs, 50 AB2 steps per call, one persistent launch per step."""
+    import numpy as np
     import torch
 
-    import paper_2107_01104_gb300 as trk
+    import oracle
     import synth
 
-    N, dt, steps = 512, 2e-3, 50
-    dev = torch.device("cuda")
-    u = synth.velocity_field_torch(N, 170, 1003, out_dtype=torch.float32)
-    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    N4, dt, steps = 512, 2e-3, 50
+    u = synth.velocity_field_torch(N4, 170, 1003, out_dtype=torch.float32)
+    t = trk.Tracker(N4, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
     t.set_field(u)
-    del u
     sizes = [1000, 10_000, 30_000, 100_000, 1_000_000, 3_000_000, 10_000_000, 20_000_000]
-    sets = []
+    pos0, sets = [], []
     for s, n in enumerate(sizes):
-        I = (4, 6, 8)[s % 3]
-        sets.append(dict(pos=synth.uniform_particles_torch(n, 10 + s, device=dev),
-                         rhs=torch.zeros((3, n), dtype=torch.float32, device=dev),
+        I_ = (4, 6, 8)[s % 3]
+        p0 = synth.uniform_particles_torch(n, 10 + s, device=dev)
+        pos0.append(p0)
+        sets.append(dict(pos=p0.clone(), rhs=torch.zeros((3, n), dtype=torch.float32, device=dev),
                          out=torch.zeros((9 if s % 2 else 3, n), dtype=torch.float32, device=dev),
-                         family=trk.TRK_SPLINE, I=I, m=I // 2 - 1, deriv=s % 2))
+                         family=trk.TRK_SPLINE, I=I_, m=I_ // 2 - 1, deriv=s % 2))
     total = sum(sizes)
-    for _ in range(args.warmup):
-        t.advance_batched(sets, dt, steps, history_valid=True)
-    torch.cuda.synchronize()
+    # error: one 50-step call from the initial positions, 16 tracers per set against the oracle
+    t.advance_batched(sets, dt, steps, history_valid=False)
+    try:
+        t.sync()
+    except trk.TrackerError as e:
+        if e.status != trk.TRK_ECFL:
+            raise
+    fs = u.double().cpu().numpy()
+    del u
+    rng = np.random.default_rng(0)
+    errs = []
+    for s, S in enumerate(sets):
+        ix = rng.choice(sizes[s], 16, replace=False)
+        x0 = pos0[s][:, ix].cpu().numpy()
+        ref, _ = oracle.advance(fs, x0, dt, steps, S["family"], S["I"], S["m"], scheme=oracle.AB2)
+        errs.append(float(np.abs(S["pos"][:, ix].cpu().numpy() - ref).max()))
+    del fs
+    call = lambda: t.advance_batched(sets, dt, steps, history_valid=True)  # noqa: E731
     l0 = t.launch_count
-    trk.tracker_profile(t.h, True)
-    trk.tracker_profile(t.h, False)   # graph replay stays on (profiling would disable it)
-    e0, e1 = _events()
-    e0.record()
-    for _ in range(args.steps):
-        t.advance_batched(sets, dt, steps, history_valid=True)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    _line("particle-steps/s", total * steps / (ms * 1e-3), "particle-steps/s", args, ms,
-          "512^3 fp32 u |k|<=170, 8 sets (1e3..2e7, sum 3.414e7), I cycling 4/6/8, 3- or 9-component outputs,"
-          " 50 AB2 steps per call, one persistent launch per step under a CUDA graph",
-          {"gpu_launches": t.launch_count - l0, "per_set_path": "direct or halo, chosen by timing"})
+    ms, reps, clk = timed(call, stream, dev_index, min_s=1.0, max_reps=5)
+    launches = (t.launch_count - l0) / (reps + 1)
+    prof = profiled(t, trk, call)
+    kms = prof["step"][0] / steps
+    outs = sum(n * (9 if s % 2 else 3) * 4 for s, n in enumerate(sizes))
+    alg = 3 * N4 ** 3 * 4 + total * 72 + outs
+    t.close()
+    del sets, pos0
+    return {"metric": "particle-steps/s", "value": total * steps / (ms * 1e-3), "unit": "particle-steps/s",
+            "ms_per_call": ms, "calls_timed": reps, "gpu_launches_per_call": launches,
+            "workload": "512^3 fp32 u |k|<=170, 8 sets (1e3..2e7, sum 3.414e7), I cycling 4/6/8, 3- or 9-component "
+                        "outputs, 50 AB2 steps per call, one persistent launch per step under a CUDA graph",
+            "step_kernel_ms": kms, "binning_ms_per_step": prof["bin"][0] / steps,
+            "roofline": hbm_roofline(alg, kms, "k_batched", "u field once (3 N^3 x 4 B) + 72 B per particle "
+                                     "(positions r/w 48, AB2 history r/w 24) + 4 B per output value, per step"),
+            "error": {"max_abs_pos_err_per_set": errs, "steps": steps, "sample_per_set": 16,
+                      "vs": "oracle AB2 on the stored float32 values (same input)"},
+            "clocks": clk}
 
 
-def run_config6(args):
-    """The paper's production density, 1.5e-3 tracers per grid cell, on an N^3
-    float32 field (default 1024^3), spline I = 6, 20 RK2 steps per call; the
-    automatic choice is the direct path.  Roofline of the step kernel in
-    algorithmic bytes: per particle and stage one stencil of I^3 x 3 x 4 B
-    (stencils do not overlap at this density) plus 52 B of particle state."""
+def config5_block(trk, dev, stream, dev_index, args, fma):
+    """256^3 float32 u, 2^22 tracers, spline I=6, 20 RK2 steps, loss sum |X_T|^2,
+    backward by the discrete adjoint with checkpoints every 5 steps: forward
+    and backward rates, each with the HBM roofline of its whole phase, and the
+    position gradient of a tracer sample against the oracle."""
+    import numpy as np
     import torch
 
-    import paper_2107_01104_gb300 as trk
+    import oracle
     import synth
 
-    Ns = args.sparse_n
+    N5, n, dt, steps = 256, 1 << 22, 5e-3, 20
+    field = synth.velocity_field_np(N5, 85, 1004).astype(np.float32)
+    t = trk.Tracker(N5, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    t.set_field(torch.from_numpy(field).to(dev))
+    p0 = synth.uniform_particles_torch(n, 5, device=dev)
+    gf = torch.zeros((3, N5, N5, N5), dtype=torch.float64, device=dev)
+    x = p0.clone()
+    lam = torch.empty_like(p0)
+
+    def fwd():
+        x.copy_(p0)
+        t.advance(x, dt, steps)
+
+    def bwd():
+        t.adjoint(p0, lam, dt, steps, 5, grad_field=gf)
+
+    fwd()
+    torch.mul(x, 2.0, out=lam)
+    gpos, _ = t.adjoint(p0, lam, dt, steps, 5, grad_field=gf)
+    try:
+        t.sync()
+    except trk.TrackerError as e:
+        if e.status != trk.TRK_ECFL:
+            raise
+    ix = np.random.default_rng(0).choice(n, 256, replace=False)
+    ps = p0[:, ix].cpu().numpy()
+    fs = field.astype(np.float64)
+    posT = oracle.advance(fs, ps, dt, steps, oracle.SPLINE, 6, 2)
+    gref, _ = oracle.adjoint_rk2(fs, ps, 2 * posT, dt, steps, oracle.SPLINE, 6, 2, with_field=False)
+    g = gpos.cpu().numpy()[:, ix]
+    rel_err = float(np.linalg.norm(g - gref) / np.linalg.norm(gref))
+    fms, freps, fclk = timed(fwd, stream, dev_index, min_s=0.6, max_reps=20)
+    bms, breps, bclk = timed(bwd, stream, dev_index, min_s=1.0, max_reps=10)
+    field_b = 3 * N5 ** 3 * 4
+    K = 5
+    nseg = (steps + K - 1) // K
+    # forward: one field sweep + 52 B per particle per step
+    f_alg = steps * (field_b + 52 * n)
+    # backward: the recomputed forward steps ((nseg - 1) K to lay the checkpoints, then
+    # steps - nseg inside the segments) and, per step, the adjoint sweep: field once,
+    # X (24 B), lambda in and out (48 B), and the float64 field gradient read and written
+    recomputed = (nseg - 1) * K + (steps - nseg)
+    b_alg = recomputed * (field_b + 52 * n) + steps * (field_b + 72 * n + 2 * 3 * N5 ** 3 * 8)
+    t.close()
+    return {"metric": "particle-steps/s", "value": n * steps / ((fms + bms) * 1e-3), "unit": "particle-steps/s",
+            "workload": "256^3 fp32 u |k|<=85, 2^22 tracers, spline I=6 m=2, 20 RK2 steps, loss sum |X_T|^2, "
+                        "backward by the discrete adjoint with checkpoints every 5 steps",
+            "forward": {"ms": fms, "calls_timed": freps, "particle_steps_per_s": n * steps / (fms * 1e-3),
+                        "roofline": hbm_roofline(f_alg, fms, "forward call (all kernels)",
+                                                 "per step: field once + 52 B per particle"),
+                        "clocks": fclk},
+            "backward": {"ms": bms, "calls_timed": breps, "particle_steps_per_s": n * steps / (bms * 1e-3),
+                         "roofline": hbm_roofline(b_alg, bms, "backward call (all kernels)",
+                                                  "recomputed forward steps + per step: field once, 72 B per particle, "
+                                                  "float64 field gradient read and written"),
+                         "clocks": bclk},
+            "error": {"grad_pos_rel_err": rel_err, "sample": len(ix), "bar": 1e-6,
+                      "vs": "oracle adjoint on the stored float32 values (same input)"}}
+
+
+def config6_block(trk, dev, stream, dev_index, args, fma, Ns=None):
+    """The paper's production density, 1.5e-3 tracers per grid cell, on a
+    1024^3 float32 field (spline I = 6, RK2, 20 steps per call): the automatic
+    choice is the direct path.  Roofline of the step kernel: per particle-step
+    one stencil of I^3 nodes x 3 components x 4 B (stencils of different
+    tracers do not overlap at this density; the stage-2 stencil is the same
+    cell's, or one cell away sharing all but I^2 of its nodes, so one stencil
+    is the compulsory part) plus 52 B of particle state."""
+    import torch
+
+    import synth
+
+    Ns = Ns or args.sparse_n
     ns, inner = int(1.5e-3 * Ns ** 3), 20
     dt = DT * 256 / Ns                      # the same CFL number as the 256^3 workload
-    dev = torch.device("cuda")
-    stream = torch.cuda.current_stream()
     field = synth.velocity_field_torch(Ns, Ns // 3, 1006, device=dev, out_dtype=torch.float32)
     t = trk.Tracker(Ns, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
     t.set_field(field)
     del field
-    kind = {trk.TRK_STEP_DIRECT: "direct", trk.TRK_STEP_COLUMN: "column",
-            trk.TRK_STEP_BLOCK: "block"}[t.step_kernel_for(ns)]
     p = synth.uniform_particles_torch(ns, 7, device=dev)
     notes = {"cfl_slow_path_used": False}
-    for _ in range(args.warmup):
-        t.advance(p, dt, inner, trk.TRK_RK2)
+    call = lambda: t.advance(p, dt, inner, trk.TRK_RK2)  # noqa: E731
+    for _ in range(2):
+        call()
     sync_flags(t, trk, notes)
+    kind = kernel_name(trk, t)
     if kind == "direct":
         notes["direct_node_loads"] = "texture" if t.field_texture() else "plain"
-    l0 = t.launch_count
-    e0, e1 = _events()
-    e0.record(stream)
-    for _ in range(args.steps):
-        t.advance(p, dt, inner, trk.TRK_RK2)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    launches = t.launch_count - l0
-    ms = e0.elapsed_time(e1) / (args.steps * inner)
-    trk.tracker_profile(t.h, True)
-    t.advance(p, dt, inner, trk.TRK_RK2)
-    torch.cuda.synchronize()
-    prof = trk.tracker_profile_read(t.h)
-    trk.tracker_profile(t.h, False)
+    ms, reps, clk = timed(call, stream, dev_index, min_s=0.6, max_reps=20)
+    prof = profiled(t, trk, call)
     sync_flags(t, trk, notes)
     step_ms, step_n = prof["step"]
-    launch_s = step_ms * 1e-3 / max(step_n, 1)
-    alg = ns * (2 * I ** 3 * 3 * 4 + 52)
-    peak, peak_kind = measured_peaks()
-    achieved = alg / launch_s / 1e9
+    launch_ms = step_ms / max(step_n, 1)
+    alg = ns * (I ** 3 * 3 * 4 + 52)
     rec = sparse_ncu_record(kind)
     per_particle = rec.get("dram_bytes_per_particle")
-    _line("particle-steps/s", ns / (ms * 1e-3), "particle-steps/s", args, ms * inner,
-          f"{Ns}^3 fp32 velocity |k|<={Ns // 3}, {ns} uniform tracers (1.5e-3 per cell, the paper's density), "
-          f"spline I={I} m={M}, {inner} RK2 steps dt={dt} per call, re-binned every step",
-          {"roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": per_particle * ns if per_particle else None, "kernel": kind,
-                        "l2_hit_rate": rec.get("l2_hit_rate"),
-                        "alg_bytes_per_launch": alg, "avg_launch_ms": launch_s * 1e3, "peak_kind": peak_kind,
-                        "alg_def": "2 stencils x I^3 x 3 x 4 B + 52 B state per particle-step"},
-           "phase_ms_per_step": {"step_kernel": step_ms / inner, "binning": prof["bin"][0] / inner},
-           "gpu_launches": launches, "notes": notes})
+    t.close()
+    del p
+    return {"metric": "particle-steps/s", "value": ns * inner / (ms * 1e-3), "unit": "particle-steps/s",
+            "workload": f"{Ns}^3 fp32 velocity |k|<={Ns // 3}, {ns} uniform tracers (1.5e-3 per cell, the paper's "
+                        f"density), spline I={I} m={M}, {inner} RK2 steps dt={dt} per call, re-binned every step",
+            "ms_per_step": ms / inner, "calls_timed": reps, "kernel": kind,
+            "roofline": hbm_roofline(alg, launch_ms, kind, "one stencil x I^3 x 3 x 4 B + 52 B state per particle-step",
+                                     traffic=per_particle * ns if per_particle else None,
+                                     l2_hit_rate=rec.get("l2_hit_rate")),
+            "phase_ms_per_step": {"step_kernel": step_ms / inner, "binning": prof["bin"][0] / inner},
+            "clocks": clk, "notes": notes}
 
 
 def sparse_ncu_record(kind):
@@ -760,47 +926,26 @@ def sparse_ncu_record(kind):
     return e
 
 
-def run_config5(args):
-    """256^3 float32 u, 2^22 tracers, spline I=6, 20 RK2 steps, adjoint with checkpoints every 5."""
-    import numpy as np
+def run_single_config(args):
+    """--config N: one configuration on its own, printed as one JSON line."""
     import torch
 
     import paper_2107_01104_gb300 as trk
-    import synth
+    from paper_2107_01104_gb300 import build as lib_build
 
-    N, n, dt, steps = 256, 1 << 22, 5e-3, 20
-    dev = torch.device("cuda")
-    field = synth.velocity_field_np(N, 85, 1004).astype(np.float32)
-    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
-    t.set_field(torch.from_numpy(field).to(dev))
-    p0 = synth.uniform_particles_torch(n, 5, device=dev)
-    gf = torch.zeros((3, N, N, N), dtype=torch.float64, device=dev)
-    x = p0.clone()
-    for _ in range(args.warmup):
-        x.copy_(p0)
-        t.advance(x, dt, steps)
-        t.adjoint(p0, 2 * x, dt, steps, 5, grad_field=gf)
-    torch.cuda.synchronize()
-    fwd = bwd = 0.0
-    for _ in range(args.steps):
-        x.copy_(p0)
-        a0, a1 = _events()
-        b1 = torch.cuda.Event(enable_timing=True)
-        a0.record()
-        t.advance(x, dt, steps)
-        a1.record()
-        t.adjoint(p0, 2 * x, dt, steps, 5, grad_field=gf)
-        b1.record()
-        torch.cuda.synchronize()
-        fwd += a0.elapsed_time(a1)
-        bwd += a1.elapsed_time(b1)
-    fwd /= args.steps
-    bwd /= args.steps
-    _line("particle-steps/s", n * steps / ((fwd + bwd) * 1e-3), "particle-steps/s", args, fwd + bwd,
-          "256^3 fp32 u |k|<=85, 2^22 tracers, spline I=6 m=2, 20 RK2 steps, loss sum |X_T|^2, backward by the"
-          " discrete adjoint (field scatter-add + position Jacobians) with checkpoints every 5 steps",
-          {"forward": {"ms": fwd, "particle_steps_per_s": n * steps / (fwd * 1e-3)},
-           "backward": {"ms": bwd, "particle_steps_per_s": n * steps / (bwd * 1e-3)}})
+    torch.cuda.set_device(0)
+    lib_build.build()
+    trk.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    fma = {"fp32": trk.tracker_probe_fma(trk.TRK_DTYPE_F32), "fp64": trk.tracker_probe_fma(trk.TRK_DTYPE_F64)}
+    fn = {1: config1_block, 3: config3_block, 4: config4_block, 5: config5_block, 6: config6_block}[args.config]
+    d = fn(trk, dev, stream, 0, args, fma)
+    line = {"metric": d.get("metric", METRIC), "value": d["value"], "unit": d.get("unit", UNIT), "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": d.get("dtype", "f32"), "data": "synthetic",
+            "config": {"workload": d.get("workload", f"config {args.config}")}, "result": d}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -810,13 +955,7 @@ def main():
     elif args.config == 2:
         run_gb300(args)
     else:
-        import torch
-
-        from paper_2107_01104_gb300 import build as lib_build
-
-        torch.cuda.set_device(0)
-        lib_build.build()
-        {1: run_config1, 3: run_config3, 4: run_config4, 5: run_config5, 6: run_config6}[args.config](args)
+        run_single_config(args)
 
 
 if __name__ == "__main__":
