@@ -73,6 +73,8 @@ typedef enum { TRK_DTYPE_F64 = 0, TRK_DTYPE_F32 = 1 } trk_dtype;
 
 typedef enum { TRK_STEP_AUTO = 0, TRK_STEP_BLOCK = 1, TRK_STEP_COLUMN = 2, TRK_STEP_DIRECT = 3 } trk_step_kernel;
 
+typedef enum { TRK_HALO_AUTO = 0, TRK_HALO_ASYNC = 1, TRK_HALO_TMA = 2 } trk_halo_copy;
+
 /* ---------------------------------------------------------------------- */
 /* Lifetime                                                                */
 /* ---------------------------------------------------------------------- */
@@ -242,6 +244,27 @@ int tracker_step_kernel_for(const tracker* t, int64_t np);
  * with, or the latest tracker_interpolate used (after any timing);
  * TRK_STEP_AUTO before the first call; negative status on error. */
 int tracker_last_step_kernel(const tracker* t);
+
+/* How the block kernel (TRK_STEP_BLOCK, and the block side of interpolation)
+ * stages each cell block's field halo in shared memory (the slab ghost
+ * layers of Sec. 3.3.1, per cell block):
+ *   TRK_HALO_ASYNC: cp.async copies of single elements (float32, float64) or
+ *     16-byte vector loads through registers (split bf16);
+ *   TRK_HALO_TMA: one tensor copy (cp.async.bulk.tensor) per chunk of three
+ *     components, issued by one thread and awaited on an mbarrier, into a
+ *     box padded so that the stencil loads meet few shared-memory bank
+ *     conflicts (float32 and float64 storage with at least three
+ *     components; elsewhere the cp.async staging is used);
+ *   TRK_HALO_AUTO (default): the choice of the tuner (tracker_advance's
+ *     first timed call), else TRK_HALO_ASYNC.
+ * Both give bit-identical results.  A tensor copy that does not complete
+ * within its wait limit skips its block and makes tracker_sync return
+ * TRK_ECUDA.  Errors: TRK_EINVAL. */
+int tracker_set_halo_copy(tracker* t, int kind);
+
+/* The halo copy (TRK_HALO_ASYNC or TRK_HALO_TMA) the block kernel uses now
+ * for interpolation and AB steps (mode 0) or RK2 steps (mode 1). */
+int tracker_halo_copy(const tracker* t, int mode);
 
 /* 1 if the direct kernel reads the node-major copy of the current field
  * through a texture object, 0 if by plain loads or if no copy has been made

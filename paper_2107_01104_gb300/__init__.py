@@ -32,6 +32,7 @@ TRK_F64, TRK_F32, TRK_BF16X2 = 0, 1, 2
 TRK_RK2, TRK_AB2, TRK_AB3, TRK_AB4 = 0, 1, 2, 3
 TRK_DTYPE_F64, TRK_DTYPE_F32 = 0, 1
 TRK_STEP_AUTO, TRK_STEP_BLOCK, TRK_STEP_COLUMN, TRK_STEP_DIRECT = 0, 1, 2, 3
+TRK_HALO_AUTO, TRK_HALO_ASYNC, TRK_HALO_TMA = 0, 1, 2
 
 _STATUS = {TRK_EINVAL: "EINVAL", TRK_ENOMEM: "ENOMEM", TRK_ECUDA: "ECUDA", TRK_ENONFINITE: "ENONFINITE",
            TRK_ENOFIELD: "ENOFIELD", TRK_ECFL: "ECFL", TRK_EIO: "EIO"}
@@ -44,7 +45,7 @@ ABI_FUNCTIONS = (
     "tracker_profile", "tracker_profile_read", "tracker_bin_static", "tracker_set_step_kernel",
     "tracker_step_kernel_for", "tracker_state_write", "tracker_state_read_info", "tracker_state_read",
     "tracker_last_step_kernel",
-    "tracker_field_texture", "tracker_probe_fma",
+    "tracker_field_texture", "tracker_probe_fma", "tracker_set_halo_copy", "tracker_halo_copy",
 )
 
 
@@ -107,6 +108,8 @@ def load_library(path: str = LIB_PATH):
             "tracker_last_step_kernel": (c_int, [vp]),
             "tracker_field_texture": (c_int, [vp]),
             "tracker_probe_fma": (c_int, [c_int, vp]),
+            "tracker_set_halo_copy": (c_int, [vp, c_int]),
+            "tracker_halo_copy": (c_int, [vp, c_int]),
             "tracker_state_write": (c_int, [ctypes.c_char_p, vp, vp, vp]),
             "tracker_state_read_info": (c_int, [ctypes.c_char_p, vp]),
             "tracker_state_read": (c_int, [ctypes.c_char_p, c_i64, vp, vp, vp]),
@@ -439,6 +442,16 @@ class Tracker:
     def last_step_kernel(self):
         """The kernel the latest advance or interpolate used (after AUTO's timing)."""
         r = int(load_library().tracker_last_step_kernel(self.h))
+        _check(min(r, 0))
+        return r
+
+    def set_halo_copy(self, kind):
+        """TRK_HALO_AUTO, _ASYNC or _TMA: how the block kernel stages its field halos."""
+        _check(load_library().tracker_set_halo_copy(self.h, int(kind)))
+
+    def halo_copy(self, rk2=False):
+        """The halo copy the block kernel uses now (TRK_HALO_ASYNC or TRK_HALO_TMA)."""
+        r = int(load_library().tracker_halo_copy(self.h, int(bool(rk2))))
         _check(min(r, 0))
         return r
 

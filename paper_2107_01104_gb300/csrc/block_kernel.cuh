@@ -30,6 +30,8 @@
 //   I = 4: lane = (i1, i2 in 0..3, p in 0..1); i3 = p and p+2
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (type only; the library does not link the driver API)
+
 #include "internal.cuh"
 
 namespace trk {
@@ -793,6 +795,58 @@ __device__ __forceinline__ void load_halo_async(T* halo, const FieldView& f, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-memory-accelerator halo staging (HC_TMA): one cp.async.bulk.tensor
+// copy per component chunk, issued by one thread, completion counted in bytes
+// on an mbarrier that every thread waits on.  The tensor map covers the
+// padded field [C][NP][NP][NP] (4-D, x1 innermost) with the box of tma_box.
+// ---------------------------------------------------------------------------
+enum { HC_ASYNC = 0, HC_TMA = 1 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// one thread: announce `bytes` for the barrier's current phase and start the copy of
+// the box at tensor coordinates (x, y, z, k) into dst
+__device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, int x, int y, int z, int k, uint64_t* bar,
+                                          uint32_t bytes)
+{
+    // shared-memory reads of the previous halo (generic proxy) are ordered
+    // before the copy's writes (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(k), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Waits for the barrier's phase `parity` to complete; false after the
+// iteration limit (each try_wait itself suspends for a bounded time), so a
+// copy that never lands cannot hang the kernel.
+constexpr int kTmaWaitLimit = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (int it = 0; it < kTmaWaitLimit; ++it) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Stage components k0 .. k0+kc-1 (KC > 0: compile-time count) of the halo
 // whose origin is the cell (o1, o2, o3): cp.async for float32 / float64
 // storage, registers (with the bf16 hi + lo sum) for split bf16.  With
@@ -834,7 +888,8 @@ struct SmemPlan {
     static constexpr size_t id = align32(cell + PB * sizeof(int));
     static constexpr size_t x = align32(id + PB * sizeof(int));
     static constexpr size_t rhs = align32(x + (STAGE >= 1 ? (size_t)3 * PB * sizeof(double) : 0));
-    static constexpr size_t total = rhs + (STAGE >= 2 ? (size_t)3 * AB_MAX_HIST * PB * sizeof(float) : 0);
+    static constexpr size_t mbar = align32(rhs + (STAGE >= 2 ? (size_t)3 * AB_MAX_HIST * PB * sizeof(float) : 0));
+    static constexpr size_t total = mbar + 16;   // the halo copy's mbarrier (tensor-copy staging)
 };
 
 template <int MODE>
@@ -854,8 +909,12 @@ __host__ __device__ constexpr int stage_of()
 // copy a.f.nm, as one 16-byte load per node when NM == NM_VEC4 (three
 // components padded to four floats), else per component (NM_SCALAR).  Must be
 // called by all threads of the CTA.
-template <typename T, int I, int DEG, int MODE, int STORE, bool HALO, int NM = NM_NONE>
-__device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0, int j1, unsigned char* smem_raw)
+// HC (with HALO): HC_ASYNC stages the halo with cp.async element copies (or
+// through registers for split bf16); HC_TMA with one tensor copy per chunk
+// through tmap (float32 and float64 storage), in the padded box of tma_box.
+template <typename T, int I, int DEG, int MODE, int STORE, bool HALO, int NM = NM_NONE, int HC = HC_ASYNC>
+__device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0, int j1, unsigned char* smem_raw,
+                                              const CUtensorMap* tmap = nullptr)
 {
     constexpr bool IS_AB2 = (MODE == MODE_AB2 || MODE == MODE_AB2_D);
     constexpr bool IS_STEP = (MODE == MODE_RK2 || IS_AB2);
@@ -865,8 +924,12 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     constexpr int G = I / 2 - 1 + MARGIN;                   // halo origin = block origin - G
     constexpr int LO = I / 2 - 1;                           // stencil node offset
     constexpr int RMAX = H - 1 - I / 2;                     // largest cell whose stencil fits the halo
+    constexpr bool TMA = HALO && HC == HC_TMA;
+    static_assert(!TMA || STORE == ST_F32 || STORE == ST_F64, "tensor-copy halos: float32 or float64 storage");
+    constexpr TmaBox TB = tma_box(I, MARGIN, (int)sizeof(T));
     using Lay = Layout<I, H>;
-    constexpr int S2 = Lay::S2, S3 = Lay::S3, SC = Lay::SC;
+    constexpr int S2 = TMA ? TB.S2() : Lay::S2, S3 = TMA ? TB.S3() : Lay::S3, SC = TMA ? TB.SC() : Lay::SC;
+    constexpr int XOFF = TMA ? TB.XOFF : 0;   // the box starts XOFF elements before the halo in x1
     using SL = SmemLd<T, S2, S3, SC>;
 
     using SM = SmemPlan<T, HALO ? SC : 0, stage_of<MODE>()>;
@@ -878,6 +941,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
     int* p_id = reinterpret_cast<int*>(smem_raw + SM::id);                  // [PB] caller ids
     double* p_x = reinterpret_cast<double*>(smem_raw + SM::x);              // [3][PB] positions (steps)
     float* p_rhs = reinterpret_cast<float*>(smem_raw + SM::rhs);            // [3 * (k-1)][PB] AB history
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + SM::mbar);      // halo copy barrier (TMA)
 
     if (j0 >= j1) return;
 
@@ -918,9 +982,20 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
 
     // the halo of component chunk ch (all three velocity components for the steps)
     constexpr bool ASYNC = STORE != ST_BF16X2;
+    uint32_t tma_phase = 0;
+    if constexpr (TMA) {
+        if (tid == 0) mbar_init(mbar);
+        __syncthreads();
+    }
     auto issue_halo = [&](int ch) {
-        if constexpr (IS_STEP) stage_halo<T, STORE, H, G, S2, S3, SC, 3, false>(halo, a.f, 0, 3, o1, o2, o3);
-        else stage_halo<T, STORE, H, G, S2, S3, SC, 0, false>(halo, a.f, 3 * ch, min(3, a.f.C - 3 * ch), o1, o2, o3);
+        if constexpr (TMA) {
+            constexpr uint32_t bytes = (uint32_t)(3 * SC * sizeof(T));
+            if (tid == 0) tma_issue(halo, tmap, o1 + PAD - XOFF, o2 + PAD, o3 + PAD, 3 * ch, mbar, bytes);
+        } else if constexpr (IS_STEP) {
+            stage_halo<T, STORE, H, G, S2, S3, SC, 3, false>(halo, a.f, 0, 3, o1, o2, o3);
+        } else {
+            stage_halo<T, STORE, H, G, S2, S3, SC, 0, false>(halo, a.f, 3 * ch, min(3, a.f.C - 3 * ch), o1, o2, o3);
+        }
     };
 
     for (int batch = j0; batch < j1; batch += PB) {
@@ -965,8 +1040,25 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                 __syncthreads();   // previous readers of the halo are done
                 issue_halo(ch);
             }
-            if constexpr (HALO && ASYNC) cp_async_wait_all();
-            __syncthreads();
+            if constexpr (TMA) {
+                // a copy was issued for this (batch, chunk) unless the one halo chunk of an
+                // earlier batch is still in place; every thread waits for it, and if it did
+                // not land within the limit the block is skipped (all threads agree) and the
+                // host is told
+                const bool issued = (batch == j0 && ch == 0) || nchunks > 1;
+                bool ok = true;
+                if (issued) {
+                    ok = mbar_wait(mbar, tma_phase);
+                    tma_phase ^= 1u;
+                }
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) atomicOr(a.flags + FLAG_HALO_TIMEOUT, 1);
+                    return;
+                }
+            } else {
+                if constexpr (HALO && ASYNC) cp_async_wait_all();
+                __syncthreads();
+            }
             for (int q = warp; q < nbat; q += NW) {
                 const PRec<T> rec = p_rec[q];
                 int rp;
@@ -975,7 +1067,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                 const T t1 = rec.t[0], t2 = rec.t[1], t3 = rec.t[2];
                 const int r1 = rp & 255, r2 = (rp >> 8) & 255, r3 = (rp >> 16) & 255;
                 if constexpr (HALO) {
-                    L.load(SL{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO)});
+                    L.load(SL{halo + (r3 - LO) * S3 + (r2 - LO) * S2 + (r1 - LO) + XOFF});
                 } else {
                     const int pc = p_cell[q];
                     gload(pc & 1023, (pc >> 10) & 1023, (pc >> 20) & 1023, 3 * ch, a.f.C - 1);
@@ -1003,7 +1095,7 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
                         const bool in =
                             HALO && s1 >= LO && s1 <= RMAX && s2 >= LO && s2 <= RMAX && s3 >= LO && s3 <= RMAX;
                         if (in) {
-                            L.load(SL{halo + (s3 - LO) * S3 + (s2 - LO) * S2 + (s1 - LO)});
+                            L.load(SL{halo + (s3 - LO) * S3 + (s2 - LO) * S2 + (s1 - LO) + XOFF});
                         } else {
                             // left the staged halo, or (direct path) moved more than one cell
                             const bool far = HALO || abs(dc[0]) > 1 || abs(dc[1]) > 1 || abs(dc[2]) > 1;
@@ -1113,13 +1205,14 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
 #define TRK_F32_MIN_BLOCKS 3   // resident CTAs per SM the float32 kernels are register-capped for (I = 4, 6)
 #endif
 
-template <typename T, int I, int DEG, int MODE, int STORE>
+// tmap: the tensor map of the padded field (read only with HC == HC_TMA)
+template <typename T, int I, int DEG, int MODE, int STORE, int HC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN_BLOCKS) : 1)
-    k_block(const __grid_constant__ BlockArgs a)
+    k_block(const __grid_constant__ BlockArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int b = blockIdx.x;
-    process_block<T, I, DEG, MODE, STORE, true>(a, b, a.offsets[b], a.offsets[b + 1], smem_raw);
+    process_block<T, I, DEG, MODE, STORE, true, NM_NONE, HC>(a, b, a.offsets[b], a.offsets[b + 1], smem_raw, &tmap);
 }
 
 // Direct path: CTA c takes the sorted particles [c PB, (c + 1) PB) and
@@ -1209,21 +1302,22 @@ cudaError_t dispatch_direct(int mode, const BlockArgs& a, cudaStream_t st)
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int I, int MODE>
+template <typename T, int I, int MODE, int HC = HC_ASYNC>
 constexpr size_t block_smem_bytes()
 {
     constexpr int MARGIN = (MODE == MODE_RK2) ? 1 : 0;
     constexpr int H = BLK + I - 1 + 2 * MARGIN;
     using Lay = Layout<I, H>;
-    return SmemPlan<T, Lay::SC, stage_of<MODE>()>::total;
+    constexpr int SC = HC == HC_TMA ? tma_box(I, MARGIN, (int)sizeof(T)).SC() : Lay::SC;
+    return SmemPlan<T, SC, stage_of<MODE>()>::total;
 }
 
-template <typename T, int I, int DEG, int MODE, int STORE>
-cudaError_t launch_block_t(const BlockArgs& a, int64_t nblocks, cudaStream_t st)
+template <typename T, int I, int DEG, int MODE, int STORE, int HC>
+cudaError_t launch_block_hc(const BlockArgs& a, const CUtensorMap& tmap, int64_t nblocks, cudaStream_t st)
 {
-    constexpr size_t smem = block_smem_bytes<T, I, MODE>();
+    constexpr size_t smem = block_smem_bytes<T, I, MODE, HC>();
     static_assert(smem <= 232448, "block shared-memory plan exceeds the per-block limit");
-    auto kern = k_block<T, I, DEG, MODE, STORE>;
+    auto kern = k_block<T, I, DEG, MODE, STORE, HC>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1231,19 +1325,31 @@ cudaError_t launch_block_t(const BlockArgs& a, int64_t nblocks, cudaStream_t st)
         attr_set = true;
     }
     if (nblocks <= 0) return cudaSuccess;
-    kern<<<(unsigned)nblocks, NT, smem, st>>>(a);
+    kern<<<(unsigned)nblocks, NT, smem, st>>>(a, tmap);
     return cudaGetLastError();
 }
 
+// tmap: the tensor map of the padded field for this mode's box (tma_box), or
+// null for the cp.async / register staging
+template <typename T, int I, int DEG, int MODE, int STORE>
+cudaError_t launch_block_t(const BlockArgs& a, const CUtensorMap* tmap, int64_t nblocks, cudaStream_t st)
+{
+    if constexpr (STORE == ST_F32 || STORE == ST_F64) {
+        if (tmap) return launch_block_hc<T, I, DEG, MODE, STORE, HC_TMA>(a, *tmap, nblocks, st);
+    }
+    const CUtensorMap none{};
+    return launch_block_hc<T, I, DEG, MODE, STORE, HC_ASYNC>(a, none, nblocks, st);
+}
+
 template <int I, int DEG>
-cudaError_t dispatch_store_mode(int mode, const BlockArgs& a, int64_t nblocks, cudaStream_t st)
+cudaError_t dispatch_store_mode(int mode, const BlockArgs& a, const CUtensorMap* tmap, int64_t nblocks, cudaStream_t st)
 {
     const int s = a.f.storage;
-#define TRK_CASE(M)                                                                        \
-    case M:                                                                                \
-        if (s == ST_F64) return launch_block_t<double, I, DEG, M, ST_F64>(a, nblocks, st); \
-        if (s == ST_F32) return launch_block_t<float, I, DEG, M, ST_F32>(a, nblocks, st);  \
-        return launch_block_t<float, I, DEG, M, ST_BF16X2>(a, nblocks, st);
+#define TRK_CASE(M)                                                                               \
+    case M:                                                                                       \
+        if (s == ST_F64) return launch_block_t<double, I, DEG, M, ST_F64>(a, tmap, nblocks, st); \
+        if (s == ST_F32) return launch_block_t<float, I, DEG, M, ST_F32>(a, tmap, nblocks, st);  \
+        return launch_block_t<float, I, DEG, M, ST_BF16X2>(a, nullptr, nblocks, st);
     switch (mode) {
         TRK_CASE(MODE_INTERP)
         TRK_CASE(MODE_INTERP_DERIV)

@@ -16,7 +16,9 @@ namespace trk {
 // ---------------------------------------------------------------------------
 // FLAG_BINNING: a counting-sort scatter found a block fuller than its count
 // (cannot happen when every step counts what it writes; guarded anyway).
-enum { FLAG_NONFINITE = 0, FLAG_CFL = 1, FLAG_BINNING = 2, NUM_FLAGS = 4 };
+// FLAG_HALO_TIMEOUT: a tensor copy of a block's halo did not complete within
+// the wait limit (the block was skipped; reported as an internal error).
+enum { FLAG_NONFINITE = 0, FLAG_CFL = 1, FLAG_BINNING = 2, FLAG_HALO_TIMEOUT = 3, NUM_FLAGS = 4 };
 
 // Storage codes (same values as trk_storage in tracker.h).
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16X2 = 2 };
@@ -52,6 +54,95 @@ struct FieldView {
 __host__ __device__ __forceinline__ int64_t padded_index(int NP, int x1, int x2, int x3)
 {
     return ((int64_t)(x3 + PAD) * NP + (x2 + PAD)) * NP + (x1 + PAD);
+}
+
+// ---------------------------------------------------------------------------
+// Halo box of the block kernel's TMA staging (cp.async.bulk.tensor): one
+// tensor copy per component chunk writes a dense box [3][H][BY][BX] of the
+// padded field into shared memory.  The box starts XOFF elements before the
+// halo (its x origin rounded down to 16 bytes, as a tensor copy must be);
+// BX (a multiple of 16 bytes) and BY >= H are padded so that the warp-wide
+// stencil loads of the lane map of kernel width I meet as few shared-memory
+// bank conflicts as the dense pitch allows (BX = row pitch, BX*BY = plane
+// pitch).  Used on the host to encode the tensor map and on the device for
+// the lane offsets.
+// ---------------------------------------------------------------------------
+// largest number of distinct words sharing a bank among `n` lane offsets
+// (in elements of esz bytes; a warp's 8-byte loads are served as two halves
+// of 16 lanes over 16 double-width banks)
+__host__ __device__ constexpr int bank_degree(const int* offs, int n, int esz)
+{
+    int worst = 0;
+    const int halves = esz == 8 ? 2 : 1, lanes = 32 / halves, banks = esz == 8 ? 16 : 32;
+    for (int h = 0; h < halves; ++h) {
+        for (int b = 0; b < banks; ++b) {
+            int seen[32] = {};
+            int ns = 0;
+            for (int l = h * lanes; l < (h + 1) * lanes && l < n; ++l) {
+                const int o = offs[l];
+                if (((o % banks) + banks) % banks != b) continue;
+                bool dup = false;
+                for (int q = 0; q < ns; ++q) dup = dup || seen[q] == o;
+                if (!dup && ns < 32) seen[ns++] = o;
+            }
+            worst = ns > worst ? ns : worst;
+        }
+    }
+    return worst;
+}
+
+// worst bank degree of the stencil loads of kernel width I for row pitch S2
+// and plane pitch S3 (the lane maps of Lane<T, I, D>::load)
+__host__ __device__ constexpr int lane_map_degree(int I, int S2, int S3, int esz)
+{
+    int worst = 0;
+    int offs[32] = {};
+    if (I == 8) {
+        for (int l = 0; l < 32; ++l) offs[l] = (l & 7) + S2 * (l >> 3);
+        worst = bank_degree(offs, 32, esz);
+    } else if (I == 6) {
+        for (int l = 0; l < 32; ++l) offs[l] = (l < 30 ? (l % 6) + S2 * (l / 6) : (l % 6));      // pass A
+        const int a = bank_degree(offs, 32, esz);
+        for (int l = 0; l < 32; ++l) offs[l] = (l < 30 ? (l % 6) + S3 * (l / 6) : (l % 6));      // pass B
+        const int b = bank_degree(offs, 32, esz);
+        worst = a > b ? a : b;
+    } else {
+        for (int l = 0; l < 32; ++l) offs[l] = (l & 3) + S2 * ((l >> 2) & 3) + S3 * (l >> 4);
+        worst = bank_degree(offs, 32, esz);
+    }
+    return worst;
+}
+
+struct TmaBox {
+    int H, XOFF, BX, BY;
+    __host__ __device__ constexpr int S2() const { return BX; }
+    __host__ __device__ constexpr int S3() const { return BX * BY; }
+    __host__ __device__ constexpr int SC() const { return BX * BY * H; }
+};
+
+// The box for kernel width I, RK2 margin `margin` (0 or 1) and element size esz:
+// among row pitches up to 6 vectors beyond the minimum and plane heights up
+// to 8 rows beyond H, the lowest bank degree, then the smallest box.
+__host__ __device__ constexpr TmaBox tma_box(int I, int margin, int esz)
+{
+    const int H = 8 + I - 1 + 2 * margin;          // BLK + I - 1 + 2 margin
+    const int G = I / 2 - 1 + margin;
+    const int VEC = 16 / esz;
+    const int XOFF = ((8 - G) % VEC + VEC) % VEC;   // PAD = 8
+    const int bx0 = (H + XOFF + VEC - 1) / VEC * VEC;
+    TmaBox best{H, XOFF, bx0, H};
+    int best_deg = 1 << 20, best_size = 1 << 30;
+    for (int bx = bx0; bx <= bx0 + 6 * VEC; bx += VEC)
+        for (int by = H; by <= H + 8; ++by) {
+            const int d = lane_map_degree(I, bx, bx * by, esz);
+            const int size = bx * by;
+            if (d < best_deg || (d == best_deg && size < best_size)) {
+                best_deg = d;
+                best_size = size;
+                best = TmaBox{H, XOFF, bx, by};
+            }
+        }
+    return best;
 }
 
 // Kernel weights beta_i(s), s = t - 1/2, as polynomial coefficients, passed by
@@ -285,9 +376,15 @@ cudaError_t launch_count_keys(int64_t np, const uint32_t* keys, uint32_t* counts
 cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,
                                  const int32_t* id_in, const float* rhs_in, int rhs_rows, double* pos_out,
                                  int32_t* id_out, float* rhs_out, int* flags, cudaStream_t st);
-cudaError_t launch_block_i4(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
-cudaError_t launch_block_i6(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
-cudaError_t launch_block_i8(int mode, const BlockArgs& a, int64_t nblocks, int deg_hi, cudaStream_t st);
+// tmap: a CUtensorMap of the padded field with the box tma_box(I, margin of
+// the mode, element size) for tensor-copy halo staging (float32 and float64
+// storage), or null for cp.async element copies
+cudaError_t launch_block_i4(int mode, const BlockArgs& a, const void* tmap, int64_t nblocks, int deg_hi,
+                            cudaStream_t st);
+cudaError_t launch_block_i6(int mode, const BlockArgs& a, const void* tmap, int64_t nblocks, int deg_hi,
+                            cudaStream_t st);
+cudaError_t launch_block_i8(int mode, const BlockArgs& a, const void* tmap, int64_t nblocks, int deg_hi,
+                            cudaStream_t st);
 // direct path (sparse particle sets): a.np sorted particles, PB per CTA, stencils from global memory
 cudaError_t launch_direct_i4(int mode, const BlockArgs& a, int deg_hi, cudaStream_t st);
 cudaError_t launch_direct_i6(int mode, const BlockArgs& a, int deg_hi, cudaStream_t st);

@@ -12,6 +12,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is looked up at run time)
+
 #include "internal.cuh"
 #include "tracker.h"
 
@@ -165,6 +167,12 @@ struct tracker {
     int last_kernel = TRK_STEP_AUTO;  // kernel of the latest tracker_advance or tracker_interpolate
     int* d_colctr = nullptr;          // work counter of the column kernel
     int col_seg = 8;                  // column kernel: x3 slabs per work item (power of two)
+    // tensor maps of the padded field for the block kernel's tensor-copy halos,
+    // one per stage-2 margin (interpolation and AB: 0, RK2: 1)
+    CUtensorMap tmap[2];
+    bool tmap_ok[2] = {false, false};
+    int halo_copy = TRK_HALO_AUTO;    // trk_halo_copy: how the block kernel stages its halo
+    bool auto_tma = false;            // TRK_HALO_AUTO's current choice (set by the tuner)
     uint32_t* d_counts = nullptr;     // [nblocks] block counts (counting-sort binning of the column path)
     int32_t* d_cursor = nullptr;      // [nblocks] scatter cursors
     uint32_t* d_scan_tmp = nullptr;   // tile sums of the multi-CTA count scan
@@ -320,14 +328,75 @@ FieldView field_view(const tracker* t)
     return f;
 }
 
+// The tensor map the block kernel stages its halos with for `mode`, or null
+// for cp.async element copies (TRK_HALO_ASYNC, no map for this field, or a
+// storage the tensor copies do not cover).
+const void* halo_tmap(const tracker* t, int mode)
+{
+    const int margin = mode == MODE_RK2 ? 1 : 0;
+    const bool tma = t->halo_copy == TRK_HALO_TMA || (t->halo_copy == TRK_HALO_AUTO && t->auto_tma);
+    if (!tma || !t->tmap_ok[margin]) return nullptr;
+    return &t->tmap[margin];
+}
+
 cudaError_t launch_block(tracker* t, int mode, const BlockArgs& a)
 {
     ProfScope ps(t, PROF_STEP);
     t->launches += 1;
+    const void* m = halo_tmap(t, mode);
     switch (t->I) {
-        case 4: return launch_block_i4(mode, a, t->nblocks, t->deg_hi, t->stream);
-        case 6: return launch_block_i6(mode, a, t->nblocks, t->deg_hi, t->stream);
-        default: return launch_block_i8(mode, a, t->nblocks, t->deg_hi, t->stream);
+        case 4: return launch_block_i4(mode, a, m, t->nblocks, t->deg_hi, t->stream);
+        case 6: return launch_block_i6(mode, a, m, t->nblocks, t->deg_hi, t->stream);
+        default: return launch_block_i8(mode, a, m, t->nblocks, t->deg_hi, t->stream);
+    }
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library does not link the driver API); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && p)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor maps of the padded field f[C][NP][NP][NP] (4-D, x1 innermost) with the
+// block kernel's halo box for both stage-2 margins: float32 and float64
+// storage with at least three components (a chunk of three per copy; the
+// last chunk of a C that is not a multiple of three reads zeros beyond C,
+// which no output uses).  Left unset (cp.async staging) otherwise.
+void build_tmaps(tracker* t)
+{
+    t->tmap_ok[0] = t->tmap_ok[1] = false;
+    if ((t->storage != TRK_F32 && t->storage != TRK_F64) || t->C < 3 || !t->field) return;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return;
+    const int esz = t->storage == TRK_F64 ? 8 : 4;
+    const cuuint64_t NP = (cuuint64_t)(t->N + 2 * PAD);
+    const cuuint64_t dims[4] = {NP, NP, NP, (cuuint64_t)t->C};
+    const cuuint64_t strides[3] = {NP * esz, NP * NP * esz, NP * NP * NP * esz};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int margin = 0; margin < 2; ++margin) {
+        const TmaBox b = tma_box(t->I, margin, esz);
+        const cuuint32_t box[4] = {(cuuint32_t)b.BX, (cuuint32_t)b.BY, (cuuint32_t)b.H, 3};
+        const CUresult r = enc(&t->tmap[margin], esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                               4, t->field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        t->tmap_ok[margin] = r == CUDA_SUCCESS;
     }
 }
 
@@ -835,6 +904,7 @@ int tracker_sync(tracker* t)
     CUDA_TRY(cudaMemset(t->d_flags, 0, sizeof(h)));
     if (h[FLAG_NONFINITE]) return fail(TRK_ENONFINITE, "a position was non-finite or beyond 2^51 cells");
     if (h[FLAG_BINNING]) return fail(TRK_ECUDA, "internal error: block counts did not match the binned particles");
+    if (h[FLAG_HALO_TIMEOUT]) return fail(TRK_ECUDA, "internal error: a halo tensor copy did not complete (block skipped)");
     if (h[FLAG_CFL]) return fail(TRK_ECFL, "a particle moved more than one cell in one stage (result computed exactly)");
     return TRK_OK;
 }
@@ -877,6 +947,7 @@ int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src
     }
     t->nm_valid = false;              // the node-major copy is refreshed before its next use
     t->launches += 1;
+    build_tmaps(t);
     if (staging) {
         CUDA_TRY(cudaStreamSynchronize(t->stream));
         dev_free(staging);
@@ -916,6 +987,23 @@ int tracker_last_step_kernel(const tracker* t)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
     return t->last_kernel;
+}
+
+int tracker_set_halo_copy(tracker* t, int kind)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (kind != TRK_HALO_AUTO && kind != TRK_HALO_ASYNC && kind != TRK_HALO_TMA)
+        return fail(TRK_EINVAL, "unknown halo copy %d", kind);
+    t->halo_copy = kind;
+    t->gen += 1;                      // captured step graphs hold the other kernels
+    return TRK_OK;
+}
+
+int tracker_halo_copy(const tracker* t, int mode)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (mode != 0 && mode != 1) return fail(TRK_EINVAL, "mode must be 0 (interpolation, AB) or 1 (RK2)");
+    return halo_tmap(t, mode ? MODE_RK2 : MODE_INTERP) ? TRK_HALO_TMA : TRK_HALO_ASYNC;
 }
 
 int tracker_field_texture(const tracker* t)
