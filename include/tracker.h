@@ -255,12 +255,52 @@ int tracker_last_step_kernel(const tracker* t);
  *     box padded so that the stencil loads meet few shared-memory bank
  *     conflicts (float32 and float64 storage with at least three
  *     components; elsewhere the cp.async staging is used);
- *   TRK_HALO_AUTO (default): the choice of the tuner (tracker_advance's
- *     first timed call), else TRK_HALO_ASYNC.
+ *   TRK_HALO_AUTO (default): TRK_HALO_TMA where the field has a tensor map
+ *     (measured faster in every case: e.g. 0.533 vs 0.708 ms per RK2 step at
+ *     256^3, I = 6, 1/16 particle per cell), else TRK_HALO_ASYNC.
  * Both give bit-identical results.  A tensor copy that does not complete
  * within its wait limit skips its block and makes tracker_sync return
  * TRK_ECUDA.  Errors: TRK_EINVAL. */
 int tracker_set_halo_copy(tracker* t, int kind);
+
+/* Launch shape of the time-step path.  step_kernel: TRK_STEP_COLUMN, _BLOCK
+ * or _DIRECT; direct_block: edge of the cubic cell blocks the direct kernel's
+ * particles are binned by (a power of two <= N; with the default 8^3 block
+ * shape; it sets how compact each thread block's 256 particles are);
+ * column_segment: x3 slabs per work item of the column kernel (a power of
+ * two <= 64, at most N/8); halo_copy: the block kernel's TRK_HALO_ASYNC or
+ * TRK_HALO_TMA.  source (tracker_get_tuning only): how they were chosen. */
+typedef enum { TRK_TUNE_DEFAULT = 0, TRK_TUNE_TIMED = 1, TRK_TUNE_CACHED = 2, TRK_TUNE_FIXED = 3 } trk_tune_source;
+typedef struct {
+    int step_kernel;
+    int direct_block;
+    int column_segment;
+    int halo_copy;
+    int source;
+} trk_tuning;
+
+/* Autotuning (no counterpart in the paper).  With TRK_STEP_AUTO (the
+ * default), the first tracker_advance call of a workload -- grid, kernel,
+ * storage, SM count, density bucket (half octaves of particles per cell) and
+ * scheme -- that has at least 2 x (candidates) + 2 steps and at least 32768
+ * particles times every candidate launch shape on 2 of its own steps (CUDA
+ * events; the host waits once; skipped while the stream is being captured)
+ * and keeps the fastest for the rest of the call and for later calls
+ * (TRK_TUNE_TIMED, then TRK_TUNE_CACHED).  Candidates: above 0.01 particles
+ * per cell the column kernel with segments 4, 8, 16 (or, without one, the
+ * block kernel), below 0.25 per cell the direct kernel
+ * with block edges 8, 16, 32.  Other calls use the density rule of
+ * tracker_set_step_kernel with the default shape (TRK_TUNE_DEFAULT).  Every
+ * candidate gives bit-identical steps.  When the environment variable
+ * TRK_TUNE_CACHE names a file, decisions are appended to it (one line per
+ * workload) and trackers created later read it.
+ * tracker_set_tuning fixes a launch shape (TRK_TUNE_FIXED; no timing); NULL
+ * returns to automatic tuning.  Errors: TRK_EINVAL. */
+int tracker_set_tuning(tracker* t, const trk_tuning* tuning);
+
+/* The launch shape the latest tracker_advance ran its remaining steps with,
+ * and how it was chosen. */
+int tracker_get_tuning(const tracker* t, trk_tuning* out);
 
 /* The halo copy (TRK_HALO_ASYNC or TRK_HALO_TMA) the block kernel uses now
  * for interpolation and AB steps (mode 0) or RK2 steps (mode 1). */

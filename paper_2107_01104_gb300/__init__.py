@@ -33,6 +33,7 @@ TRK_RK2, TRK_AB2, TRK_AB3, TRK_AB4 = 0, 1, 2, 3
 TRK_DTYPE_F64, TRK_DTYPE_F32 = 0, 1
 TRK_STEP_AUTO, TRK_STEP_BLOCK, TRK_STEP_COLUMN, TRK_STEP_DIRECT = 0, 1, 2, 3
 TRK_HALO_AUTO, TRK_HALO_ASYNC, TRK_HALO_TMA = 0, 1, 2
+TRK_TUNE_DEFAULT, TRK_TUNE_TIMED, TRK_TUNE_CACHED, TRK_TUNE_FIXED = 0, 1, 2, 3
 
 _STATUS = {TRK_EINVAL: "EINVAL", TRK_ENOMEM: "ENOMEM", TRK_ECUDA: "ECUDA", TRK_ENONFINITE: "ENONFINITE",
            TRK_ENOFIELD: "ENOFIELD", TRK_ECFL: "ECFL", TRK_EIO: "EIO"}
@@ -46,6 +47,7 @@ ABI_FUNCTIONS = (
     "tracker_step_kernel_for", "tracker_state_write", "tracker_state_read_info", "tracker_state_read",
     "tracker_last_step_kernel",
     "tracker_field_texture", "tracker_probe_fma", "tracker_set_halo_copy", "tracker_halo_copy",
+    "tracker_set_tuning", "tracker_get_tuning",
 )
 
 
@@ -62,6 +64,11 @@ class trk_state_info(ctypes.Structure):
         ("history_valid", ctypes.c_int32), ("step", ctypes.c_int64), ("time", ctypes.c_double),
         ("dt", ctypes.c_double),
     ]
+
+
+class trk_tuning(ctypes.Structure):
+    _fields_ = [("step_kernel", ctypes.c_int), ("direct_block", ctypes.c_int), ("column_segment", ctypes.c_int),
+                ("halo_copy", ctypes.c_int), ("source", ctypes.c_int)]
 
 
 class trk_set(ctypes.Structure):
@@ -109,6 +116,8 @@ def load_library(path: str = LIB_PATH):
             "tracker_field_texture": (c_int, [vp]),
             "tracker_probe_fma": (c_int, [c_int, vp]),
             "tracker_set_halo_copy": (c_int, [vp, c_int]),
+            "tracker_set_tuning": (c_int, [vp, vp]),
+            "tracker_get_tuning": (c_int, [vp, vp]),
             "tracker_halo_copy": (c_int, [vp, c_int]),
             "tracker_state_write": (c_int, [ctypes.c_char_p, vp, vp, vp]),
             "tracker_state_read_info": (c_int, [ctypes.c_char_p, vp]),
@@ -444,6 +453,21 @@ class Tracker:
         r = int(load_library().tracker_last_step_kernel(self.h))
         _check(min(r, 0))
         return r
+
+    def set_tuning(self, step_kernel=None, direct_block=8, column_segment=8, halo_copy=TRK_HALO_TMA):
+        """Fix the time-step launch shape (see tracker_set_tuning); no arguments: automatic tuning."""
+        if step_kernel is None:
+            _check(load_library().tracker_set_tuning(self.h, None))
+            return
+        p = trk_tuning(step_kernel=int(step_kernel), direct_block=int(direct_block),
+                       column_segment=int(column_segment), halo_copy=int(halo_copy), source=0)
+        _check(load_library().tracker_set_tuning(self.h, ctypes.byref(p)))
+
+    def tuning(self):
+        """The launch shape the latest advance ran with and how it was chosen (a dict)."""
+        p = trk_tuning()
+        _check(load_library().tracker_get_tuning(self.h, ctypes.byref(p)))
+        return {f: getattr(p, f) for f, _ in trk_tuning._fields_}
 
     def set_halo_copy(self, kind):
         """TRK_HALO_AUTO, _ASYNC or _TMA: how the block kernel stages its field halos."""

@@ -5,7 +5,9 @@
 // Every entry point validates its arguments on the host, issues kernels on
 // the tracker's stream and returns a status; nothing here computes on the CPU.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <string>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -162,17 +164,21 @@ struct tracker {
     std::vector<std::pair<uint64_t, int>> tune_cache;   // set signature -> direct path?
     int nsm = 0;
     int step_kernel = TRK_STEP_AUTO;  // trk_step_kernel
-    std::vector<std::pair<uint64_t, int>> path_cache;   // (np, mode, order) -> step kernel chosen by timing
     std::vector<std::pair<uint64_t, int>> interp_cache; // (np, C, deriv, out dtype) -> interpolation kernel
     int last_kernel = TRK_STEP_AUTO;  // kernel of the latest tracker_advance or tracker_interpolate
     int* d_colctr = nullptr;          // work counter of the column kernel
     int col_seg = 8;                  // column kernel: x3 slabs per work item (power of two)
+    int dir_blk = BLK;                // direct path: edge of its cubic binning blocks (default shape only)
+    int64_t bin_cap = 0;              // entries of offsets / counts / cursor (largest geometry in use)
+    int tune_source = TRK_TUNE_DEFAULT;   // how the latest call's parameters were chosen
+    std::array<int, 4> last_tuning = {TRK_STEP_AUTO, BLK, 8, 0};   // path, dir_blk, col_seg, tma of the latest call
+    std::vector<std::pair<std::string, std::array<int, 4>>> step_tune;   // tuner decisions by workload
     // tensor maps of the padded field for the block kernel's tensor-copy halos,
     // one per stage-2 margin (interpolation and AB: 0, RK2: 1)
     CUtensorMap tmap[2];
     bool tmap_ok[2] = {false, false};
     int halo_copy = TRK_HALO_AUTO;    // trk_halo_copy: how the block kernel stages its halo
-    bool auto_tma = false;            // TRK_HALO_AUTO's current choice (set by the tuner)
+    bool auto_tma = true;             // TRK_HALO_AUTO's current choice (tensor copies, where there is a map)
     uint32_t* d_counts = nullptr;     // [nblocks] block counts (counting-sort binning of the column path)
     int32_t* d_cursor = nullptr;      // [nblocks] scatter cursors
     uint32_t* d_scan_tmp = nullptr;   // tile sums of the multi-CTA count scan
@@ -219,6 +225,34 @@ struct ProfScope {
     }
 };
 
+// The binning arrays (offsets, block counts, scatter cursors, scan scratch)
+// for at least nb blocks; grown, never shrunk (the direct path's tuned block
+// edge may need more blocks than the tracker's block shape).
+int ensure_bin(tracker* t, int64_t nb)
+{
+    if (nb <= t->bin_cap) return TRK_OK;
+    dev_free(t->offsets);
+    dev_free(t->d_counts);
+    dev_free(t->d_cursor);
+    dev_free(t->d_scan_tmp);
+    t->offsets = nullptr;
+    t->d_counts = nullptr;
+    t->d_cursor = nullptr;
+    t->d_scan_tmp = nullptr;
+    t->bin_cap = 0;
+    t->gen += 1;
+    if (dev_alloc(&t->offsets, (size_t)(nb + 1) * sizeof(int32_t)) != cudaSuccess ||
+        dev_alloc(&t->d_counts, (size_t)nb * sizeof(uint32_t)) != cudaSuccess ||
+        dev_alloc(&t->d_cursor, (size_t)nb * sizeof(int32_t)) != cudaSuccess ||
+        dev_alloc(&t->d_scan_tmp, std::max<size_t>(count_scan_scratch_bytes(nb), 16)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TRK_ENOMEM, "cannot allocate binning arrays for %lld blocks", (long long)nb);
+    }
+    CUDA_TRY(cudaMemset(t->d_counts, 0, (size_t)nb * sizeof(uint32_t)));
+    t->bin_cap = nb;
+    return TRK_OK;
+}
+
 int set_geometry(tracker* t, int bx, int by, int bz)
 {
     const int N = t->N;
@@ -232,21 +266,7 @@ int set_geometry(tracker* t, int bx, int by, int bz)
     t->g.nb3 = N / bz;
     t->nblocks = (int64_t)t->g.nb1 * t->g.nb2 * t->g.nb3;
     t->key_bits = ilog2(t->nblocks);
-    dev_free(t->offsets);
-    dev_free(t->d_counts);
-    dev_free(t->d_cursor);
-    dev_free(t->d_scan_tmp);
-    t->offsets = nullptr;
-    t->d_counts = nullptr;
-    t->d_cursor = nullptr;
-    t->d_scan_tmp = nullptr;
-    t->gen += 1;
-    CUDA_TRY(dev_alloc(&t->offsets, (size_t)(t->nblocks + 1) * sizeof(int32_t)));
-    CUDA_TRY(dev_alloc(&t->d_counts, (size_t)t->nblocks * sizeof(uint32_t)));
-    CUDA_TRY(dev_alloc(&t->d_cursor, (size_t)t->nblocks * sizeof(int32_t)));
-    CUDA_TRY(dev_alloc(&t->d_scan_tmp, std::max<size_t>(count_scan_scratch_bytes(t->nblocks), 16)));
-    CUDA_TRY(cudaMemset(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t)));
-    return TRK_OK;
+    return ensure_bin(t, t->nblocks);
 }
 
 // keys and permutation of np particles (every binning)
@@ -539,6 +559,28 @@ bool column_available(const tracker* t)
            t->g.lb3 == LBLK;
 }
 
+bool default_shape(const tracker* t) { return t->g.lb1 == LBLK && t->g.lb2 == LBLK && t->g.lb3 == LBLK; }
+
+// Binning geometry of a step path: the tracker's block shape, except that the
+// direct path bins by cubes of edge dir_blk when the shape is the default
+// (the direct kernel takes 256 grouped particles per CTA whatever the blocks
+// are; the block edge only sets how compact each CTA's particles are).
+struct BinGeom {
+    GridGeom g;
+    int64_t nb;
+};
+BinGeom geom_of(const tracker* t, int path)
+{
+    if (path != TRK_STEP_DIRECT || t->dir_blk == BLK || !default_shape(t)) return {t->g, t->nblocks};
+    BinGeom b{t->g, 0};
+    const int lb = ilog2(t->dir_blk);
+    b.g.lb1 = b.g.lb2 = b.g.lb3 = lb;
+    b.g.nb1 = b.g.nb2 = b.g.nb3 = t->N >> lb;
+    b.nb = (int64_t)b.g.nb1 * b.g.nb2 * b.g.nb3;
+    return b;
+}
+bool same_geom(const GridGeom& a, const GridGeom& b) { return a.lb1 == b.lb1 && a.lb2 == b.lb2 && a.lb3 == b.lb3; }
+
 void destroy_nm_texture(tracker* t)
 {
     if (t->nm_tex) cudaDestroyTextureObject(t->nm_tex);
@@ -657,7 +699,6 @@ void remember(std::vector<std::pair<uint64_t, int>>& cache, uint64_t sig, int ch
 // the faster: the crossover moves with the grid (L2 holds a 256^3 float32
 // field but not a 512^3 one) and with the scheme.
 constexpr double kProbeMin = 0.01, kProbeMax = 0.25;
-constexpr int kProbeSteps = 4;   // two timed steps per kernel (the first launch of a kernel may load its module)
 
 // The kernel tracker_advance (and, between BLOCK and DIRECT, tracker_interpolate)
 // uses for np particles before any timing.
@@ -682,10 +723,11 @@ int advance_step(tracker* t, int64_t np, int path, int mode, int ab_order, int h
 {
     const int nxt = cur ^ 1;
     const bool ab = mode == MODE_AB2;
+    const BinGeom bg = geom_of(t, path);
     {
         ProfScope ps(t, PROF_BIN);
         const float* rin = ab && hist > 0 ? (first ? rhs : t->rhs_s[cur]) : nullptr;
-        CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->d_scan_tmp, t->stream,
+        CUDA_TRY(launch_count_scan(t->d_counts, bg.nb, t->offsets, t->d_cursor, t->d_scan_tmp, t->stream,
                                    &t->launches));
         CUDA_TRY(launch_scatter_state(np, t->keys, t->d_cursor, first ? pos : t->pos_s[cur],
                                       first ? nullptr : t->id_s[cur], rin, 3 * (ab_order - 1), t->pos_s[nxt],
@@ -714,6 +756,7 @@ int advance_step(tracker* t, int64_t np, int path, int mode, int ab_order, int h
         return TRK_OK;
     }
     BlockArgs a = base_args(t);
+    a.g = bg.g;
     a.np = np;
     a.dt = dt;
     a.perm = nullptr;   // the state is grouped: read and written at j
@@ -726,6 +769,133 @@ int advance_step(tracker* t, int64_t np, int path, int mode, int ab_order, int h
     a.counts = t->d_counts;
     if (path == TRK_STEP_DIRECT) CUDA_TRY(launch_direct(t, mode, a));
     else CUDA_TRY(launch_block(t, mode, a));
+    return TRK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tuner of the time-step path.  A candidate fixes the step kernel and its
+// launch shape: the column kernel's segment length (x3 slabs per work item),
+// the direct kernel's binning block edge, the block kernel's halo copy
+// (cp.async or tensor copies).  On the first tracker_advance call of a
+// workload (grid, kernel, storage, SM count, density bucket, scheme) with
+// enough steps, every candidate runs kTuneStepsPerCand real steps of the call,
+// timed with CUDA events, and the fastest is kept for the rest of the call and
+// for later calls; all candidates give bit-identical steps.  Decisions are
+// also appended to the file named by the environment variable TRK_TUNE_CACHE
+// (if set), which a new tracker reads at creation.
+// ---------------------------------------------------------------------------
+constexpr int64_t kTuneMinNp = 32768;   // below this a step is launch-bound: no timing
+constexpr int kTuneStepsPerCand = 2;    // the first run of a kernel may load its module: keep the faster
+
+struct Cand {
+    int path, dir_blk, col_seg, tma;
+};
+
+std::string tune_key(const tracker* t, int64_t np, int mode, int ab_order)
+{
+    const double dens = (double)np / ((double)t->N * t->N * t->N);
+    const int bucket = (int)std::floor(2.0 * std::log2(dens));   // half-octave density buckets
+    char buf[200];
+    snprintf(buf, sizeof(buf), "advance N=%d family=%d I=%d m=%d storage=%d sm=%d dens2=%d mode=%d order=%d", t->N,
+             t->family, t->I, t->m, t->storage, t->nsm, bucket, mode, ab_order);
+    return buf;
+}
+
+bool valid_cand(const tracker* t, const Cand& c)
+{
+    const bool path_ok = c.path == TRK_STEP_DIRECT || c.path == TRK_STEP_BLOCK ||
+                         (c.path == TRK_STEP_COLUMN && column_available(t));
+    return path_ok && is_pow2(c.dir_blk) && c.dir_blk <= t->N && is_pow2(c.col_seg) && c.col_seg <= MAXSEG &&
+           (c.tma == 0 || c.tma == 1);
+}
+
+void apply_cand(tracker* t, const Cand& c)
+{
+    if (t->dir_blk == c.dir_blk && t->col_seg == c.col_seg && t->auto_tma == (c.tma != 0)) return;
+    t->dir_blk = c.dir_blk;
+    t->col_seg = c.col_seg;
+    t->auto_tma = c.tma != 0;
+    t->gen += 1;                      // captured step graphs hold the old launch shapes
+}
+
+void remember_tuning(tracker* t, const std::string& key, const Cand& c, bool persist)
+{
+    if (t->step_tune.size() >= kCacheMax) t->step_tune.erase(t->step_tune.begin());
+    t->step_tune.push_back({key, {c.path, c.dir_blk, c.col_seg, c.tma}});
+    const char* path = getenv("TRK_TUNE_CACHE");
+    if (!persist || !path || !*path) return;
+    if (FILE* f = fopen(path, "a")) {
+        fprintf(f, "%s|%d %d %d %d\n", key.c_str(), c.path, c.dir_blk, c.col_seg, c.tma);
+        fclose(f);
+    }
+}
+
+bool lookup_tuning(const tracker* t, const std::string& key, Cand* out)
+{
+    for (auto it = t->step_tune.rbegin(); it != t->step_tune.rend(); ++it)
+        if (it->first == key) {
+            *out = Cand{it->second[0], it->second[1], it->second[2], it->second[3]};
+            return true;
+        }
+    return false;
+}
+
+// Decisions of earlier processes (TRK_TUNE_CACHE): lines "key|path dir_blk
+// col_seg tma"; malformed lines and values this tracker cannot run are skipped.
+void load_tune_file(tracker* t)
+{
+    const char* path = getenv("TRK_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        char* bar = strchr(line, '|');
+        if (!bar) continue;
+        *bar = 0;
+        Cand c{};
+        if (sscanf(bar + 1, "%d %d %d %d", &c.path, &c.dir_blk, &c.col_seg, &c.tma) != 4 || !valid_cand(t, c)) continue;
+        remember_tuning(t, line, c, false);
+    }
+    fclose(f);
+}
+
+// The candidates for np particles: the column kernel (or, without one, the
+// block kernel with both halo copies) above kProbeMin particles per cell, the
+// direct kernel below kProbeMax, each with its launch-shape variants.
+std::vector<Cand> tune_candidates(const tracker* t, int64_t np)
+{
+    std::vector<Cand> c;
+    const double dens = (double)np / ((double)t->N * t->N * t->N);
+    if (dens >= kProbeMin && default_shape(t)) {
+        if (column_available(t)) {
+            for (int seg : {4, 8, 16})
+                if (seg <= t->g.nb3) c.push_back({TRK_STEP_COLUMN, BLK, seg, 1});
+        } else {
+            // the tensor-copy halo measured faster than cp.async in every case
+            // (float32 and float64, I = 4, 6, 8, steps and interpolation)
+            c.push_back({TRK_STEP_BLOCK, BLK, 8, 1});
+        }
+    }
+    if (dens <= kProbeMax) {
+        if (default_shape(t)) {
+            for (int b : {8, 16, 32})
+                if (b <= t->N) c.push_back({TRK_STEP_DIRECT, b, 8, 1});
+        } else {
+            c.push_back({TRK_STEP_DIRECT, BLK, 8, 1});
+        }
+    }
+    return c;
+}
+
+// keys and block counts of the grouped state pos_s[cur] in geometry bg (after
+// a change of binning geometry between two steps)
+int rekey(tracker* t, int64_t np, int cur, const BinGeom& bg)
+{
+    ProfScope ps(t, PROF_BIN);
+    CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)bg.nb * sizeof(uint32_t), t->stream));
+    CUDA_TRY(launch_keys_count(bg.g, np, t->pos_s[cur], t->keys, t->d_counts, t->d_flags, t->stream));
+    t->launches += 1;
     return TRK_OK;
 }
 
@@ -799,6 +969,7 @@ int tracker_create(tracker** out, int N, double L, int family, int I, int m, int
         tracker_destroy(t);
         return rc;
     }
+    load_tune_file(t);
     *out = t;
     return TRK_OK;
 }
@@ -989,6 +1160,42 @@ int tracker_last_step_kernel(const tracker* t)
     return t->last_kernel;
 }
 
+int tracker_set_tuning(tracker* t, const trk_tuning* p)
+{
+    if (!t) return fail(TRK_EINVAL, "tracker is NULL");
+    if (!p) {   // back to the automatic choice
+        t->step_kernel = TRK_STEP_AUTO;
+        t->halo_copy = TRK_HALO_AUTO;
+        apply_cand(t, Cand{TRK_STEP_AUTO, BLK, 8, 1});
+        t->gen += 1;
+        return TRK_OK;
+    }
+    if (p->step_kernel != TRK_STEP_BLOCK && p->step_kernel != TRK_STEP_COLUMN && p->step_kernel != TRK_STEP_DIRECT)
+        return fail(TRK_EINVAL, "step_kernel must be TRK_STEP_BLOCK, _COLUMN or _DIRECT");
+    if (p->halo_copy != TRK_HALO_ASYNC && p->halo_copy != TRK_HALO_TMA)
+        return fail(TRK_EINVAL, "halo_copy must be TRK_HALO_ASYNC or TRK_HALO_TMA");
+    const Cand c{p->step_kernel, p->direct_block, p->column_segment, p->halo_copy == TRK_HALO_TMA ? 1 : 0};
+    if (!valid_cand(t, c))
+        return fail(TRK_EINVAL, "invalid tuning (direct_block a power of two <= N, column_segment a power of two "
+                                "<= %d, a column kernel only for F32 storage with I = 4, 6 and 8^3 blocks)", MAXSEG);
+    t->step_kernel = c.path;
+    t->halo_copy = p->halo_copy;
+    apply_cand(t, c);
+    t->gen += 1;
+    return TRK_OK;
+}
+
+int tracker_get_tuning(const tracker* t, trk_tuning* out)
+{
+    if (!t || !out) return fail(TRK_EINVAL, "NULL argument");
+    out->step_kernel = t->last_tuning[0];
+    out->direct_block = t->last_tuning[1];
+    out->column_segment = t->last_tuning[2];
+    out->halo_copy = t->last_tuning[3] ? TRK_HALO_TMA : TRK_HALO_ASYNC;
+    out->source = t->tune_source;
+    return TRK_OK;
+}
+
 int tracker_set_halo_copy(tracker* t, int kind)
 {
     if (!t) return fail(TRK_EINVAL, "tracker is NULL");
@@ -1122,34 +1329,51 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     const int mode = k ? MODE_AB2 : MODE_RK2;
     const int ab_order = k ? k : 2;
     int path = step_path(t, np);
-    // AUTO between the column and the direct kernel: a cached timing decision,
-    // or time both now (both give bit-identical steps and share the binning)
-    bool probe = false;
-    const uint64_t sig = mix(mix(mix(0, (uint64_t)np), (uint64_t)mode), (uint64_t)ab_order);
-    if (t->step_kernel == TRK_STEP_AUTO && column_available(t) && np > 0) {
-        int cached = -1;
-        for (const auto& e : t->path_cache)
-            if (e.first == sig) cached = e.second;
-        if (cached >= 0) {
-            path = cached;
+    // AUTO: a remembered tuning decision for this workload, or time the
+    // candidates now (steps of this call), or the density rule with the
+    // default launch shapes
+    std::vector<Cand> cands;
+    std::string key;
+    t->tune_source = t->step_kernel == TRK_STEP_AUTO ? TRK_TUNE_DEFAULT : TRK_TUNE_FIXED;
+    if (t->step_kernel == TRK_STEP_AUTO && np > 0) {
+        key = tune_key(t, np, mode, ab_order);
+        Cand hit{};
+        if (lookup_tuning(t, key, &hit)) {
+            apply_cand(t, hit);
+            path = hit.path;
+            t->tune_source = TRK_TUNE_CACHED;
         } else {
-            const double dens = (double)np / ((double)t->N * t->N * t->N);
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
             CUDA_TRY(cudaStreamIsCapturing(t->stream, &cs));
-            probe = dens >= kProbeMin && dens <= kProbeMax && steps >= kProbeSteps + 2 &&
-                    cs == cudaStreamCaptureStatusNone;
+            cands = tune_candidates(t, np);
+            const bool timed = np >= kTuneMinNp && cands.size() >= 2 &&
+                               steps >= kTuneStepsPerCand * (int)cands.size() + 2 && cs == cudaStreamCaptureStatusNone;
+            if (!timed) cands.clear();
+            apply_cand(t, Cand{path, BLK, 8, 1});
         }
     }
     if (path != TRK_STEP_DIRECT && (rc = check_block_kernel_shape(t))) return rc;
     if (np == 0 || steps == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
     if ((rc = ensure_state(t, np))) return rc;
-    if ((path == TRK_STEP_DIRECT || probe) && (rc = ensure_node_major(t))) return rc;
+    bool any_direct = path == TRK_STEP_DIRECT;
+    for (const Cand& c : cands) {
+        any_direct = any_direct || c.path == TRK_STEP_DIRECT;
+        Cand save{path, t->dir_blk, t->col_seg, t->auto_tma};
+        apply_cand(t, c);
+        rc = ensure_bin(t, geom_of(t, c.path).nb);
+        apply_cand(t, save);
+        if (rc) return rc;
+    }
+    if ((rc = ensure_bin(t, geom_of(t, path).nb))) return rc;
+    if (any_direct && (rc = ensure_node_major(t))) return rc;
     // initial keys and block counts from the caller's positions
+    GridGeom last_g = geom_of(t, path).g;
     {
+        const BinGeom bg = geom_of(t, path);
         ProfScope ps(t, PROF_BIN);
-        CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
-        CUDA_TRY(launch_keys_count(t->g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
+        CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)bg.nb * sizeof(uint32_t), t->stream));
+        CUDA_TRY(launch_keys_count(bg.g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
         t->launches += 1;
     }
     // the first step reads the caller's arrays; the others ping-pong between
@@ -1160,6 +1384,12 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     int cur = 0, rest = steps;
     bool first = true;
     auto eager = [&](int p) {
+        const BinGeom bg = geom_of(t, p);
+        if (!first && !same_geom(bg.g, last_g)) {   // counts of the last step are in another geometry
+            const int r = rekey(t, np, cur, bg);
+            if (r) return r;
+        }
+        last_g = bg.g;
         const int r = advance_step(t, np, p, mode, ab_order, hist, dt, cur, first, first ? pos : nullptr,
                                    first ? rhs : nullptr);
         if (r == TRK_OK) {
@@ -1171,37 +1401,52 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
         return r;
     };
     if ((rc = eager(path))) return rc;
-    if (probe) {
-        // kProbeSteps eager steps, the first half on the column kernel, then on the direct one
-        cudaEvent_t ev[kProbeSteps + 1] = {};
+    if (!cands.empty()) {
+        // kTuneStepsPerCand timed steps per candidate, then the fastest
+        const int nst = kTuneStepsPerCand * (int)cands.size();
+        std::vector<cudaEvent_t> ev(nst + 1, nullptr);
         for (auto& e : ev)
             if (cudaEventCreate(&e) != cudaSuccess) rc = fail(TRK_ECUDA, "cudaEventCreate failed");
-        for (int i = 0; rc == TRK_OK && i < kProbeSteps; ++i) {
+        for (int i = 0; rc == TRK_OK && i < nst; ++i) {
+            const Cand& c = cands[i / kTuneStepsPerCand];
+            apply_cand(t, c);
             if (cudaEventRecord(ev[i], t->stream) != cudaSuccess) rc = fail(TRK_ECUDA, "cudaEventRecord failed");
-            if (rc == TRK_OK) rc = eager(2 * i < kProbeSteps ? TRK_STEP_COLUMN : TRK_STEP_DIRECT);
+            if (rc == TRK_OK) rc = eager(c.path);
         }
-        float ms[kProbeSteps] = {};
-        if (rc == TRK_OK && (cudaEventRecord(ev[kProbeSteps], t->stream) != cudaSuccess ||
-                             cudaEventSynchronize(ev[kProbeSteps]) != cudaSuccess))
-            rc = fail(TRK_ECUDA, "timing the step kernels failed");
-        for (int i = 0; rc == TRK_OK && i < kProbeSteps; ++i)
+        std::vector<float> ms(nst, 0.f);
+        if (rc == TRK_OK && (cudaEventRecord(ev[nst], t->stream) != cudaSuccess || cudaEventSynchronize(ev[nst]) != cudaSuccess))
+            rc = fail(TRK_ECUDA, "timing the step candidates failed");
+        for (int i = 0; rc == TRK_OK && i < nst; ++i)
             if (cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) != cudaSuccess) rc = fail(TRK_ECUDA, "cudaEventElapsedTime failed");
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
         if (rc) return rc;
-        float col = ms[0], dir = ms[kProbeSteps / 2];
-        for (int i = 1; i < kProbeSteps / 2; ++i) {
-            col = std::min(col, ms[i]);
-            dir = std::min(dir, ms[kProbeSteps / 2 + i]);
+        int best = 0;
+        float best_ms = 0.f;
+        for (int c = 0; c < (int)cands.size(); ++c) {
+            float m = ms[c * kTuneStepsPerCand];
+            for (int r = 1; r < kTuneStepsPerCand; ++r) m = std::min(m, ms[c * kTuneStepsPerCand + r]);
+            if (c == 0 || m < best_ms) {
+                best = c;
+                best_ms = m;
+            }
         }
-        path = dir < col ? TRK_STEP_DIRECT : TRK_STEP_COLUMN;
-        remember(t->path_cache, sig, path);
+        apply_cand(t, cands[best]);
+        path = cands[best].path;
+        remember_tuning(t, key, cands[best], true);
+        t->tune_source = TRK_TUNE_TIMED;
+        const BinGeom bg = geom_of(t, path);
+        if (!same_geom(bg.g, last_g)) {
+            if ((rc = rekey(t, np, cur, bg))) return rc;
+            last_g = bg.g;
+        }
     }
     for (; rest > 0 && k && hist < k - 1;)
         if ((rc = eager(path))) return rc;
     if (!t->prof && rest >= 2) {
         uint64_t key = mix(mix(mix(mix(0, (uint64_t)np), (uint64_t)mode), t->gen), dbits(dt));
         key = mix(mix(mix(key, (uint64_t)(uintptr_t)t->field), (uint64_t)ab_order), (uint64_t)path);
+        key = mix(mix(mix(key, (uint64_t)t->dir_blk), (uint64_t)t->col_seg), (uint64_t)t->auto_tma);
         const int c0 = cur;
         rc = replay_graph(t, t->adv_graph, mix(key, (uint64_t)c0), rest / 2, [&]() {
             int r = advance_step(t, np, path, mode, ab_order, hist, dt, c0, false, nullptr, nullptr);
@@ -1215,6 +1460,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
         cur ^= 1;
     }
     t->last_kernel = path;
+    t->last_tuning = {path, t->dir_blk, t->col_seg, halo_tmap(t, mode) ? 1 : 0};
     ProfScope ps(t, PROF_OTHER);
     CUDA_TRY(launch_unpermute_pos(np, t->pos_s[cur], t->id_s[cur], pos, t->stream));
     t->launches += 1;
