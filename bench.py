@@ -54,10 +54,16 @@ def parse():
                     help="step kernel of the headline workload (default: auto, the tracker's timed choice)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other configurations (precision, batching, differentiation, small, sparse)")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6],
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 7],
                     help="2: the headline workload (default); 1 small, 3 precision, 4 batching, 5 adjoint, "
-                         "6 the paper's sparse tracer density")
+                         "6 the paper's sparse tracer density, 7 the step tuner's table against density")
     ap.add_argument("--sparse-n", type=int, default=1024, help="grid of config 6 (1.5e-3 tracers per cell)")
+    ap.add_argument("--direct-block", type=int, default=0,
+                    help="with --step-kernel direct: the binning block edge of the direct path (0: default)")
+    ap.add_argument("--halo-copy", default="auto", choices=["auto", "async", "tma"],
+                    help="the block kernel's halo staging (config 3; default: the tracker's choice)")
+    ap.add_argument("--c3-n", type=int, default=1024, help="grid of config 3 (smaller grids for profiling)")
+    ap.add_argument("--c3-np-log2", type=int, default=27, help="log2 of the tracer count of config 3")
     return ap.parse_args()
 
 
@@ -404,6 +410,8 @@ def run_gb300(args):
     tr = trk.Tracker(N, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
     tr.set_step_kernel({"auto": trk.TRK_STEP_AUTO, "block": trk.TRK_STEP_BLOCK,
                         "column": trk.TRK_STEP_COLUMN, "direct": trk.TRK_STEP_DIRECT}[args.step_kernel])
+    if args.step_kernel == "direct" and args.direct_block:
+        tr.set_tuning(step_kernel=trk.TRK_STEP_DIRECT, direct_block=args.direct_block)
     tr.set_field(torch.from_numpy(field).to(dev))
     p = torch.from_numpy(pos).to(dev)
     stream = torch.cuda.current_stream()
@@ -667,7 +675,8 @@ def config3_block(trk, dev, stream, dev_index, args, fma):
     import oracle
     import synth
 
-    N3, KM, NPART, NSUB, I8, M8 = 1024, 340, 1 << 27, 100_000, 8, 3
+    N3, NPART, I8, M8 = args.c3_n, 1 << args.c3_np_log2, 8, 3
+    KM, NSUB = N3 // 3, min(100_000, NPART)
     pos = synth.uniform_particles_torch(NPART, 3, device=dev)
     sub = pos[:, :NSUB].cpu().numpy()
     cell, frac = oracle.split(sub, N3)
@@ -691,12 +700,14 @@ def config3_block(trk, dev, stream, dev_index, args, fma):
     del idx_t
     torch.cuda.empty_cache()
     rms_u, rms_g = float(np.sqrt(np.mean(rms[:3] ** 2))), float(np.sqrt(np.mean(rms[3:] ** 2)))
-    out = {"workload": "1024^3 u (3) + grad u (9, spectral), |k|<=340, 2^27 uniform tracers (fp64 positions), "
-                       "spline I=8 m=3, interpolation; error vs the fp64 oracle on 1e5 tracers",
+    out = {"workload": f"{N3}^3 u (3) + grad u (9, spectral), |k|<={KM}, 2^{args.c3_np_log2} uniform tracers "
+                       f"(fp64 positions), spline I=8 m=3, interpolation; error vs the fp64 oracle on {NSUB} tracers",
            "metric": "particles/s", "unit": "particles/s", "prep_s": prep_s}
     for sname, storage in (("f32", trk.TRK_F32), ("bf16x2", trk.TRK_BF16X2)):
         for C in (3, 12):
             t = trk.Tracker(N3, family=trk.TRK_SPLINE, I=I8, m=M8, storage=storage)
+            t.set_halo_copy({"auto": trk.TRK_HALO_AUTO, "async": trk.TRK_HALO_ASYNC,
+                             "tma": trk.TRK_HALO_TMA}[args.halo_copy])
             t.set_field(f12[:C])
             o = torch.empty((C, NPART), dtype=torch.float32, device=dev)
             call = lambda: t.interpolate(pos, out=o)  # noqa: E731
@@ -927,6 +938,60 @@ def sparse_ncu_record(kind):
     return e
 
 
+def tuner_table(trk, dev, stream, dev_index, args, fma):
+    """The step tuner against tracer density (256^3 float32 field, spline I = 6,
+    RK2 and AB2, dt = 5e-3): per density, the ms per step of every candidate
+    launch shape fixed, and the one the tuner picks on its own (first call of
+    24 steps)."""
+    import torch
+
+    import synth
+
+    Nt = 256
+    field = torch.from_numpy(synth.velocity_field_np(Nt, 85, 1001).astype("float32")).to(dev)
+    rows = []
+    cands = [("column seg 4", dict(step_kernel=trk.TRK_STEP_COLUMN, column_segment=4)),
+             ("column seg 8", dict(step_kernel=trk.TRK_STEP_COLUMN, column_segment=8)),
+             ("column seg 16", dict(step_kernel=trk.TRK_STEP_COLUMN, column_segment=16)),
+             ("block (tensor-copy halo)", dict(step_kernel=trk.TRK_STEP_BLOCK, halo_copy=trk.TRK_HALO_TMA)),
+             ("block (cp.async halo)", dict(step_kernel=trk.TRK_STEP_BLOCK, halo_copy=trk.TRK_HALO_ASYNC)),
+             ("direct edge 8", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=8)),
+             ("direct edge 16", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=16)),
+             ("direct edge 32", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=32))]
+    names = {trk.TRK_STEP_COLUMN: "column", trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_DIRECT: "direct"}
+    for scheme, sname in ((trk.TRK_RK2, "RK2"), (trk.TRK_AB2, "AB2")):
+        for dens in (1.5e-3, 1 / 64, 1 / 32, 1 / 16, 1 / 8, 1 / 4, 1 / 2):
+            n = int(dens * Nt ** 3)
+            pos0 = synth.uniform_particles_torch(n, 8, device=dev)
+            row = {"scheme": sname, "per_cell": dens, "np": n, "ms_per_step": {}}
+            for label, tun in [("tuner", None)] + cands:
+                t = trk.Tracker(Nt, family=trk.TRK_SPLINE, I=I, m=M, storage=trk.TRK_F32)
+                if tun is not None:
+                    t.set_tuning(**tun)
+                t.set_field(field)
+                p = pos0.clone()
+                rhs = torch.zeros((3, n), dtype=torch.float32, device=dev) if scheme == trk.TRK_AB2 else None
+                t.advance(p, DT, 24, scheme, rhs=rhs)       # the tuner's first call (timed candidates)
+                if tun is None:
+                    info = t.tuning()
+                    row["tuner_pick"] = {"kernel": names.get(info["step_kernel"], "?"),
+                                         "direct_block": info["direct_block"],
+                                         "column_segment": info["column_segment"], "source": info["source"]}
+                ms, _, _ = timed(lambda: t.advance(p, DT, 20, scheme, rhs=rhs, history_valid=scheme != trk.TRK_RK2),
+                                 stream, dev_index, min_s=0.2, max_reps=10)
+                row["ms_per_step"][label] = ms / 20
+                try:
+                    t.sync()
+                except trk.TrackerError as e:
+                    if e.status != trk.TRK_ECFL:
+                        raise
+                t.close()
+            rows.append(row)
+            del pos0
+            torch.cuda.empty_cache()
+    return {"value": 0.0, "workload": "tuner table: 256^3 fp32, spline I=6, RK2 and AB2 against density", "rows": rows}
+
+
 def run_single_config(args):
     """--config N: one configuration on its own, printed as one JSON line."""
     import torch
@@ -940,7 +1005,8 @@ def run_single_config(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     fma = {"fp32": trk.tracker_probe_fma(trk.TRK_DTYPE_F32), "fp64": trk.tracker_probe_fma(trk.TRK_DTYPE_F64)}
-    fn = {1: config1_block, 3: config3_block, 4: config4_block, 5: config5_block, 6: config6_block}[args.config]
+    fn = {1: config1_block, 3: config3_block, 4: config4_block, 5: config5_block, 6: config6_block,
+          7: tuner_table}[args.config]
     d = fn(trk, dev, stream, 0, args, fma)
     line = {"metric": d.get("metric", METRIC), "value": d["value"], "unit": d.get("unit", UNIT), "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",

@@ -346,7 +346,10 @@ cudaError_t launch_nonempty_list(const int32_t* offsets, int64_t nblocks, int32_
                                  cudaStream_t st, int64_t* launches);
 
 // One persistent launch over all sets (float32 or split-bf16 storage); grid = 2 CTAs per SM.
-cudaError_t launch_batched(int storage, const BatchSet* sets, int nsets, int* ctr, int nsm, cudaStream_t st);
+// maps: null, or three CUtensorMap pointers (AB2 halo boxes of widths 4, 6, 8) for
+// tensor-copy halos of the float32 field
+cudaError_t launch_batched(int storage, const BatchSet* sets, int nsets, int* ctr, int nsm, const void* const* maps,
+                           cudaStream_t st);
 
 // Sets the thread-local message returned by tracker_last_error().
 void set_error_message(const char* msg);

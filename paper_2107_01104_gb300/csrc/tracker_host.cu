@@ -177,6 +177,7 @@ struct tracker {
     // one per stage-2 margin (interpolation and AB: 0, RK2: 1)
     CUtensorMap tmap[2];
     bool tmap_ok[2] = {false, false};
+    CUtensorMap batch_map[3];         // batched sets: AB2 halo boxes of widths 4, 6, 8
     int halo_copy = TRK_HALO_AUTO;    // trk_halo_copy: how the block kernel stages its halo
     bool auto_tma = true;             // TRK_HALO_AUTO's current choice (tensor copies, where there is a map)
     uint32_t* d_counts = nullptr;     // [nblocks] block counts (counting-sort binning of the column path)
@@ -398,26 +399,27 @@ EncodeTiledFn encode_tiled()
 // storage with at least three components (a chunk of three per copy; the
 // last chunk of a C that is not a multiple of three reads zeros beyond C,
 // which no output uses).  Left unset (cp.async staging) otherwise.
-void build_tmaps(tracker* t)
+// the tensor map of the tracker's field with the halo box of kernel width I
+// and stage-2 margin `margin` (tma_box); false if it cannot be made
+bool encode_field_map(const tracker* t, int I, int margin, CUtensorMap* out)
 {
-    t->tmap_ok[0] = t->tmap_ok[1] = false;
-    if ((t->storage != TRK_F32 && t->storage != TRK_F64) || t->C < 3 || !t->field) return;
     const EncodeTiledFn enc = encode_tiled();
-    if (!enc) return;
+    if (!enc || (t->storage != TRK_F32 && t->storage != TRK_F64) || t->C < 3 || !t->field) return false;
     const int esz = t->storage == TRK_F64 ? 8 : 4;
     const cuuint64_t NP = (cuuint64_t)(t->N + 2 * PAD);
     const cuuint64_t dims[4] = {NP, NP, NP, (cuuint64_t)t->C};
     const cuuint64_t strides[3] = {NP * esz, NP * NP * esz, NP * NP * NP * esz};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    for (int margin = 0; margin < 2; ++margin) {
-        const TmaBox b = tma_box(t->I, margin, esz);
-        const cuuint32_t box[4] = {(cuuint32_t)b.BX, (cuuint32_t)b.BY, (cuuint32_t)b.H, 3};
-        const CUresult r = enc(&t->tmap[margin], esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                               4, t->field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        t->tmap_ok[margin] = r == CUDA_SUCCESS;
-    }
+    const TmaBox b = tma_box(I, margin, esz);
+    const cuuint32_t box[4] = {(cuuint32_t)b.BX, (cuuint32_t)b.BY, (cuuint32_t)b.H, 3};
+    return enc(out, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, t->field, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void build_tmaps(tracker* t)
+{
+    for (int margin = 0; margin < 2; ++margin) t->tmap_ok[margin] = encode_field_map(t, t->I, margin, &t->tmap[margin]);
 }
 
 cudaError_t launch_direct(tracker* t, int mode, const BlockArgs& a)
@@ -1539,7 +1541,18 @@ static int batched_launch(tracker* t, const BatchSet* d_desc, int nsets)
 {
     ProfScope ps(t, PROF_STEP);
     CUDA_TRY(cudaMemsetAsync(t->d_ctr, 0, (size_t)nsets * sizeof(int), t->stream));
-    CUDA_TRY(launch_batched(t->storage, d_desc, nsets, t->d_ctr, t->nsm, t->stream));
+    // tensor-copy halos for the halo-staged sets of a float32 field, one box per kernel width
+    const void* maps[3] = {nullptr, nullptr, nullptr};
+    const bool tma = t->halo_copy == TRK_HALO_TMA || (t->halo_copy == TRK_HALO_AUTO && t->auto_tma);
+    if (tma && t->storage == TRK_F32) {
+        bool ok = true;
+        for (int i = 0; i < 3; ++i) {
+            ok = ok && encode_field_map(t, 4 + 2 * i, 0, &t->batch_map[i]);
+            maps[i] = &t->batch_map[i];
+        }
+        if (!ok) maps[0] = maps[1] = maps[2] = nullptr;
+    }
+    CUDA_TRY(launch_batched(t->storage, d_desc, nsets, t->d_ctr, t->nsm, maps[0] ? maps : nullptr, t->stream));
     t->launches += 1;
     return TRK_OK;
 }
