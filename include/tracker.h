@@ -217,19 +217,17 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     mostly hits in L2 otherwise saturate).  The stage-2
  *     point of RK2 is gathered wherever it lies; TRK_ECFL is raised when it
  *     is more than one cell away.
- *   TRK_STEP_AUTO (default): DIRECT below 0.05 particles per grid cell
+ *   TRK_STEP_AUTO (default): the tuner's choice (see tracker_set_tuning):
+ *     on the first call of a workload with enough steps, every candidate
+ *     kernel and launch shape is timed on real steps of the call and the
+ *     fastest kept; otherwise DIRECT below 0.05 particles per grid cell
  *     (np < 0.05 N^3), else COLUMN where available; without a column kernel
- *     DIRECT below 0.25 per cell, else BLOCK (measured crossovers).  Where the
- *     column kernel exists and the density lies in [0.01, 0.25], the first
- *     tracker_advance call of at least 6 steps for a given (np, scheme) runs
- *     two of its steps on each kernel, timed with CUDA events (the host waits
- *     for them once; skipped while the stream is being captured), and that
- *     and later calls use the faster (the crossover moves with N and the
- *     scheme).  tracker_interpolate uses DIRECT or BLOCK, and in the same
- *     density range its first call per (np, C, deriv, out_dtype) runs both
- *     kernels (they write the same values) and keeps the faster: which one
- *     wins depends on C (the direct kernel gathers every component of a node
- *     at once for C = 3).
+ *     DIRECT below 0.25 per cell, else BLOCK (measured crossovers).
+ *     tracker_interpolate uses DIRECT or BLOCK; between 0.01 and 0.25 per
+ *     cell its first call per (np, C, deriv, out_dtype) runs the block kernel
+ *     with each halo copy and the direct kernel (they write the same values)
+ *     and keeps the fastest: which one wins depends on C (the direct kernel
+ *     gathers every component of a node at once for C = 3).
  * All kernels perform the same floating-point operations in the same
  * order, so their results are bit-identical.  TRK_STEP_COLUMN on a tracker
  * without a column kernel is TRK_EINVAL.  Errors: TRK_EINVAL. */
@@ -256,8 +254,11 @@ int tracker_last_step_kernel(const tracker* t);
  *     conflicts (float32 and float64 storage with at least three
  *     components; elsewhere the cp.async staging is used);
  *   TRK_HALO_AUTO (default): TRK_HALO_TMA where the field has a tensor map
- *     (measured faster in every case: e.g. 0.533 vs 0.708 ms per RK2 step at
- *     256^3, I = 6, 1/16 particle per cell), else TRK_HALO_ASYNC.
+ *     (faster where few particles share a halo: 0.338 vs 0.526 ms per RK2
+ *     step at 256^3, I = 6, 1/64 particle per cell), unless the tuner (the
+ *     first timed tracker_advance or tracker_interpolate call of a workload)
+ *     measured the cp.async halo faster (e.g. 2.93 vs 3.20 ms at 1/2 per
+ *     cell, where the smem reads dominate); else TRK_HALO_ASYNC.
  * Both give bit-identical results.  A tensor copy that does not complete
  * within its wait limit skips its block and makes tracker_sync return
  * TRK_ECUDA.  Errors: TRK_EINVAL. */
@@ -286,10 +287,11 @@ typedef struct {
  * particles times every candidate launch shape on 2 of its own steps (CUDA
  * events; the host waits once; skipped while the stream is being captured)
  * and keeps the fastest for the rest of the call and for later calls
- * (TRK_TUNE_TIMED, then TRK_TUNE_CACHED).  Candidates: above 0.01 particles
- * per cell the column kernel with segments 4, 8, 16 (or, without one, the
- * block kernel), below 0.25 per cell the direct kernel
- * with block edges 8, 16, 32.  Other calls use the density rule of
+ * (TRK_TUNE_TIMED, then TRK_TUNE_CACHED).  Candidates: from 0.01 particles
+ * per cell on, the column kernel with segments 8 and 16; the block kernel
+ * with tensor-copy and with cp.async halos from 0.1 per cell on (from 0.01
+ * without a column kernel); the direct kernel with block edges 8 and 16 up
+ * to one particle per cell.  Other calls use the density rule of
  * tracker_set_step_kernel with the default shape (TRK_TUNE_DEFAULT).  Every
  * candidate gives bit-identical steps.  When the environment variable
  * TRK_TUNE_CACHE names a file, decisions are appended to it (one line per

@@ -360,6 +360,8 @@ const void* halo_tmap(const tracker* t, int mode)
     return &t->tmap[margin];
 }
 
+bool halo_tmap_exists(const tracker* t, int mode) { return t->tmap_ok[mode == MODE_RK2 ? 1 : 0]; }
+
 cudaError_t launch_block(tracker* t, int mode, const BlockArgs& a)
 {
     ProfScope ps(t, PROF_STEP);
@@ -862,31 +864,32 @@ void load_tune_file(tracker* t)
     fclose(f);
 }
 
-// The candidates for np particles: the column kernel (or, without one, the
-// block kernel with both halo copies) above kProbeMin particles per cell, the
-// direct kernel below kProbeMax, each with its launch-shape variants.
+// The candidates for np particles (measured on GB300, 256^3 float32, spline
+// I = 6, RK2 and AB2 from 1.5e-3 to 1/2 particle per cell: the winners were
+// always among these): the column kernel with segments of 8 and 16 slabs
+// from kProbeMin particles per cell on; the block kernel with both halo
+// copies (the tensor-copy box wins where few particles share a halo, the
+// bank-conflict-free cp.async layout where many do) from kBlockMin on, or from
+// kProbeMin on without a column kernel; the direct kernel with binning edges
+// 8 and 16 up to one particle per cell.  Other block shapes than the default
+// run only the direct kernel.
+constexpr double kBlockMin = 0.1;
 std::vector<Cand> tune_candidates(const tracker* t, int64_t np)
 {
     std::vector<Cand> c;
     const double dens = (double)np / ((double)t->N * t->N * t->N);
-    if (dens >= kProbeMin && default_shape(t)) {
-        if (column_available(t)) {
-            for (int seg : {4, 8, 16})
-                if (seg <= t->g.nb3) c.push_back({TRK_STEP_COLUMN, BLK, seg, 1});
-        } else {
-            // the tensor-copy halo measured faster than cp.async in every case
-            // (float32 and float64, I = 4, 6, 8, steps and interpolation)
-            c.push_back({TRK_STEP_BLOCK, BLK, 8, 1});
-        }
+    if (!default_shape(t)) return {Cand{TRK_STEP_DIRECT, BLK, 8, 1}};
+    const bool col = column_available(t);
+    if (col && dens >= kProbeMin)
+        for (int seg : {8, 16})
+            if (seg <= t->g.nb3) c.push_back({TRK_STEP_COLUMN, BLK, seg, 1});
+    if (dens >= (col ? kBlockMin : kProbeMin)) {
+        if (t->tmap_ok[0] && t->tmap_ok[1]) c.push_back({TRK_STEP_BLOCK, BLK, 8, 1});
+        c.push_back({TRK_STEP_BLOCK, BLK, 8, 0});
     }
-    if (dens <= kProbeMax) {
-        if (default_shape(t)) {
-            for (int b : {8, 16, 32})
-                if (b <= t->N) c.push_back({TRK_STEP_DIRECT, b, 8, 1});
-        } else {
-            c.push_back({TRK_STEP_DIRECT, BLK, 8, 1});
-        }
-    }
+    if (dens <= 1.0)
+        for (int b : {8, 16})
+            if (b <= t->N) c.push_back({TRK_STEP_DIRECT, b, 8, 1});
     return c;
 }
 
@@ -1254,6 +1257,7 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     // now (they write the same values; the better one depends on density, C
     // and the grid)
     bool probe = false;
+    int interp_choice = -1;   // remembered: 0 block (cp.async halo), 1 block (tensor copy), 2 direct
     const uint64_t sig = mix(mix(mix(mix(0x1f, (uint64_t)np), (uint64_t)t->C), (uint64_t)deriv), (uint64_t)out_dtype);
     const bool block_shape = t->g.lb1 == LBLK && t->g.lb2 == LBLK && t->g.lb3 == LBLK;
     if (t->step_kernel == TRK_STEP_AUTO && np > 0 && block_shape) {
@@ -1261,7 +1265,8 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
         for (const auto& e : t->interp_cache)
             if (e.first == sig) cached = e.second;
         if (cached >= 0) {
-            direct = cached == TRK_STEP_DIRECT;
+            direct = cached == 2;
+            interp_choice = cached;
         } else {
             const double dens = (double)np / ((double)t->N * t->N * t->N);
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1282,30 +1287,48 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     a.out_f64 = out_dtype == TRK_DTYPE_F64;
     const int mode = deriv ? MODE_INTERP_DERIV : MODE_INTERP;
     if (probe) {
-        cudaEvent_t ev[3] = {};
+        // the block kernel with each halo copy it has, then the direct kernel;
+        // all write the same values, the fastest is remembered
+        const bool saved = t->auto_tma;
+        std::vector<int> kinds;   // 0: block, cp.async halo; 1: block, tensor copy; 2: direct
+        if (t->halo_copy == TRK_HALO_AUTO && halo_tmap_exists(t, mode)) kinds.push_back(1);
+        kinds.push_back(t->halo_copy == TRK_HALO_TMA && halo_tmap_exists(t, mode) ? 1 : 0);
+        kinds.push_back(2);
+        std::vector<cudaEvent_t> ev(kinds.size() + 1, nullptr);
         for (auto& e : ev)
             if (cudaEventCreate(&e) != cudaSuccess) rc = fail(TRK_ECUDA, "cudaEventCreate failed");
-        float tb = 0, td = 0;
+        std::vector<float> ms(kinds.size(), 0.f);
         if (rc == TRK_OK) {
             cudaError_t e = cudaEventRecord(ev[0], t->stream);
-            if (e == cudaSuccess) e = launch_block(t, mode, a);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[1], t->stream);
-            if (e == cudaSuccess) e = launch_direct(t, mode, a);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2], t->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&tb, ev[0], ev[1]);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&td, ev[1], ev[2]);
+            for (size_t i = 0; e == cudaSuccess && i < kinds.size(); ++i) {
+                t->auto_tma = kinds[i] == 1;
+                e = kinds[i] == 2 ? launch_direct(t, mode, a) : launch_block(t, mode, a);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[i + 1], t->stream);
+            }
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+            for (size_t i = 0; e == cudaSuccess && i < kinds.size(); ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
             if (e != cudaSuccess) rc = fail(TRK_ECUDA, "timing the interpolation kernels: %s", cudaGetErrorString(e));
         }
+        t->auto_tma = saved;
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
         if (rc) return rc;
-        remember(t->interp_cache, sig, td < tb ? TRK_STEP_DIRECT : TRK_STEP_BLOCK);
-        t->last_kernel = td < tb ? TRK_STEP_DIRECT : TRK_STEP_BLOCK;
+        size_t best = 0;
+        for (size_t i = 1; i < kinds.size(); ++i)
+            if (ms[i] < ms[best]) best = i;
+        remember(t->interp_cache, sig, kinds[best]);
+        t->last_kernel = kinds[best] == 2 ? TRK_STEP_DIRECT : TRK_STEP_BLOCK;
         return TRK_OK;
     }
-    if (direct) CUDA_TRY(launch_direct(t, mode, a));
-    else CUDA_TRY(launch_block(t, mode, a));
+    if (direct) {
+        CUDA_TRY(launch_direct(t, mode, a));
+    } else {
+        const bool saved = t->auto_tma;
+        if (interp_choice >= 0) t->auto_tma = interp_choice == 1;
+        const cudaError_t e = launch_block(t, mode, a);
+        t->auto_tma = saved;
+        CUDA_TRY(e);
+    }
     t->last_kernel = direct ? TRK_STEP_DIRECT : TRK_STEP_BLOCK;
     return TRK_OK;
 }

@@ -39,22 +39,20 @@ def _run(N, storage, field, pos, steps, tuning=None, scheme=trk.TRK_RK2, dt=5e-3
 
 CASES = {
     # (N, particles per cell, storage): candidates the tuner times
-    "column_and_direct": (128, 1 / 16, trk.TRK_F32),    # column 4/8/16 and direct 8/16/32
-    "dense_column_only": (64, 1 / 2, trk.TRK_F32),      # column 4/8 (N/8 = 8 slabs)
-    "sparse_direct_only": (256, 1 / 200, trk.TRK_F32),  # direct 8/16/32
-    "no_column_float64": (128, 1 / 16, trk.TRK_F64),    # block (tensor-copy halo) and direct 8/16/32
+    "column_and_direct": (128, 1 / 16, trk.TRK_F32),    # column 8/16, direct 8/16
+    "dense_all_kernels": (64, 1 / 2, trk.TRK_F32),      # column 8 (N/8 = 8 slabs), block tma/async, direct 8/16
+    "sparse_direct_only": (256, 1 / 200, trk.TRK_F32),  # direct 8/16
+    "no_column_float64": (128, 1 / 16, trk.TRK_F64),    # block tma/async, direct 8/16
 }
 
 
 def _candidates(N, dens, storage):
+    """The tuner's candidates and a few more launch shapes, all fixed in turn."""
     c = []
-    if dens >= 0.01:
-        if storage == trk.TRK_F32:
-            c += [dict(step_kernel=trk.TRK_STEP_COLUMN, column_segment=s) for s in (4, 8, 16) if s <= N // 8]
-        else:
-            c += [dict(step_kernel=trk.TRK_STEP_BLOCK, halo_copy=h) for h in (trk.TRK_HALO_TMA, trk.TRK_HALO_ASYNC)]
-    if dens <= 0.25:
-        c += [dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=b) for b in (4, 8, 16, 32)]
+    if dens >= 0.01 and storage == trk.TRK_F32:
+        c += [dict(step_kernel=trk.TRK_STEP_COLUMN, column_segment=s) for s in (4, 8, 16) if s <= N // 8]
+    c += [dict(step_kernel=trk.TRK_STEP_BLOCK, halo_copy=h) for h in (trk.TRK_HALO_TMA, trk.TRK_HALO_ASYNC)]
+    c += [dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=b) for b in (4, 8, 16, 32)]
     return c
 
 
