@@ -883,7 +883,7 @@ template <typename T, int SC, int STAGE>
 struct SmemPlan {
     static constexpr size_t rec = align32((size_t)3 * SC * sizeof(T));
     static constexpr size_t k = align32(rec + PB * sizeof(PRec<T>));
-    static constexpr size_t w = align32(k + (size_t)6 * PB * sizeof(T));
+    static constexpr size_t w = align32(k + (STAGE >= 1 ? (size_t)6 * PB * sizeof(T) : 0));   // k values: steps only
     static constexpr size_t cell = align32(w + (size_t)NW * 48 * sizeof(T));
     static constexpr size_t id = align32(cell + PB * sizeof(int));
     static constexpr size_t x = align32(id + PB * sizeof(int));
@@ -1206,8 +1206,20 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
 #endif
 
 // tmap: the tensor map of the padded field (read only with HC == HC_TMA)
+// resident CTAs per SM the block kernel is register-capped for: float32 I = 4, 6
+// TRK_F32_MIN_BLOCKS; I = 8 two, three for value interpolation of a float32
+// field (its shared-memory plan has no k values and fits three CTAs; 79-80
+// registers without spills)
+template <typename T, int I, int MODE, int STORE>
+constexpr int block_min_ctas()
+{
+    if constexpr (sizeof(T) != 4) return 1;
+    else if constexpr (I != 8) return TRK_F32_MIN_BLOCKS;
+    else return MODE == MODE_INTERP && STORE == ST_F32 ? 3 : 2;
+}
+
 template <typename T, int I, int DEG, int MODE, int STORE, int HC>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN_BLOCKS) : 1)
+__global__ void __launch_bounds__(NT, block_min_ctas<T, I, MODE, STORE>())
     k_block(const __grid_constant__ BlockArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];

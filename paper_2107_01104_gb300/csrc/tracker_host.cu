@@ -132,6 +132,9 @@ struct tracker {
     // sort scratch
     int64_t sort_cap = 0;             // keys, perm
     int64_t radix_cap = 0;            // sort_scratch, keys_sorted (stable binning)
+    int64_t interp_cap = 0;           // ipos, iid
+    double* ipos = nullptr;           // [3][np] positions grouped by block (interpolation)
+    int32_t* iid = nullptr;           // [np] their caller indices
     void* sort_scratch = nullptr;
     uint32_t* keys = nullptr;
     uint32_t* keys_sorted = nullptr;
@@ -447,7 +450,41 @@ int bin_into(tracker* t, int64_t np, const double* pos, uint32_t* keys, int32_t*
     return TRK_OK;
 }
 
-// Counting-sort binning of interpolation and the adjoint: keys and block
+// Grouped copies of the positions and caller ids of np particles (interpolation).
+int ensure_interp_state(tracker* t, int64_t np)
+{
+    if (np <= t->interp_cap) return TRK_OK;
+    dev_free(t->ipos);
+    dev_free(t->iid);
+    t->ipos = nullptr;
+    t->iid = nullptr;
+    t->interp_cap = 0;
+    if (dev_alloc(&t->ipos, (size_t)np * 24) != cudaSuccess || dev_alloc(&t->iid, (size_t)np * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TRK_ENOMEM, "cannot allocate the grouped positions of %lld particles", (long long)np);
+    }
+    t->interp_cap = np;
+    return TRK_OK;
+}
+
+// Counting-sort binning of interpolation: keys and block counts from the
+// positions, offsets and cursors from one scan, then the positions and
+// caller ids scattered into block order (t->ipos, t->iid), so that the
+// kernels read them contiguously instead of through a permutation.
+int bin_counting_state(tracker* t, int64_t np, const double* pos)
+{
+    ProfScope ps(t, PROF_BIN);
+    CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
+    CUDA_TRY(launch_keys_count(t->g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
+    CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->d_scan_tmp, t->stream,
+                               &t->launches));
+    CUDA_TRY(launch_scatter_state(np, t->keys, t->d_cursor, pos, nullptr, nullptr, 0, t->ipos, t->iid, nullptr,
+                                  t->d_flags, t->stream));
+    t->launches += 2;
+    return TRK_OK;
+}
+
+// Counting-sort binning of the adjoint: keys and block
 // counts from the positions, offsets and cursors from one scan, then the
 // permutation t->perm (grouped by block; the order inside a block is not
 // reproducible, and every particle's result is independent of it).
@@ -989,6 +1026,8 @@ int tracker_destroy(tracker* t)
     if (t->stream) cudaStreamSynchronize(t->stream);
     else cudaDeviceSynchronize();
     dev_free(t->field);
+    dev_free(t->ipos);
+    dev_free(t->iid);
     dev_free(t->sort_scratch);
     dev_free(t->keys);
     dev_free(t->keys_sorted);
@@ -1278,11 +1317,13 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     if (np == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
     if ((direct || probe) && (rc = ensure_node_major(t))) return rc;
-    if ((rc = bin_counting(t, np, pos))) return rc;
+    if ((rc = ensure_interp_state(t, np))) return rc;
+    if ((rc = bin_counting_state(t, np, pos))) return rc;
     BlockArgs a = base_args(t);
     a.np = np;
-    a.perm = t->perm;
-    a.pos_in = pos;
+    a.perm = nullptr;          // positions and caller ids grouped by block: read at j
+    a.pos_in = t->ipos;
+    a.id_in = t->iid;
     a.out = out;
     a.out_f64 = out_dtype == TRK_DTYPE_F64;
     const int mode = deriv ? MODE_INTERP_DERIV : MODE_INTERP;
