@@ -272,6 +272,19 @@ __global__ void k_scatter_perm(int64_t np, const uint32_t* __restrict__ keys, in
     perm[d] = (int32_t)j;
 }
 
+// Positions in permutation order: dst[a][j] = src[a][perm[j]] (the writes are
+// contiguous; a scatter of the positions by destination would write 8-byte
+// pieces of random sectors instead).
+__global__ void k_gather_pos(int64_t np, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                             double* __restrict__ dst)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const int64_t p = perm[j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dst[a * np + j] = src[a * np + p];
+}
+
 // Block counts of np keys, one atomic add per group of equal keys in a warp
 // (keys written by a step kernel arrive grouped by the previous binning).
 __global__ void k_count_keys(int64_t np, const uint32_t* __restrict__ keys, uint32_t* __restrict__ counts)
@@ -637,6 +650,13 @@ cudaError_t launch_scatter_perm(int64_t np, const uint32_t* keys, int32_t* curso
 {
     if (np <= 0) return cudaSuccess;
     k_scatter_perm<<<grid_for(np, 256), 256, 0, st>>>(np, keys, cursor, perm, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pos(int64_t np, const int32_t* perm, const double* src, double* dst, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_gather_pos<<<grid_for(np, 256), 256, 0, st>>>(np, perm, src, dst);
     return cudaGetLastError();
 }
 

@@ -374,6 +374,8 @@ cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offset
 // counting-sort permutation of keys (cursor from launch_count_scan): perm[d] = j
 cudaError_t launch_scatter_perm(int64_t np, const uint32_t* keys, int32_t* cursor, int32_t* perm, int* flags,
                                 cudaStream_t st);
+// dst[a][j] = src[a][perm[j]] for the three rows of [3][np] positions
+cudaError_t launch_gather_pos(int64_t np, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
 // counts[key] += number of particles with that key
 cudaError_t launch_count_keys(int64_t np, const uint32_t* keys, uint32_t* counts, cudaStream_t st);
 cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,

@@ -132,9 +132,8 @@ struct tracker {
     // sort scratch
     int64_t sort_cap = 0;             // keys, perm
     int64_t radix_cap = 0;            // sort_scratch, keys_sorted (stable binning)
-    int64_t interp_cap = 0;           // ipos, iid
-    double* ipos = nullptr;           // [3][np] positions grouped by block (interpolation)
-    int32_t* iid = nullptr;           // [np] their caller indices
+    int64_t interp_cap = 0;           // ipos
+    double* ipos = nullptr;           // [3][np] positions grouped by block (interpolation; caller index in perm)
     void* sort_scratch = nullptr;
     uint32_t* keys = nullptr;
     uint32_t* keys_sorted = nullptr;
@@ -450,37 +449,18 @@ int bin_into(tracker* t, int64_t np, const double* pos, uint32_t* keys, int32_t*
     return TRK_OK;
 }
 
-// Grouped copies of the positions and caller ids of np particles (interpolation).
+// The positions of np particles in block order (interpolation).
 int ensure_interp_state(tracker* t, int64_t np)
 {
     if (np <= t->interp_cap) return TRK_OK;
     dev_free(t->ipos);
-    dev_free(t->iid);
     t->ipos = nullptr;
-    t->iid = nullptr;
     t->interp_cap = 0;
-    if (dev_alloc(&t->ipos, (size_t)np * 24) != cudaSuccess || dev_alloc(&t->iid, (size_t)np * 4) != cudaSuccess) {
+    if (dev_alloc(&t->ipos, (size_t)np * 24) != cudaSuccess) {
         cudaGetLastError();
         return fail(TRK_ENOMEM, "cannot allocate the grouped positions of %lld particles", (long long)np);
     }
     t->interp_cap = np;
-    return TRK_OK;
-}
-
-// Counting-sort binning of interpolation: keys and block counts from the
-// positions, offsets and cursors from one scan, then the positions and
-// caller ids scattered into block order (t->ipos, t->iid), so that the
-// kernels read them contiguously instead of through a permutation.
-int bin_counting_state(tracker* t, int64_t np, const double* pos)
-{
-    ProfScope ps(t, PROF_BIN);
-    CUDA_TRY(cudaMemsetAsync(t->d_counts, 0, (size_t)t->nblocks * sizeof(uint32_t), t->stream));
-    CUDA_TRY(launch_keys_count(t->g, np, pos, t->keys, t->d_counts, t->d_flags, t->stream));
-    CUDA_TRY(launch_count_scan(t->d_counts, t->nblocks, t->offsets, t->d_cursor, t->d_scan_tmp, t->stream,
-                               &t->launches));
-    CUDA_TRY(launch_scatter_state(np, t->keys, t->d_cursor, pos, nullptr, nullptr, 0, t->ipos, t->iid, nullptr,
-                                  t->d_flags, t->stream));
-    t->launches += 2;
     return TRK_OK;
 }
 
@@ -497,6 +477,20 @@ int bin_counting(tracker* t, int64_t np, const double* pos)
                                &t->launches));
     CUDA_TRY(launch_scatter_perm(np, t->keys, t->d_cursor, t->perm, t->d_flags, t->stream));
     t->launches += 2;
+    return TRK_OK;
+}
+
+// Counting-sort binning of interpolation: the permutation of bin_counting,
+// then the positions gathered into block order (t->ipos; t->perm holds the
+// caller index of each), so that the kernels read them contiguously instead
+// of through the permutation.
+int bin_counting_state(tracker* t, int64_t np, const double* pos)
+{
+    int rc = bin_counting(t, np, pos);
+    if (rc) return rc;
+    ProfScope ps(t, PROF_BIN);
+    CUDA_TRY(launch_gather_pos(np, t->perm, pos, t->ipos, t->stream));
+    t->launches += 1;
     return TRK_OK;
 }
 
@@ -1027,7 +1021,6 @@ int tracker_destroy(tracker* t)
     else cudaDeviceSynchronize();
     dev_free(t->field);
     dev_free(t->ipos);
-    dev_free(t->iid);
     dev_free(t->sort_scratch);
     dev_free(t->keys);
     dev_free(t->keys_sorted);
@@ -1321,9 +1314,9 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     if ((rc = bin_counting_state(t, np, pos))) return rc;
     BlockArgs a = base_args(t);
     a.np = np;
-    a.perm = nullptr;          // positions and caller ids grouped by block: read at j
+    a.perm = nullptr;          // positions grouped by block: read at j, caller index perm[j]
     a.pos_in = t->ipos;
-    a.id_in = t->iid;
+    a.id_in = t->perm;
     a.out = out;
     a.out_f64 = out_dtype == TRK_DTYPE_F64;
     const int mode = deriv ? MODE_INTERP_DERIV : MODE_INTERP;
