@@ -177,6 +177,42 @@ def test_ab2_parity_and_history(storage):
     assert np.abs(rhs.cpu().numpy() - ref_rhs).max() <= 2e-6 * 3
 
 
+@pytest.mark.parametrize("N,layout", [(64, "uniform"), (256, "uniform"), (64, "cluster"), (32, "slices")])
+def test_interpolate_large_sets_two_level_binning(N, layout):
+    """Interpolation of more than 2^20 particles bins with the two-level
+    counting sort (shared-memory histograms over coarse buckets, then one CTA
+    per bucket): every output of both kernels (block: positions written in
+    block order by the sort; direct: read through its permutation) against
+    the oracle on a sample, the two kernels bit-identical on all particles.
+    Ragged count; a cluster where one coarse bucket holds every particle; x3
+    slices (the block shape N x N x 1)."""
+    n = (1 << 20) + 12345
+    rng = np.random.default_rng(N)
+    field = synth.velocity_field_np(N, min(10, N // 3), 85)
+    if layout == "cluster":
+        pos = rng.uniform(0.01, 8 * L / N - 0.01, (3, n))
+    else:
+        pos = rng.uniform(-L, 2 * L, (3, n))
+    p = torch.from_numpy(pos).to(DEV)
+    outs = []
+    for kind in (trk.TRK_STEP_BLOCK, trk.TRK_STEP_DIRECT):
+        t = make_tracker(N, trk.TRK_SPLINE, 6, 2, trk.TRK_F32, field)
+        if layout == "slices":
+            trk.tracker_set_block(t.h, N, N, 1)
+        t.set_step_kernel(kind)
+        if layout == "slices" and kind == trk.TRK_STEP_BLOCK:
+            t.close()
+            continue
+        outs.append(t.interpolate(p, out_dtype=torch.float64).cpu())
+        t.sync()
+        t.close()
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    ix = rng.choice(n, 3000, replace=False)
+    ref = oracle.interp(stored(field, trk.TRK_F32), pos[:, ix], trk.TRK_SPLINE, 6, 2)
+    assert np.abs(outs[0].numpy()[:, ix] - ref).max() <= 2e-6 * np.sqrt(np.mean(field ** 2))
+
+
 def test_cfl_violation_takes_exact_slow_path():
     N, n = 32, 500
     field = synth.velocity_field_np(N, 10, 81) * 30.0     # |dt u| >> delta
