@@ -957,7 +957,10 @@ def tuner_table(trk, dev, stream, dev_index, args, fma):
              ("block (cp.async halo)", dict(step_kernel=trk.TRK_STEP_BLOCK, halo_copy=trk.TRK_HALO_ASYNC)),
              ("direct edge 8", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=8)),
              ("direct edge 16", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=16)),
-             ("direct edge 32", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=32))]
+             ("direct edge 32", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=32)),
+             ("direct edge 8, 128 per CTA", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=8, direct_particles=128)),
+             ("direct edge 16, 128 per CTA", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=16,
+                                                   direct_particles=128))]
     names = {trk.TRK_STEP_COLUMN: "column", trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_DIRECT: "direct"}
     for scheme, sname in ((trk.TRK_RK2, "RK2"), (trk.TRK_AB2, "AB2")):
         for dens in (1.5e-3, 1 / 64, 1 / 32, 1 / 16, 1 / 8, 1 / 4, 1 / 2):
@@ -976,6 +979,7 @@ def tuner_table(trk, dev, stream, dev_index, args, fma):
                     info = t.tuning()
                     row["tuner_pick"] = {"kernel": names.get(info["step_kernel"], "?"),
                                          "direct_block": info["direct_block"],
+                                         "direct_particles": info["direct_particles"],
                                          "column_segment": info["column_segment"], "source": info["source"]}
                 ms, _, _ = timed(lambda: t.advance(p, DT, 20, scheme, rhs=rhs, history_valid=scheme != trk.TRK_RK2),
                                  stream, dev_index, min_s=0.2, max_reps=10)

@@ -270,13 +270,16 @@ int tracker_set_halo_copy(tracker* t, int kind);
  * shape; it sets how compact each thread block's 256 particles are);
  * column_segment: x3 slabs per work item of the column kernel (a power of
  * two <= 64, at most N/8); halo_copy: the block kernel's TRK_HALO_ASYNC or
- * TRK_HALO_TMA.  source (tracker_get_tuning only): how they were chosen. */
+ * TRK_HALO_TMA; direct_particles: particles per thread block of the direct
+ * kernel (128 or 256; 0 in tracker_set_tuning means 256).  source
+ * (tracker_get_tuning only): how they were chosen. */
 typedef enum { TRK_TUNE_DEFAULT = 0, TRK_TUNE_TIMED = 1, TRK_TUNE_CACHED = 2, TRK_TUNE_FIXED = 3 } trk_tune_source;
 typedef struct {
     int step_kernel;
     int direct_block;
     int column_segment;
     int halo_copy;
+    int direct_particles;
     int source;
 } trk_tuning;
 
@@ -290,8 +293,8 @@ typedef struct {
  * (TRK_TUNE_TIMED, then TRK_TUNE_CACHED).  Candidates: from 0.01 particles
  * per cell on, the column kernel with segments 8 and 16; the block kernel
  * with tensor-copy and with cp.async halos from 0.1 per cell on (from 0.01
- * without a column kernel); the direct kernel with block edges 8 and 16 up
- * to one particle per cell.  Other calls use the density rule of
+ * without a column kernel); the direct kernel with block edges 8 and 16 and
+ * 256 or 128 particles per thread block, up to one particle per cell.  Other calls use the density rule of
  * tracker_set_step_kernel with the default shape (TRK_TUNE_DEFAULT).  Every
  * candidate gives bit-identical steps.  When the environment variable
  * TRK_TUNE_CACHE names a file, decisions are appended to it (one line per

@@ -68,7 +68,7 @@ class trk_state_info(ctypes.Structure):
 
 class trk_tuning(ctypes.Structure):
     _fields_ = [("step_kernel", ctypes.c_int), ("direct_block", ctypes.c_int), ("column_segment", ctypes.c_int),
-                ("halo_copy", ctypes.c_int), ("source", ctypes.c_int)]
+                ("halo_copy", ctypes.c_int), ("direct_particles", ctypes.c_int), ("source", ctypes.c_int)]
 
 
 class trk_set(ctypes.Structure):
@@ -454,13 +454,15 @@ class Tracker:
         _check(min(r, 0))
         return r
 
-    def set_tuning(self, step_kernel=None, direct_block=8, column_segment=8, halo_copy=TRK_HALO_TMA):
+    def set_tuning(self, step_kernel=None, direct_block=8, column_segment=8, halo_copy=TRK_HALO_TMA,
+                   direct_particles=256):
         """Fix the time-step launch shape (see tracker_set_tuning); no arguments: automatic tuning."""
         if step_kernel is None:
             _check(load_library().tracker_set_tuning(self.h, None))
             return
         p = trk_tuning(step_kernel=int(step_kernel), direct_block=int(direct_block),
-                       column_segment=int(column_segment), halo_copy=int(halo_copy), source=0)
+                       column_segment=int(column_segment), halo_copy=int(halo_copy),
+                       direct_particles=int(direct_particles), source=0)
         _check(load_library().tracker_set_tuning(self.h, ctypes.byref(p)))
 
     def tuning(self):

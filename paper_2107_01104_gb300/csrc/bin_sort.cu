@@ -272,19 +272,6 @@ __global__ void k_scatter_perm(int64_t np, const uint32_t* __restrict__ keys, in
     perm[d] = (int32_t)j;
 }
 
-// Positions in permutation order: dst[a][j] = src[a][perm[j]] (the writes are
-// contiguous; a scatter of the positions by destination would write 8-byte
-// pieces of random sectors instead).
-__global__ void k_gather_pos(int64_t np, const int32_t* __restrict__ perm, const double* __restrict__ src,
-                             double* __restrict__ dst)
-{
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= np) return;
-    const int64_t p = perm[j];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dst[a * np + j] = src[a * np + p];
-}
-
 // Block counts of np keys, one atomic add per group of equal keys in a warp
 // (keys written by a step kernel arrive grouped by the previous binning).
 __global__ void k_count_keys(int64_t np, const uint32_t* __restrict__ keys, uint32_t* __restrict__ counts)
@@ -535,183 +522,6 @@ __global__ void k_node_major_bf16(const __nv_bfloat16* __restrict__ hi, const __
 
 unsigned grid_for(int64_t n, int threads) { return (unsigned)ceil_div(n > 0 ? n : 1, threads); }
 
-// ---------------------------------------------------------------------------
-// Two-level counting sort for large particle sets in random order (the
-// interpolation binning): keys split into a coarse bucket (key >> shift, at
-// most MSD_MAX_COARSE buckets) and a fine block inside it (at most
-// MSD_MAX_FINE).  Every histogram lives in shared memory, so no particle
-// takes a global atomic:
-//   1. k_msd_keys:    block keys (caller order) and the coarse histogram;
-//   2. (scan of the coarse counts: bucket starts and cursors);
-//   3. k_msd_scatter: tiles of MSD_TILE particles ranked per bucket in shared
-//                     memory, one global reservation per (tile, bucket), each
-//                     particle's record written into its bucket's range;
-//   4. k_msd_fine:    one CTA per bucket: fine histogram, scan, the offsets of
-//                     its blocks, then perm (and the positions) written in
-//                     block order inside the bucket's range.
-// The order inside a block follows the shared-memory atomics (not
-// reproducible); the blocks and offsets are those of the stable sort.
-// ---------------------------------------------------------------------------
-constexpr int MSD_THREADS = 512;
-constexpr int MSD_TILE = 4096;
-
-struct alignas(32) MsdRec {      // a particle on its way to its block: 32 bytes, one sector
-    uint32_t key;
-    int32_t idx;
-    double x[3];
-};
-
-__global__ void __launch_bounds__(MSD_THREADS) k_msd_keys(GridGeom g, int64_t np, const double* __restrict__ pos,
-                                                          uint32_t* __restrict__ keys, int shift, int ncoarse,
-                                                          uint32_t* __restrict__ coarse_counts, int* flags)
-{
-    extern __shared__ uint32_t hist[];   // [ncoarse]
-    for (int b = threadIdx.x; b < ncoarse; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    bool bad = false;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-        int c[3];
-        bool ok = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ok &= split_cell(pos[a * np + p], g.inv_delta, g.mask, c[a]);
-        bad |= !ok;
-        const uint32_t key = block_key(g, c[0], c[1], c[2]);
-        keys[p] = key;
-        atomicAdd(&hist[key >> shift], 1u);
-    }
-    if (bad) atomicOr(flags + FLAG_NONFINITE, 1);
-    __syncthreads();
-    for (int b = threadIdx.x; b < ncoarse; b += blockDim.x)
-        if (hist[b]) atomicAdd(coarse_counts + b, hist[b]);
-}
-
-template <bool POS>
-__global__ void __launch_bounds__(MSD_THREADS) k_msd_scatter(int64_t np, const uint32_t* __restrict__ keys,
-                                                             const double* __restrict__ pos, int shift, int ncoarse,
-                                                             int32_t* __restrict__ cursor, MsdRec* __restrict__ rec,
-                                                             uint2* __restrict__ rec_small, int* flags)
-{
-    extern __shared__ uint32_t sm[];   // [ncoarse] counts, then [ncoarse] tile bases
-    uint32_t* cnt = sm;
-    int32_t* base = reinterpret_cast<int32_t*>(sm + ncoarse);
-    constexpr int PER = MSD_TILE / MSD_THREADS;
-    const int64_t ntiles = (np + MSD_TILE - 1) / MSD_TILE;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        for (int b = threadIdx.x; b < ncoarse; b += blockDim.x) cnt[b] = 0;
-        __syncthreads();
-        const int64_t t0 = tile * MSD_TILE;
-        uint32_t k[PER];
-        uint32_t rank[PER];
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int64_t p = t0 + (int64_t)u * MSD_THREADS + threadIdx.x;
-            k[u] = p < np ? keys[p] : 0u;
-            rank[u] = p < np ? atomicAdd(&cnt[k[u] >> shift], 1u) : 0u;
-        }
-        __syncthreads();
-        for (int b = threadIdx.x; b < ncoarse; b += blockDim.x)
-            base[b] = cnt[b] ? atomicAdd(cursor + b, (int32_t)cnt[b]) : 0;
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int64_t p = t0 + (int64_t)u * MSD_THREADS + threadIdx.x;
-            if (p >= np) continue;
-            const int64_t d = (int64_t)base[k[u] >> shift] + rank[u];
-            if (d < 0 || d >= np) {
-                atomicOr(flags + FLAG_BINNING, 1);
-                continue;
-            }
-            if constexpr (POS) {
-                MsdRec r;
-                r.key = k[u];
-                r.idx = (int32_t)p;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) r.x[a] = pos[a * np + p];
-                rec[d] = r;
-            } else {
-                rec_small[d] = make_uint2(k[u], (uint32_t)p);
-            }
-        }
-        __syncthreads();
-    }
-}
-
-template <bool POS>
-__global__ void __launch_bounds__(MSD_THREADS) k_msd_fine(int64_t np, int64_t nblocks, int shift,
-                                                          const int32_t* __restrict__ start,
-                                                          const MsdRec* __restrict__ rec,
-                                                          const uint2* __restrict__ rec_small,
-                                                          int32_t* __restrict__ offsets, int32_t* __restrict__ perm,
-                                                          double* __restrict__ ipos, int* flags)
-{
-    extern __shared__ uint32_t sm[];   // [nfine] counts, then [nfine] cursors
-    const int nfine = 1 << shift;
-    uint32_t* cnt = sm;
-    uint32_t* cur = sm + nfine;
-    __shared__ uint32_t wsum[MSD_THREADS / 32];
-    const int b = blockIdx.x;
-    const int64_t s0 = start[b], s1 = start[b + 1];
-    for (int f = threadIdx.x; f < nfine; f += blockDim.x) cnt[f] = 0;
-    __syncthreads();
-    const uint32_t fmask = (uint32_t)nfine - 1u;
-    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-        const uint32_t key = POS ? rec[i].key : rec_small[i].x;
-        atomicAdd(&cnt[key & fmask], 1u);
-    }
-    __syncthreads();
-    // exclusive scan of the nfine counts: each thread a contiguous run, then the warps
-    const int per = (nfine + MSD_THREADS - 1) / MSD_THREADS;
-    const int f0 = threadIdx.x * per;
-    uint32_t run = 0;
-    for (int f = f0; f < f0 + per && f < nfine; ++f) run += cnt[f];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t inc = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) wsum[w] = inc;
-    __syncthreads();
-    uint32_t wp = 0;
-    for (int i = 0; i < w; ++i) wp += wsum[i];
-    uint32_t e = wp + inc - run;
-    for (int f = f0; f < f0 + per && f < nfine; ++f) {
-        const uint32_t c = cnt[f];
-        cur[f] = e;
-        const int64_t blk = ((int64_t)b << shift) + f;
-        if (blk < nblocks) offsets[blk] = (int32_t)(s0 + e);
-        e += c;
-    }
-    if (b == gridDim.x - 1 && threadIdx.x == 0) offsets[nblocks] = (int32_t)np;
-    __syncthreads();
-    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-        uint32_t key;
-        int32_t idx;
-        double x[3] = {0, 0, 0};
-        if constexpr (POS) {
-            const MsdRec r = rec[i];
-            key = r.key;
-            idx = r.idx;
-            x[0] = r.x[0], x[1] = r.x[1], x[2] = r.x[2];
-        } else {
-            const uint2 r = rec_small[i];
-            key = r.x;
-            idx = (int32_t)r.y;
-        }
-        const int64_t d = s0 + atomicAdd(&cur[key & fmask], 1u);
-        if (d < s0 || d >= s1) {
-            atomicOr(flags + FLAG_BINNING, 1);
-            continue;
-        }
-        perm[d] = idx;
-        if constexpr (POS) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) ipos[a * np + d] = x[a];
-        }
-    }
-}
-
 }  // namespace
 
 size_t scan_scratch_bytes_u32(int64_t len) { return scan_scratch_bytes(len); }
@@ -827,68 +637,6 @@ cudaError_t launch_scatter_perm(int64_t np, const uint32_t* keys, int32_t* curso
 {
     if (np <= 0) return cudaSuccess;
     k_scatter_perm<<<grid_for(np, 256), 256, 0, st>>>(np, keys, cursor, perm, flags);
-    return cudaGetLastError();
-}
-
-size_t msd_scratch_bytes(int64_t np, bool with_pos)
-{
-    return align256((size_t)(np > 0 ? np : 1) * (with_pos ? sizeof(MsdRec) : sizeof(uint2)));
-}
-
-bool msd_shape(int64_t nblocks, int* shift, int* ncoarse)
-{
-    int bits = 0;
-    while ((int64_t(1) << bits) < nblocks) ++bits;
-    const int s = bits > 12 ? bits - 12 : 0;             // at most 4096 coarse buckets
-    if ((1 << s) > MSD_MAX_FINE) return false;
-    *shift = s;
-    *ncoarse = (int)((nblocks + (int64_t(1) << s) - 1) >> s);
-    return true;
-}
-
-cudaError_t launch_msd_bin(const GridGeom& g, int64_t np, const double* pos, int64_t nblocks, uint32_t* keys,
-                           uint32_t* coarse_counts, int32_t* coarse_start, int32_t* coarse_cursor, uint32_t* scan_tmp,
-                           void* scratch, int32_t* perm, int32_t* offsets, double* ipos, int* flags, int nsm,
-                           cudaStream_t st, int64_t* launches)
-{
-    int shift = 0, nc = 0;
-    if (np <= 0 || !msd_shape(nblocks, &shift, &nc)) return cudaErrorInvalidValue;
-    const bool with_pos = ipos != nullptr;
-    cudaError_t e = cudaMemsetAsync(coarse_counts, 0, (size_t)nc * sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 2, ceil_div(np, MSD_THREADS)));
-    k_msd_keys<<<grid, MSD_THREADS, (size_t)nc * sizeof(uint32_t), st>>>(g, np, pos, keys, shift, nc, coarse_counts,
-                                                                        flags);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // bucket starts and cursors (the counts are left zero)
-    if ((e = launch_count_scan(coarse_counts, nc, coarse_start, coarse_cursor, scan_tmp, st, launches)) != cudaSuccess)
-        return e;
-    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 2, ceil_div(np, MSD_TILE)));
-    const size_t sm_scatter = (size_t)2 * nc * sizeof(uint32_t);
-    MsdRec* rec = reinterpret_cast<MsdRec*>(scratch);
-    uint2* rec_small = reinterpret_cast<uint2*>(scratch);
-    if (with_pos)
-        k_msd_scatter<true><<<gs, MSD_THREADS, sm_scatter, st>>>(np, keys, pos, shift, nc, coarse_cursor, rec, nullptr,
-                                                                flags);
-    else
-        k_msd_scatter<false><<<gs, MSD_THREADS, sm_scatter, st>>>(np, keys, pos, shift, nc, coarse_cursor, nullptr,
-                                                                 rec_small, flags);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t sm_fine = (size_t)2 * (1 << shift) * sizeof(uint32_t);
-    if (with_pos)
-        k_msd_fine<true><<<nc, MSD_THREADS, sm_fine, st>>>(np, nblocks, shift, coarse_start, rec, nullptr, offsets,
-                                                          perm, ipos, flags);
-    else
-        k_msd_fine<false><<<nc, MSD_THREADS, sm_fine, st>>>(np, nblocks, shift, coarse_start, nullptr, rec_small,
-                                                           offsets, perm, nullptr, flags);
-    if (launches) *launches += 3;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gather_pos(int64_t np, const int32_t* perm, const double* src, double* dst, cudaStream_t st)
-{
-    if (np <= 0) return cudaSuccess;
-    k_gather_pos<<<grid_for(np, 256), 256, 0, st>>>(np, perm, src, dst);
     return cudaGetLastError();
 }
 

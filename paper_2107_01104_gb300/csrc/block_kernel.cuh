@@ -1227,7 +1227,11 @@ __global__ void __launch_bounds__(NT, block_min_ctas<T, I, MODE, STORE>())
     process_block<T, I, DEG, MODE, STORE, true, NM_NONE, HC>(a, b, a.offsets[b], a.offsets[b + 1], smem_raw, &tmap);
 }
 
-// Direct path: CTA c takes the sorted particles [c PB, (c + 1) PB) and
+// particles per CTA of the direct kernel: a.ppc in [1, PB], 0 for PB (a launch
+// shape the tuner chooses; every value gives the same results)
+__host__ __device__ __forceinline__ int direct_ppc(const BlockArgs& a) { return a.ppc > 0 && a.ppc < PB ? a.ppc : PB; }
+
+// Direct path: CTA c takes the sorted particles [c ppc, (c + 1) ppc) and
 // gathers their stencils from global memory (no halo, no cell-block grid);
 // float32 fields are read from the node-major copy a.f.nm.
 template <typename T, int I, int DEG, int MODE, int STORE, int NM>
@@ -1235,8 +1239,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (I == 8 ? 2 : TRK_F32_MIN
     k_direct(const __grid_constant__ BlockArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int64_t j0 = (int64_t)blockIdx.x * PB;
-    const int64_t j1 = j0 + PB < a.np ? j0 + PB : a.np;
+    const int ppc = direct_ppc(a);
+    const int64_t j0 = (int64_t)blockIdx.x * ppc;
+    const int64_t j1 = j0 + ppc < a.np ? j0 + ppc : a.np;
     process_block<T, I, DEG, MODE, STORE, false, NM>(a, 0, (int)j0, (int)j1, smem_raw);
 }
 
@@ -1258,7 +1263,8 @@ cudaError_t launch_direct_nm(const BlockArgs& a, cudaStream_t st)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    kern<<<(unsigned)((a.np + PB - 1) / PB), NT, smem, st>>>(a);
+    const int ppc = direct_ppc(a);
+    kern<<<(unsigned)((a.np + ppc - 1) / ppc), NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 

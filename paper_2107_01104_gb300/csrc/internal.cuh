@@ -181,6 +181,7 @@ struct BlockArgs {
     int out_f64;
     int history_valid;        // AB: valid history entries on entry, 0 .. ab_order-1
     int ab_order;             // AB order k (2, 3, 4); the history holds k-1 entries
+    int ppc;                  // direct kernel: particles per CTA (1 .. 256; 0 means 256)
     double dt;
     int* flags;
 };
@@ -374,20 +375,6 @@ cudaError_t launch_count_scan(uint32_t* counts, int64_t nblocks, int32_t* offset
 // counting-sort permutation of keys (cursor from launch_count_scan): perm[d] = j
 cudaError_t launch_scatter_perm(int64_t np, const uint32_t* keys, int32_t* cursor, int32_t* perm, int* flags,
                                 cudaStream_t st);
-// Two-level counting sort of np particles in random order (interpolation):
-// keys, perm (grouped by block), offsets[nblocks + 1], and, if ipos is not
-// null, the positions in block order.  msd_shape: false if the blocks are too
-// many for it (more than 4096 x MSD_MAX_FINE).  Scratch: msd_scratch_bytes;
-// coarse_counts (zeroed here), coarse_start, coarse_cursor: 4096 (+1) entries.
-constexpr int MSD_MAX_FINE = 2048;
-bool msd_shape(int64_t nblocks, int* shift, int* ncoarse);
-size_t msd_scratch_bytes(int64_t np, bool with_pos);
-cudaError_t launch_msd_bin(const GridGeom& g, int64_t np, const double* pos, int64_t nblocks, uint32_t* keys,
-                           uint32_t* coarse_counts, int32_t* coarse_start, int32_t* coarse_cursor, uint32_t* scan_tmp,
-                           void* scratch, int32_t* perm, int32_t* offsets, double* ipos, int* flags, int nsm,
-                           cudaStream_t st, int64_t* launches);
-// dst[a][j] = src[a][perm[j]] for the three rows of [3][np] positions
-cudaError_t launch_gather_pos(int64_t np, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
 // counts[key] += number of particles with that key
 cudaError_t launch_count_keys(int64_t np, const uint32_t* keys, uint32_t* counts, cudaStream_t st);
 cudaError_t launch_scatter_state(int64_t np, const uint32_t* keys, int32_t* cursor, const double* pos_in,

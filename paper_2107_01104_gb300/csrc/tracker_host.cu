@@ -132,13 +132,6 @@ struct tracker {
     // sort scratch
     int64_t sort_cap = 0;             // keys, perm
     int64_t radix_cap = 0;            // sort_scratch, keys_sorted (stable binning)
-    int64_t interp_cap = 0;           // ipos
-    size_t msd_bytes = 0;             // records of the two-level counting sort
-    void* msd_scratch = nullptr;
-    uint32_t* msd_counts = nullptr;   // [4096] coarse bucket counts
-    int32_t* msd_start = nullptr;     // [4097] coarse bucket starts
-    int32_t* msd_cursor = nullptr;    // [4096] coarse bucket cursors
-    double* ipos = nullptr;           // [3][np] positions grouped by block (interpolation; caller index in perm)
     void* sort_scratch = nullptr;
     uint32_t* keys = nullptr;
     uint32_t* keys_sorted = nullptr;
@@ -176,10 +169,11 @@ struct tracker {
     int* d_colctr = nullptr;          // work counter of the column kernel
     int col_seg = 8;                  // column kernel: x3 slabs per work item (power of two)
     int dir_blk = BLK;                // direct path: edge of its cubic binning blocks (default shape only)
+    int dir_ppc = 256;                // direct path: particles per CTA
     int64_t bin_cap = 0;              // entries of offsets / counts / cursor (largest geometry in use)
     int tune_source = TRK_TUNE_DEFAULT;   // how the latest call's parameters were chosen
-    std::array<int, 4> last_tuning = {TRK_STEP_AUTO, BLK, 8, 0};   // path, dir_blk, col_seg, tma of the latest call
-    std::vector<std::pair<std::string, std::array<int, 4>>> step_tune;   // tuner decisions by workload
+    std::array<int, 5> last_tuning = {TRK_STEP_AUTO, BLK, 8, 0, 256};   // path, dir_blk, col_seg, tma, ppc of the latest call
+    std::vector<std::pair<std::string, std::array<int, 5>>> step_tune;   // tuner decisions by workload
     // tensor maps of the padded field for the block kernel's tensor-copy halos,
     // one per stage-2 margin (interpolation and AB: 0, RK2: 1)
     CUtensorMap tmap[2];
@@ -454,22 +448,7 @@ int bin_into(tracker* t, int64_t np, const double* pos, uint32_t* keys, int32_t*
     return TRK_OK;
 }
 
-// The positions of np particles in block order (interpolation).
-int ensure_interp_state(tracker* t, int64_t np)
-{
-    if (np <= t->interp_cap) return TRK_OK;
-    dev_free(t->ipos);
-    t->ipos = nullptr;
-    t->interp_cap = 0;
-    if (dev_alloc(&t->ipos, (size_t)np * 24) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(TRK_ENOMEM, "cannot allocate the grouped positions of %lld particles", (long long)np);
-    }
-    t->interp_cap = np;
-    return TRK_OK;
-}
-
-// Counting-sort binning of the adjoint: keys and block
+// Counting-sort binning of interpolation and the adjoint: keys and block
 // counts from the positions, offsets and cursors from one scan, then the
 // permutation t->perm (grouped by block; the order inside a block is not
 // reproducible, and every particle's result is independent of it).
@@ -482,59 +461,6 @@ int bin_counting(tracker* t, int64_t np, const double* pos)
                                &t->launches));
     CUDA_TRY(launch_scatter_perm(np, t->keys, t->d_cursor, t->perm, t->d_flags, t->stream));
     t->launches += 2;
-    return TRK_OK;
-}
-
-// Large particle sets in random order (interpolation): the two-level counting
-// sort, whose histograms are all in shared memory (no global atomic per
-// particle); with_pos also writes the positions in block order (t->ipos).
-// Measured on GB300 at 2^27 tracers, 1024^3 in 8^3 blocks: see bin_interp.
-constexpr int64_t kMsdMinNp = int64_t(1) << 20;
-int bin_msd(tracker* t, int64_t np, const double* pos, bool with_pos)
-{
-    const size_t need = msd_scratch_bytes(np, with_pos);
-    if (need > t->msd_bytes) {
-        dev_free(t->msd_scratch);
-        t->msd_scratch = nullptr;
-        t->msd_bytes = 0;
-        if (dev_alloc(&t->msd_scratch, need) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(TRK_ENOMEM, "cannot allocate the binning records of %lld particles", (long long)np);
-        }
-        t->msd_bytes = need;
-    }
-    if (!t->msd_counts) {
-        if (dev_alloc(&t->msd_counts, 4096 * sizeof(uint32_t)) != cudaSuccess ||
-            dev_alloc(&t->msd_start, 4097 * sizeof(int32_t)) != cudaSuccess ||
-            dev_alloc(&t->msd_cursor, 4096 * sizeof(int32_t)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(TRK_ENOMEM, "cannot allocate the bucket counts");
-        }
-    }
-    ProfScope ps(t, PROF_BIN);
-    CUDA_TRY(launch_msd_bin(t->g, np, pos, t->nblocks, t->keys, t->msd_counts, t->msd_start, t->msd_cursor,
-                            t->d_scan_tmp, t->msd_scratch, t->perm, t->offsets, with_pos ? t->ipos : nullptr,
-                            t->d_flags, t->nsm, t->stream, &t->launches));
-    return TRK_OK;
-}
-
-bool msd_applies(const tracker* t, int64_t np)
-{
-    int shift = 0, nc = 0;
-    return np >= kMsdMinNp && msd_shape(t->nblocks, &shift, &nc);
-}
-
-// Counting-sort binning of interpolation: the permutation of bin_counting,
-// then the positions gathered into block order (t->ipos; t->perm holds the
-// caller index of each), so that the kernels read them contiguously instead
-// of through the permutation.
-int bin_counting_state(tracker* t, int64_t np, const double* pos)
-{
-    int rc = bin_counting(t, np, pos);
-    if (rc) return rc;
-    ProfScope ps(t, PROF_BIN);
-    CUDA_TRY(launch_gather_pos(np, t->perm, pos, t->ipos, t->stream));
-    t->launches += 1;
     return TRK_OK;
 }
 
@@ -581,6 +507,7 @@ BlockArgs base_args(tracker* t)
     a.offsets = t->offsets;
     a.flags = t->d_flags;
     a.ab_order = 2;
+    a.ppc = t->dir_ppc;
     return a;
 }
 
@@ -868,6 +795,7 @@ constexpr int kTuneStepsPerCand = 2;    // the first run of a kernel may load it
 
 struct Cand {
     int path, dir_blk, col_seg, tma;
+    int ppc = PB_HOST;               // direct kernel: particles per CTA
 };
 
 std::string tune_key(const tracker* t, int64_t np, int mode, int ab_order)
@@ -875,7 +803,7 @@ std::string tune_key(const tracker* t, int64_t np, int mode, int ab_order)
     const double dens = (double)np / ((double)t->N * t->N * t->N);
     const int bucket = (int)std::floor(2.0 * std::log2(dens));   // half-octave density buckets
     char buf[200];
-    snprintf(buf, sizeof(buf), "advance N=%d family=%d I=%d m=%d storage=%d sm=%d dens2=%d mode=%d order=%d", t->N,
+    snprintf(buf, sizeof(buf), "advance2 N=%d family=%d I=%d m=%d storage=%d sm=%d dens2=%d mode=%d order=%d", t->N,
              t->family, t->I, t->m, t->storage, t->nsm, bucket, mode, ab_order);
     return buf;
 }
@@ -885,26 +813,27 @@ bool valid_cand(const tracker* t, const Cand& c)
     const bool path_ok = c.path == TRK_STEP_DIRECT || c.path == TRK_STEP_BLOCK ||
                          (c.path == TRK_STEP_COLUMN && column_available(t));
     return path_ok && is_pow2(c.dir_blk) && c.dir_blk <= t->N && is_pow2(c.col_seg) && c.col_seg <= MAXSEG &&
-           (c.tma == 0 || c.tma == 1);
+           (c.tma == 0 || c.tma == 1) && (c.ppc == 128 || c.ppc == 256);
 }
 
 void apply_cand(tracker* t, const Cand& c)
 {
-    if (t->dir_blk == c.dir_blk && t->col_seg == c.col_seg && t->auto_tma == (c.tma != 0)) return;
+    if (t->dir_blk == c.dir_blk && t->col_seg == c.col_seg && t->auto_tma == (c.tma != 0) && t->dir_ppc == c.ppc) return;
     t->dir_blk = c.dir_blk;
     t->col_seg = c.col_seg;
     t->auto_tma = c.tma != 0;
+    t->dir_ppc = c.ppc;
     t->gen += 1;                      // captured step graphs hold the old launch shapes
 }
 
 void remember_tuning(tracker* t, const std::string& key, const Cand& c, bool persist)
 {
     if (t->step_tune.size() >= kCacheMax) t->step_tune.erase(t->step_tune.begin());
-    t->step_tune.push_back({key, {c.path, c.dir_blk, c.col_seg, c.tma}});
+    t->step_tune.push_back({key, {c.path, c.dir_blk, c.col_seg, c.tma, c.ppc}});
     const char* path = getenv("TRK_TUNE_CACHE");
     if (!persist || !path || !*path) return;
     if (FILE* f = fopen(path, "a")) {
-        fprintf(f, "%s|%d %d %d %d\n", key.c_str(), c.path, c.dir_blk, c.col_seg, c.tma);
+        fprintf(f, "%s|%d %d %d %d %d\n", key.c_str(), c.path, c.dir_blk, c.col_seg, c.tma, c.ppc);
         fclose(f);
     }
 }
@@ -913,14 +842,14 @@ bool lookup_tuning(const tracker* t, const std::string& key, Cand* out)
 {
     for (auto it = t->step_tune.rbegin(); it != t->step_tune.rend(); ++it)
         if (it->first == key) {
-            *out = Cand{it->second[0], it->second[1], it->second[2], it->second[3]};
+            *out = Cand{it->second[0], it->second[1], it->second[2], it->second[3], it->second[4]};
             return true;
         }
     return false;
 }
 
 // Decisions of earlier processes (TRK_TUNE_CACHE): lines "key|path dir_blk
-// col_seg tma"; malformed lines and values this tracker cannot run are skipped.
+// col_seg tma ppc"; malformed lines and values this tracker cannot run are skipped.
 void load_tune_file(tracker* t)
 {
     const char* path = getenv("TRK_TUNE_CACHE");
@@ -933,7 +862,8 @@ void load_tune_file(tracker* t)
         if (!bar) continue;
         *bar = 0;
         Cand c{};
-        if (sscanf(bar + 1, "%d %d %d %d", &c.path, &c.dir_blk, &c.col_seg, &c.tma) != 4 || !valid_cand(t, c)) continue;
+        if (sscanf(bar + 1, "%d %d %d %d %d", &c.path, &c.dir_blk, &c.col_seg, &c.tma, &c.ppc) != 5 || !valid_cand(t, c))
+            continue;
         remember_tuning(t, line, c, false);
     }
     fclose(f);
@@ -964,7 +894,8 @@ std::vector<Cand> tune_candidates(const tracker* t, int64_t np)
     }
     if (dens <= 1.0)
         for (int b : {8, 16})
-            if (b <= t->N) c.push_back({TRK_STEP_DIRECT, b, 8, 1});
+            for (int ppc : {256, 128})
+                if (b <= t->N) c.push_back({TRK_STEP_DIRECT, b, 8, 1, ppc});
     return c;
 }
 
@@ -1064,11 +995,6 @@ int tracker_destroy(tracker* t)
     if (t->stream) cudaStreamSynchronize(t->stream);
     else cudaDeviceSynchronize();
     dev_free(t->field);
-    dev_free(t->ipos);
-    dev_free(t->msd_scratch);
-    dev_free(t->msd_counts);
-    dev_free(t->msd_start);
-    dev_free(t->msd_cursor);
     dev_free(t->sort_scratch);
     dev_free(t->keys);
     dev_free(t->keys_sorted);
@@ -1259,10 +1185,12 @@ int tracker_set_tuning(tracker* t, const trk_tuning* p)
         return fail(TRK_EINVAL, "step_kernel must be TRK_STEP_BLOCK, _COLUMN or _DIRECT");
     if (p->halo_copy != TRK_HALO_ASYNC && p->halo_copy != TRK_HALO_TMA)
         return fail(TRK_EINVAL, "halo_copy must be TRK_HALO_ASYNC or TRK_HALO_TMA");
-    const Cand c{p->step_kernel, p->direct_block, p->column_segment, p->halo_copy == TRK_HALO_TMA ? 1 : 0};
+    const Cand c{p->step_kernel, p->direct_block, p->column_segment, p->halo_copy == TRK_HALO_TMA ? 1 : 0,
+                 p->direct_particles == 0 ? 256 : p->direct_particles};
     if (!valid_cand(t, c))
         return fail(TRK_EINVAL, "invalid tuning (direct_block a power of two <= N, column_segment a power of two "
-                                "<= %d, a column kernel only for F32 storage with I = 4, 6 and 8^3 blocks)", MAXSEG);
+                                "<= %d, direct_particles 128 or 256, a column kernel only for F32 storage with "
+                                "I = 4, 6 and 8^3 blocks)", MAXSEG);
     t->step_kernel = c.path;
     t->halo_copy = p->halo_copy;
     apply_cand(t, c);
@@ -1277,6 +1205,7 @@ int tracker_get_tuning(const tracker* t, trk_tuning* out)
     out->direct_block = t->last_tuning[1];
     out->column_segment = t->last_tuning[2];
     out->halo_copy = t->last_tuning[3] ? TRK_HALO_TMA : TRK_HALO_ASYNC;
+    out->direct_particles = t->last_tuning[4];
     out->source = t->tune_source;
     return TRK_OK;
 }
@@ -1358,26 +1287,14 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     if (np == 0) return TRK_OK;
     if ((rc = ensure_sort(t, np))) return rc;
     if ((direct || probe) && (rc = ensure_node_major(t))) return rc;
-    // the block kernel reads the positions gathered into block order (its
-    // particle phase otherwise waits on two dependent scattered loads with few
-    // CTAs per SM: 1024^3, I = 8, 12 components 189 -> 173 ms for a 7 ms
-    // gather); the direct kernel reads them through the permutation (the
-    // gather costs it more than it saves)
-    const bool gather = probe || !direct;
+    // the kernels read the positions through the permutation (gathering them
+    // into block order first measured slower overall: 1024^3, I = 8, 2^27
+    // tracers, the block kernel gains 5.2 ms, the gather costs 7.8 ms)
+    if ((rc = bin_counting(t, np, pos))) return rc;
     BlockArgs a = base_args(t);
     a.np = np;
-    const bool msd = msd_applies(t, np);
-    if (gather) {
-        if ((rc = ensure_interp_state(t, np))) return rc;
-        if ((rc = msd ? bin_msd(t, np, pos, true) : bin_counting_state(t, np, pos))) return rc;
-        a.perm = nullptr;      // positions grouped by block: read at j, caller index perm[j]
-        a.pos_in = t->ipos;
-        a.id_in = t->perm;
-    } else {
-        if ((rc = msd ? bin_msd(t, np, pos, false) : bin_counting(t, np, pos))) return rc;
-        a.perm = t->perm;
-        a.pos_in = pos;
-    }
+    a.perm = t->perm;
+    a.pos_in = pos;
     a.out = out;
     a.out_f64 = out_dtype == TRK_DTYPE_F64;
     const int mode = deriv ? MODE_INTERP_DERIV : MODE_INTERP;
@@ -1479,7 +1396,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     bool any_direct = path == TRK_STEP_DIRECT;
     for (const Cand& c : cands) {
         any_direct = any_direct || c.path == TRK_STEP_DIRECT;
-        Cand save{path, t->dir_blk, t->col_seg, t->auto_tma};
+        Cand save{path, t->dir_blk, t->col_seg, t->auto_tma, t->dir_ppc};
         apply_cand(t, c);
         rc = ensure_bin(t, geom_of(t, c.path).nb);
         apply_cand(t, save);
@@ -1566,7 +1483,8 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
     if (!t->prof && rest >= 2) {
         uint64_t key = mix(mix(mix(mix(0, (uint64_t)np), (uint64_t)mode), t->gen), dbits(dt));
         key = mix(mix(mix(key, (uint64_t)(uintptr_t)t->field), (uint64_t)ab_order), (uint64_t)path);
-        key = mix(mix(mix(key, (uint64_t)t->dir_blk), (uint64_t)t->col_seg), (uint64_t)t->auto_tma);
+        key = mix(mix(mix(mix(key, (uint64_t)t->dir_blk), (uint64_t)t->col_seg), (uint64_t)t->auto_tma),
+                  (uint64_t)t->dir_ppc);
         const int c0 = cur;
         rc = replay_graph(t, t->adv_graph, mix(key, (uint64_t)c0), rest / 2, [&]() {
             int r = advance_step(t, np, path, mode, ab_order, hist, dt, c0, false, nullptr, nullptr);
@@ -1580,7 +1498,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
         cur ^= 1;
     }
     t->last_kernel = path;
-    t->last_tuning = {path, t->dir_blk, t->col_seg, halo_tmap(t, mode) ? 1 : 0};
+    t->last_tuning = {path, t->dir_blk, t->col_seg, halo_tmap(t, mode) ? 1 : 0, t->dir_ppc};
     ProfScope ps(t, PROF_OTHER);
     CUDA_TRY(launch_unpermute_pos(np, t->pos_s[cur], t->id_s[cur], pos, t->stream));
     t->launches += 1;

@@ -178,14 +178,12 @@ def test_ab2_parity_and_history(storage):
 
 
 @pytest.mark.parametrize("N,layout", [(64, "uniform"), (256, "uniform"), (64, "cluster"), (32, "slices")])
-def test_interpolate_large_sets_two_level_binning(N, layout):
-    """Interpolation of more than 2^20 particles bins with the two-level
-    counting sort (shared-memory histograms over coarse buckets, then one CTA
-    per bucket): every output of both kernels (block: positions written in
-    block order by the sort; direct: read through its permutation) against
-    the oracle on a sample, the two kernels bit-identical on all particles.
-    Ragged count; a cluster where one coarse bucket holds every particle; x3
-    slices (the block shape N x N x 1)."""
+def test_interpolate_large_sets(N, layout):
+    """Interpolation of more than 2^20 particles (counting-sort binning with
+    the permutation read by the kernels): every output of the block and the
+    direct kernel bit-identical on all particles, and against the oracle on a
+    sample.  Ragged count; a cluster where one cell block holds every
+    particle; x3 slices (the block shape N x N x 1, direct kernel only)."""
     n = (1 << 20) + 12345
     rng = np.random.default_rng(N)
     field = synth.velocity_field_np(N, min(10, N // 3), 85)

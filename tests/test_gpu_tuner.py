@@ -39,10 +39,11 @@ def _run(N, storage, field, pos, steps, tuning=None, scheme=trk.TRK_RK2, dt=5e-3
 
 CASES = {
     # (N, particles per cell, storage): candidates the tuner times
-    "column_and_direct": (128, 1 / 16, trk.TRK_F32),    # column 8/16, direct 8/16
-    "dense_all_kernels": (64, 1 / 2, trk.TRK_F32),      # column 8 (N/8 = 8 slabs), block tma/async, direct 8/16
-    "sparse_direct_only": (256, 1 / 200, trk.TRK_F32),  # direct 8/16
-    "no_column_float64": (128, 1 / 16, trk.TRK_F64),    # block tma/async, direct 8/16
+    # (direct: edges 8/16 x 256/128 particles per CTA)
+    "column_and_direct": (128, 1 / 16, trk.TRK_F32),    # column 8/16, direct
+    "dense_all_kernels": (64, 1 / 2, trk.TRK_F32),      # column 8 (N/8 = 8 slabs), block tma/async, direct
+    "sparse_direct_only": (256, 1 / 200, trk.TRK_F32),  # direct
+    "no_column_float64": (128, 1 / 16, trk.TRK_F64),    # block tma/async, direct
 }
 
 
@@ -53,6 +54,7 @@ def _candidates(N, dens, storage):
         c += [dict(step_kernel=trk.TRK_STEP_COLUMN, column_segment=s) for s in (4, 8, 16) if s <= N // 8]
     c += [dict(step_kernel=trk.TRK_STEP_BLOCK, halo_copy=h) for h in (trk.TRK_HALO_TMA, trk.TRK_HALO_ASYNC)]
     c += [dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=b) for b in (4, 8, 16, 32)]
+    c += [dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=b, direct_particles=128) for b in (8, 16)]
     return c
 
 
@@ -102,7 +104,7 @@ def test_tuning_is_remembered_and_persisted(tmp_path, monkeypatch):
     assert first["source"] == trk.TRK_TUNE_TIMED and again["source"] == trk.TRK_TUNE_CACHED
     assert {k: first[k] for k in first if k != "source"} == {k: again[k] for k in again if k != "source"}
     lines = cache.read_text().splitlines()
-    assert len(lines) == 1 and lines[0].startswith("advance N=128 ")
+    assert len(lines) == 1 and lines[0].startswith("advance2 N=128 ")
     # a new tracker (as in a new process) reads the file and times nothing
     t2 = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
     t2.set_field(torch.from_numpy(field).cuda())
@@ -113,7 +115,7 @@ def test_tuning_is_remembered_and_persisted(tmp_path, monkeypatch):
     assert third["source"] == trk.TRK_TUNE_CACHED
     assert third["step_kernel"] == first["step_kernel"]
     # malformed lines and shapes this tracker cannot run are ignored
-    cache.write_text("garbage\nadvance N=128 x|3 7 8 1\n" + "\n".join(lines) + "\n")
+    cache.write_text("garbage\nadvance2 N=128 x|3 7 8 1 256\nadvance2 N=128 y|3 8 8 1\n" + "\n".join(lines) + "\n")
     t3 = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
     t3.set_field(torch.from_numpy(field).cuda())
     t3.advance(torch.from_numpy(pos).cuda(), 5e-3, 16)
@@ -121,10 +123,33 @@ def test_tuning_is_remembered_and_persisted(tmp_path, monkeypatch):
     t3.close()
 
 
+def test_tuned_block_edge_bins_bit_exactly():
+    """The block edge the tuner picked for the direct path, given to the oracle:
+    binning by cubes of that edge (tracker_bin with that block shape) equals the
+    oracle's stable binning bit for bit, for the tracers the tuner ran on."""
+    N, n = 128, 128 ** 3 // 32
+    field = synth.velocity_field_np(N, 42, 64).astype(np.float32)
+    pos = synth.uniform_particles_np(n, 65)
+    t = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
+    t.set_field(torch.from_numpy(field).cuda())
+    t.advance(torch.from_numpy(pos).cuda(), 5e-3, 16)
+    info = t.tuning()
+    assert info["source"] == trk.TRK_TUNE_TIMED
+    B = info["direct_block"] if info["step_kernel"] == trk.TRK_STEP_DIRECT else 8
+    trk.tracker_set_block(t.h, B, B, B)
+    keys, perm, offsets = t.bin(torch.from_numpy(pos).cuda())
+    rk, rp, ro = oracle.bin_particles(pos, N, (B, B, B))
+    np.testing.assert_array_equal(keys.cpu().numpy(), rk)
+    np.testing.assert_array_equal(perm.cpu().numpy(), rp)
+    np.testing.assert_array_equal(offsets.cpu().numpy(), ro)
+    t.close()
+
+
 @pytest.mark.parametrize("bad", [dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=3),
                                  dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=512),
                                  dict(step_kernel=trk.TRK_STEP_COLUMN, column_segment=128),
                                  dict(step_kernel=trk.TRK_STEP_AUTO),
+                                 dict(step_kernel=trk.TRK_STEP_DIRECT, direct_particles=100),
                                  dict(step_kernel=trk.TRK_STEP_BLOCK, halo_copy=trk.TRK_HALO_AUTO)])
 def test_set_tuning_rejects_invalid_shapes(bad):
     t = trk.Tracker(256, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_F32)
