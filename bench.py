@@ -960,7 +960,8 @@ def tuner_table(trk, dev, stream, dev_index, args, fma):
              ("direct edge 32", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=32)),
              ("direct edge 8, 128 per CTA", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=8, direct_particles=128)),
              ("direct edge 16, 128 per CTA", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=16,
-                                                   direct_particles=128))]
+                                                   direct_particles=128)),
+             ("direct edge 8, 64 per CTA", dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=8, direct_particles=64))]
     names = {trk.TRK_STEP_COLUMN: "column", trk.TRK_STEP_BLOCK: "block", trk.TRK_STEP_DIRECT: "direct"}
     for scheme, sname in ((trk.TRK_RK2, "RK2"), (trk.TRK_AB2, "AB2")):
         for dens in (1.5e-3, 1 / 64, 1 / 32, 1 / 16, 1 / 8, 1 / 4, 1 / 2):

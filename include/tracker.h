@@ -271,7 +271,8 @@ int tracker_set_halo_copy(tracker* t, int kind);
  * column_segment: x3 slabs per work item of the column kernel (a power of
  * two <= 64, at most N/8); halo_copy: the block kernel's TRK_HALO_ASYNC or
  * TRK_HALO_TMA; direct_particles: particles per thread block of the direct
- * kernel (128 or 256; 0 in tracker_set_tuning means 256).  source
+ * kernel (64, 128 or 256; 0 in tracker_set_tuning means 256; untimed calls
+ * use the largest that gives three thread blocks per SM).  source
  * (tracker_get_tuning only): how they were chosen. */
 typedef enum { TRK_TUNE_DEFAULT = 0, TRK_TUNE_TIMED = 1, TRK_TUNE_CACHED = 2, TRK_TUNE_FIXED = 3 } trk_tune_source;
 typedef struct {

@@ -813,7 +813,7 @@ bool valid_cand(const tracker* t, const Cand& c)
     const bool path_ok = c.path == TRK_STEP_DIRECT || c.path == TRK_STEP_BLOCK ||
                          (c.path == TRK_STEP_COLUMN && column_available(t));
     return path_ok && is_pow2(c.dir_blk) && c.dir_blk <= t->N && is_pow2(c.col_seg) && c.col_seg <= MAXSEG &&
-           (c.tma == 0 || c.tma == 1) && (c.ppc == 128 || c.ppc == 256);
+           (c.tma == 0 || c.tma == 1) && (c.ppc == 64 || c.ppc == 128 || c.ppc == 256);
 }
 
 void apply_cand(tracker* t, const Cand& c)
@@ -867,6 +867,17 @@ void load_tune_file(tracker* t)
         remember_tuning(t, line, c, false);
     }
     fclose(f);
+}
+
+// Particles per CTA of the direct kernel when nothing was timed: the largest
+// of 256, 128, 64 that still gives three CTAs per SM (smaller sets leave SMs
+// idle with 256: at 256^3 and 1.5e-3 particles per cell, 25,000 particles,
+// 128 per CTA took 0.044 ms per RK2 step against 0.065 ms).
+int default_ppc(const tracker* t, int64_t np)
+{
+    for (int p : {256, 128})
+        if ((np + p - 1) / p >= 3 * (int64_t)std::max(t->nsm, 1)) return p;
+    return 64;
 }
 
 // The candidates for np particles (measured on GB300, 256^3 float32, spline
@@ -1295,6 +1306,7 @@ int tracker_interpolate(tracker* t, int64_t np, const double* pos, void* out, in
     a.np = np;
     a.perm = t->perm;
     a.pos_in = pos;
+    a.ppc = default_ppc(t, np);
     a.out = out;
     a.out_f64 = out_dtype == TRK_DTYPE_F64;
     const int mode = deriv ? MODE_INTERP_DERIV : MODE_INTERP;
@@ -1386,7 +1398,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
             const bool timed = np >= kTuneMinNp && cands.size() >= 2 &&
                                steps >= kTuneStepsPerCand * (int)cands.size() + 2 && cs == cudaStreamCaptureStatusNone;
             if (!timed) cands.clear();
-            apply_cand(t, Cand{path, BLK, 8, 1});
+            apply_cand(t, Cand{path, BLK, 8, 1, default_ppc(t, np)});
         }
     }
     if (path != TRK_STEP_DIRECT && (rc = check_block_kernel_shape(t))) return rc;

@@ -55,6 +55,7 @@ def _candidates(N, dens, storage):
     c += [dict(step_kernel=trk.TRK_STEP_BLOCK, halo_copy=h) for h in (trk.TRK_HALO_TMA, trk.TRK_HALO_ASYNC)]
     c += [dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=b) for b in (4, 8, 16, 32)]
     c += [dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=b, direct_particles=128) for b in (8, 16)]
+    c += [dict(step_kernel=trk.TRK_STEP_DIRECT, direct_block=8, direct_particles=64)]
     return c
 
 
