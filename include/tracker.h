@@ -205,7 +205,7 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     through the sort permutation (all storages and kernels).
  *   TRK_STEP_DIRECT: for sparse particle sets (the paper's production runs
  *     carry ~1e-3 tracers per grid cell, Sec. 4): particles sorted by block
- *     as for BLOCK, 256 of them per thread block, each stencil gathered
+ *     as for BLOCK, 64 to 256 of them per thread block, each stencil gathered
  *     from the field in global memory, so no field sweep and no halo per
  *     cell block (all storages and kernels, any block shape; float32 and
  *     three-component split-bf16 fields are read from a node-major copy the
@@ -267,7 +267,7 @@ int tracker_set_halo_copy(tracker* t, int kind);
 /* Launch shape of the time-step path.  step_kernel: TRK_STEP_COLUMN, _BLOCK
  * or _DIRECT; direct_block: edge of the cubic cell blocks the direct kernel's
  * particles are binned by (a power of two <= N; with the default 8^3 block
- * shape; it sets how compact each thread block's 256 particles are);
+ * shape; it sets how compact each thread block's particles are);
  * column_segment: x3 slabs per work item of the column kernel (a power of
  * two <= 64, at most N/8); halo_copy: the block kernel's TRK_HALO_ASYNC or
  * TRK_HALO_TMA; direct_particles: particles per thread block of the direct
@@ -295,8 +295,10 @@ typedef struct {
  * per cell on, the column kernel with segments 8 and 16; the block kernel
  * with tensor-copy and with cp.async halos from 0.1 per cell on (from 0.01
  * without a column kernel); the direct kernel with block edges 8 and 16 and
- * 256 or 128 particles per thread block, up to one particle per cell.  Other calls use the density rule of
- * tracker_set_step_kernel with the default shape (TRK_TUNE_DEFAULT).  Every
+ * 256 or 128 particles per thread block, up to one particle per cell.
+ * Other calls use the density rule of tracker_set_step_kernel with the
+ * default shape, the direct kernel with the largest of 256, 128, 64
+ * particles per thread block that gives three per SM (TRK_TUNE_DEFAULT).  Every
  * candidate gives bit-identical steps.  When the environment variable
  * TRK_TUNE_CACHE names a file, decisions are appended to it (one line per
  * workload) and trackers created later read it.
