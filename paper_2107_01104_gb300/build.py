@@ -37,9 +37,19 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
+STAMP = LIB + ".flags"   # the extra nvcc flags the library was built with
+
+
 def up_to_date() -> bool:
+    """The library exists, is newer than every source, and was built with the
+    current extra flags (a library built with other flags is rebuilt)."""
     if not os.path.exists(LIB) or EXTRA:
         return False
+    if not os.path.exists(STAMP):
+        return False
+    with open(STAMP) as fh:
+        if fh.read().split():
+            return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
@@ -74,6 +84,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(" ".join(EXTRA))
     return LIB
 
 
