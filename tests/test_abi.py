@@ -67,3 +67,23 @@ def test_oracle_and_library_share_no_code():
         if f.endswith(".py"):
             text = open(os.path.join(ROOT, "paper_2107_01104_gb300", f)).read()
             assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_library_built_with_other_flags_is_rebuilt(lib):
+    """A library made with extra nvcc flags (an experiment) is not reused by a
+    plain build: the flags it was built with are recorded beside it."""
+    if build.EXTRA:
+        pytest.skip("extra nvcc flags set for this session")
+    assert build.up_to_date()
+    with open(build.STAMP) as fh:
+        saved = fh.read()
+    try:
+        with open(build.STAMP, "w") as fh:
+            fh.write("-DSOME_EXPERIMENT=1")
+        assert not build.up_to_date()
+        os.remove(build.STAMP)
+        assert not build.up_to_date()
+    finally:
+        with open(build.STAMP, "w") as fh:
+            fh.write(saved)
+    assert build.up_to_date()
