@@ -207,14 +207,17 @@ int tracker_advance(tracker* t, int64_t np, double* pos, float* rhs, double dt, 
  *     carry ~1e-3 tracers per grid cell, Sec. 4): particles sorted by block
  *     as for BLOCK, 64 to 256 of them per thread block, each stencil gathered
  *     from the field in global memory, so no field sweep and no halo per
- *     cell block (all storages and kernels, any block shape; float32 and
- *     three-component split-bf16 fields are read from a node-major copy the
- *     tracker keeps, 16 bytes per node, made on first use; where that copy
- *     is at most four times the L2 size (or the byte count in the
- *     environment variable TRK_NM_TEXTURE_BYTES, 0 for never) it is read
- *     through a texture object: the same bits, on the texture data path
- *     instead of the load/store one, which the gathers of a copy that
- *     mostly hits in L2 otherwise saturate).  The stage-2
+ *     cell block (all storages and kernels, any block shape; float32 fields
+ *     and split-bf16 fields whose component count is a multiple of three are
+ *     read from a node-major copy the tracker keeps, made on first use: 16
+ *     bytes per node for three float32 components, one 16-byte record per
+ *     node and chunk of three split-bf16 components (a split-bf16 field
+ *     whose copy cannot be allocated is read from the field itself); where
+ *     a three-component copy is at most four times the L2 size (or the byte
+ *     count in the environment variable TRK_NM_TEXTURE_BYTES, 0 for never)
+ *     it is read through a texture object: the same bits, on the texture
+ *     data path instead of the load/store one, which the gathers of a copy
+ *     that mostly hits in L2 otherwise saturate).  The stage-2
  *     point of RK2 is gathered wherever it lies; TRK_ECFL is raised when it
  *     is more than one cell away.
  *   TRK_STEP_AUTO (default): the tuner's choice (see tracker_set_tuning):

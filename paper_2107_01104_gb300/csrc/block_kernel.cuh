@@ -1005,8 +1005,8 @@ __device__ __forceinline__ void process_block(const BlockArgs& a, int b, int j0,
         const int base = (int)padded_index(a.f.NP, c1 - LO, c2 - LO, c3 - LO);
         if constexpr (NM == NM_TEX4)   // three components, one 16-byte texel per node
             L.load(NodeLd4<I, STORE, true>{a.f.nm, base, a.f.NP, a.f.nm_tex});
-        else if constexpr (NM == NM_VEC4)   // three components, 16 bytes per node
-            L.load(NodeLd4<I, STORE>{a.f.nm, base, a.f.NP, 0});
+        else if constexpr (NM == NM_VEC4)   // three components, 16 bytes per node (split bf16: chunk k0 / 3)
+            L.load(NodeLd4<I, STORE>{a.f.nm + (int64_t)(k0 / 3) * a.f.plane * 4, base, a.f.NP, 0});
         else if constexpr (NM == NM_SCALAR)
             L.load(NodeLd<T, I>{a.f.nm, base, a.f.NP, a.f.nmc, k0, kmax});
         else
@@ -1343,11 +1343,11 @@ cudaError_t launch_direct_t(const BlockArgs& a, cudaStream_t st)
         if constexpr (!STEP) return launch_direct_nm<T, I, DEG, MODE, STORE, NM_SCALAR>(a, st);
         return cudaErrorInvalidValue;
     } else if constexpr (STORE == ST_BF16X2) {
-        // three-component fields (all time steps) read the node-major copy
-        if (a.f.C == 3) {
-            if (!a.f.nm) return cudaErrorInvalidValue;
-            return launch_direct_vec<T, I, DEG, MODE, STORE>(a, st);
-        }
+        // the node-major copy (16 bytes per node and chunk of three components;
+        // always there for three components, i.e. for every time step), else
+        // the component-major field
+        if (a.f.nm) return launch_direct_vec<T, I, DEG, MODE, STORE>(a, st);
+        if (a.f.C == 3) return cudaErrorInvalidValue;
         return launch_direct_nm<T, I, DEG, MODE, STORE, NM_NONE>(a, st);
     } else {
         return launch_direct_nm<T, I, DEG, MODE, STORE, NM_NONE>(a, st);

@@ -125,7 +125,8 @@ struct tracker {
     // field
     int C = 0;
     void* field = nullptr;
-    float* field_nm = nullptr;        // node-major copy of the field for the direct path (float32; split-bf16 with C = 3), built on first use
+    float* field_nm = nullptr;        // node-major copy of the field for the direct path (float32; split-bf16 with C a multiple of 3), built on first use
+    bool nm_skip = false;             // split-bf16, C > 3: the copy could not be allocated for this field
     cudaTextureObject_t nm_tex = 0;   // 16-byte-texel texture over field_nm (C = 3), or 0 for plain loads
     size_t nm_bytes = 0;
     bool nm_valid = false;
@@ -634,11 +635,13 @@ void create_nm_texture(tracker* t, int64_t plane, size_t bytes, bool f32)
 // needs it; never inside a graph capture (the first step of a call is eager).
 int ensure_node_major(tracker* t)
 {
-    const bool f32 = t->storage == ST_F32, bf16 = t->storage == ST_BF16X2 && t->C == 3;
-    if (!(f32 || bf16) || t->nm_valid) return TRK_OK;
+    // split bf16: one 16-byte record per node and chunk of three components,
+    // the chunks one after the other (C = 3: one chunk)
+    const bool f32 = t->storage == ST_F32, bf16 = t->storage == ST_BF16X2 && t->C % 3 == 0;
+    if (!(f32 || bf16) || t->nm_valid || t->nm_skip) return TRK_OK;
     const int64_t NP = t->N + 2 * PAD;
     const int64_t plane = NP * NP * NP;
-    const int nmc = t->C == 3 ? 4 : t->C;
+    const int nmc = f32 ? (t->C == 3 ? 4 : t->C) : 4 * (t->C / 3);
     const size_t bytes = (size_t)plane * nmc * sizeof(float);   // 16 bytes per node for C = 3
     if (t->nm_bytes != bytes) {
         destroy_nm_texture(t);
@@ -648,6 +651,12 @@ int ensure_node_major(tracker* t)
         t->gen += 1;                  // captured graphs hold the old pointer
         if (dev_alloc(&t->field_nm, bytes) != cudaSuccess) {
             cudaGetLastError();
+            // split bf16 with more than three components: the direct kernel reads
+            // the component-major field instead
+            if (bf16 && t->C > 3) {
+                t->nm_skip = true;
+                return TRK_OK;
+            }
             return fail(TRK_ENOMEM, "cannot allocate the node-major field copy (%zu bytes)", bytes);
         }
         t->nm_bytes = bytes;
@@ -661,10 +670,13 @@ int ensure_node_major(tracker* t)
             CUDA_TRY(launch_node_major(reinterpret_cast<const float*>(t->field), t->C, nmc, plane, t->field_nm, t->stream));
         } else {
             const __nv_bfloat16* hi = reinterpret_cast<const __nv_bfloat16*>(t->field);
-            CUDA_TRY(launch_node_major_bf16(hi, hi + plane * 3, plane, t->field_nm, t->stream));
+            const __nv_bfloat16* lo = hi + plane * t->C;
+            for (int ch = 0; ch < t->C / 3; ++ch)
+                CUDA_TRY(launch_node_major_bf16(hi + plane * 3 * ch, lo + plane * 3 * ch, plane,
+                                                t->field_nm + plane * 4 * ch, t->stream));
         }
     }
-    t->launches += 1;
+    t->launches += f32 ? 1 : t->C / 3;
     t->nm_valid = true;
     return TRK_OK;
 }
@@ -1138,6 +1150,7 @@ int tracker_set_field(tracker* t, const void* src, int C, int src_dtype, int src
         ProfScope ps(t, PROF_OTHER);
         CUDA_TRY(launch_convert_field(t->storage, src_dtype == TRK_DTYPE_F64, dsrc, C, t->N, t->field, t->stream));
     }
+    t->nm_skip = false;
     t->nm_valid = false;              // the node-major copy is refreshed before its next use
     t->launches += 1;
     build_tmaps(t);

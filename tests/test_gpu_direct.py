@@ -115,7 +115,7 @@ def test_direct_texture_and_plain_loads_agree(monkeypatch, storage, I, m, scheme
 
 @pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("I,m", KERNELS)
-@pytest.mark.parametrize("C,deriv", [(3, 0), (3, 1), (9, 0), (4, 1)])
+@pytest.mark.parametrize("C,deriv", [(3, 0), (3, 1), (9, 0), (4, 1), (12, 0), (6, 1)])
 def test_direct_interpolation_bit_identical_to_block(storage, I, m, C, deriv):
     N, n = 32, 2000
     rng = np.random.default_rng(C)
@@ -299,20 +299,44 @@ def test_no_timing_for_short_calls():
     assert t.last_step_kernel() == t.step_kernel_for(n)
 
 
+@pytest.mark.parametrize("storage", [trk.TRK_F32, trk.TRK_BF16X2])
 @pytest.mark.parametrize("C,deriv", [(3, 0), (3, 1), (12, 0)])
-def test_interpolation_choice_by_timing(C, deriv):
+def test_interpolation_choice_by_timing(storage, C, deriv):
     """Inside the timed density range the first AUTO call runs both kernels and
     keeps one; every call gives the block kernel's values."""
     N, n = 32, 4099
     rng = np.random.default_rng(40 + C)
     field = rng.standard_normal((C, N, N, N)).astype(np.float32)
     x = torch.from_numpy(synth.uniform_particles_np(n, 28)).to(DEV)
-    ta = trk.Tracker(N, family=trk.TRK_SPLINE, I=8, m=3, storage=trk.TRK_F32)
+    ta = trk.Tracker(N, family=trk.TRK_SPLINE, I=8, m=3, storage=storage)
     ta.set_field(torch.from_numpy(field).to(DEV))
-    tb = trk.Tracker(N, family=trk.TRK_SPLINE, I=8, m=3, storage=trk.TRK_F32)
+    tb = trk.Tracker(N, family=trk.TRK_SPLINE, I=8, m=3, storage=storage)
     tb.set_step_kernel(trk.TRK_STEP_BLOCK)
     tb.set_field(torch.from_numpy(field).to(DEV))
     ref = tb.interpolate(x, deriv=bool(deriv))
     for _ in range(2):   # timed, then cached
         assert torch.equal(ta.interpolate(x, deriv=bool(deriv)), ref)
     ta.sync()
+
+
+def test_split_bf16_copy_follows_the_component_count():
+    """Split-bf16 fields: the direct kernel's node-major copy holds one 16-byte
+    record per node and chunk of three components; a field with another
+    component count replaces it (and a count that is not a multiple of three
+    is read from the component-major field)."""
+    N, n = 32, 1500
+    rng = np.random.default_rng(77)
+    x = torch.from_numpy(positions("uniform", N, n, 31)).to(DEV)
+    td = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_BF16X2)
+    td.set_step_kernel(trk.TRK_STEP_DIRECT)
+    tb = trk.Tracker(N, family=trk.TRK_SPLINE, I=6, m=2, storage=trk.TRK_BF16X2)
+    tb.set_step_kernel(trk.TRK_STEP_BLOCK)
+    for C in (3, 12, 4, 6, 3):
+        f = torch.from_numpy(rng.standard_normal((C, N, N, N)).astype(np.float32)).to(DEV)
+        td.set_field(f)
+        tb.set_field(f)
+        for deriv in (False, True):
+            assert torch.equal(td.interpolate(x, deriv=deriv), tb.interpolate(x, deriv=deriv)), (C, deriv)
+        assert td.field_texture() == (C == 3)
+    td.sync()
+    tb.sync()
