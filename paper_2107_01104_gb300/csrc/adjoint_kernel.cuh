@@ -367,6 +367,17 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
 // [ceil((x + G - H + 1) / BLK), floor((x + G) / BLK)], at halo offset
 // x + G - BLK bi in [0, H), taken mod nb (periodic images of the same block
 // included).
+// h + l += x with the rounding error of the float32 add kept in l (Knuth's
+// TwoSum: s = h + x exactly equals s + e; the errors are summed in l)
+__device__ __forceinline__ void two_sum_acc(float& h, float& l, float x)
+{
+    const float s = __fadd_rn(h, x);
+    const float bv = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(x, bv));
+    h = s;
+    l = __fadd_rn(l, e);
+}
+
 template <typename T, int H>
 __global__ void k_adj_gather(const __grid_constant__ AdjArgs a)
 {
@@ -413,14 +424,32 @@ __global__ void k_adj_gather(const __grid_constant__ AdjArgs a)
         if (use[c]) use[c] = a.offsets[bidx[c] + 1] != a.offsets[bidx[c]];   // empty block: no partials
     double s0 = 0, s1 = 0, s2 = 0;
     const T* gs = reinterpret_cast<const T*>(a.gscratch);
+    if constexpr (sizeof(T) == 4) {
+        // float32 partials: a compensated float32 sum (Ogita, Rump and Oishi's
+        // Sum2: the sum as hi + lo within ~1e-13 of the sum of the magnitudes)
+        // instead of float64 adds, whose pipe this GPU has little of (with
+        // float64 adds the gather ran at 86% of that pipe)
+        float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int c = 0; c < NA * NA * NA; ++c)
-        if (use[c]) {
-            const T* sb = gs + bidx[c] * 3 * H3 + hoff[c];
-            s0 += (double)sb[0];
-            s1 += (double)sb[H3];
-            s2 += (double)sb[2 * H3];
-        }
+        for (int c = 0; c < NA * NA * NA; ++c)
+            if (use[c]) {
+                const T* sb = gs + bidx[c] * 3 * H3 + hoff[c];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) two_sum_acc(h[k], l[k], (float)sb[k * H3]);
+            }
+        s0 = (double)h[0] + (double)l[0];
+        s1 = (double)h[1] + (double)l[1];
+        s2 = (double)h[2] + (double)l[2];
+    } else {
+#pragma unroll
+        for (int c = 0; c < NA * NA * NA; ++c)
+            if (use[c]) {
+                const T* sb = gs + bidx[c] * 3 * H3 + hoff[c];
+                s0 += (double)sb[0];
+                s1 += (double)sb[H3];
+                s2 += (double)sb[2 * H3];
+            }
+    }
     // every slab value is read by exactly one node: leave the slabs zero for the
     // next step's atomic adds
     T* gz = reinterpret_cast<T*>(a.gscratch);
