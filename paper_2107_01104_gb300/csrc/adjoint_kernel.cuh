@@ -361,14 +361,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_adjoint(const __
     }
 }
 
-// dLoss/dfield[k][node] += sum over the non-empty blocks whose halo holds the
-// node of their partial sums, in a fixed order of the blocks.  Along each
-// axis the blocks are those with integer index bi in
-// [ceil((x + G - H + 1) / BLK), floor((x + G) / BLK)], at halo offset
-// x + G - BLK bi in [0, H), taken mod nb (periodic images of the same block
-// included).
-// h + l += x with the rounding error of the float32 add kept in l (Knuth's
-// TwoSum: s = h + x exactly equals s + e; the errors are summed in l)
+// h + l += x, keeping the rounding error of the float32 add in l: Knuth's
+// TwoSum gives the rounded sum s = fl(h + x) and its error e with
+// h + x = s + e exactly; the errors are summed in l
 __device__ __forceinline__ void two_sum_acc(float& h, float& l, float x)
 {
     const float s = __fadd_rn(h, x);
@@ -378,6 +373,12 @@ __device__ __forceinline__ void two_sum_acc(float& h, float& l, float x)
     l = __fadd_rn(l, e);
 }
 
+// dLoss/dfield[k][node] += sum over the non-empty blocks whose halo holds the
+// node of their partial sums, in a fixed order of the blocks.  Along each
+// axis the blocks are those with integer index bi in
+// [ceil((x + G - H + 1) / BLK), floor((x + G) / BLK)], at halo offset
+// x + G - BLK bi in [0, H), taken mod nb (periodic images of the same block
+// included).
 template <typename T, int H>
 __global__ void k_adj_gather(const __grid_constant__ AdjArgs a)
 {
